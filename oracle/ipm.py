@@ -1,0 +1,405 @@
+"""Primal-dual interior-point solve of problem (10), plain and slow.  Test infrastructure.
+
+The method is the filter line-search interior-point algorithm of Wachter & Biegler,
+"On the implementation of an interior-point filter line-search algorithm for large-scale
+nonlinear programming", Math. Program. 106 (2006) (the published method of Ipopt, the
+solver family the paper's MadNLP belongs to), with that paper's default constants:
+
+  * barrier problem min phi_mu = d - mu sum ln(x - x^L) - mu sum ln(x^U - x), c(x) = 0;
+  * optimality error E_mu with the s_max = 100 scaling, stop when E_0 <= tol = 1e-8 (the
+    paper's solver tolerance, Section "Numerical results");
+  * monotone barrier update mu <- max(tol/10, min(kappa_mu mu, mu^theta_mu)) while
+    E_mu <= kappa_eps mu, tau = max(tau_min, 1 - mu);
+  * Newton step from the primal-dual system with bound multipliers eliminated, inertia
+    correction of delta_w / delta_c (their Algorithm IC);
+  * fraction-to-the-boundary step sizes, backtracking filter line search with the
+    switching condition and Armijo rule, filter augmentation, the kappa_Sigma reset of
+    the bound multipliers.
+Not included (as in the GPU path): second-order corrections, the watchdog and the
+feasibility-restoration phase; a line search that falls below alpha_min stops with
+status "linesearch".
+
+Unknowns: the diameter d (bounds (10c)) and the per-scenario z (S, 220) of model.py with
+bounds (10d).  The KKT systems are solved by kkt.SchurKKT (dense per-scenario
+Bunch-Kaufman LDL^T + scalar Schur complement on d).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import kkt, model
+
+
+@dataclass
+class Options:
+    tol: float = 1e-8
+    max_iter: int = 300
+    mu_init: float = 0.1
+    kappa_eps: float = 10.0
+    kappa_mu: float = 0.2
+    theta_mu: float = 1.5
+    tau_min: float = 0.99
+    s_max: float = 100.0
+    kappa_sigma: float = 1e10
+    bound_push: float = 1e-2
+    bound_frac: float = 1e-2
+    gamma_theta: float = 1e-5
+    gamma_phi: float = 1e-5
+    delta: float = 1.0
+    s_theta: float = 1.1
+    s_phi: float = 2.3
+    eta_phi: float = 1e-4
+    gamma_alpha: float = 0.05
+    lam_init_max: float = 1e3
+    dw0: float = 1e-4
+    dw_min: float = 1e-20
+    dw_max: float = 1e40
+    kw_minus: float = 1.0 / 3.0
+    kw_plus: float = 8.0
+    kw_plus_bar: float = 100.0
+    dc_bar: float = 1e-8
+    kappa_c: float = 0.25
+    max_ls: int = 60
+    verbose: bool = False
+
+
+@dataclass
+class State:
+    d: float
+    Z: np.ndarray
+    lam: np.ndarray
+    zL: np.ndarray
+    zU: np.ndarray
+    zLd: float
+    zUd: float
+
+
+@dataclass
+class Result:
+    status: str
+    iters: int
+    d: float
+    Z: np.ndarray
+    lam: np.ndarray
+    zL: np.ndarray
+    zU: np.ndarray
+    zLd: float
+    zUd: float
+    E0: float
+    mu: float
+    history: list = field(default_factory=list)
+
+
+class Problem:
+    """Data of one instance: parameters P, feeds F (18, S), bounds."""
+
+    def __init__(self, P, F):
+        self.P, self.F = P, F
+        self.S = F.shape[1]
+        self.n = model.NS
+        self.lo, self.hi, self.dlo, self.dhi = model.bounds(P, self.S)
+        self.hasL = np.isfinite(self.lo)
+        self.hasU = np.isfinite(self.hi)
+        self.nL = int(self.hasL.sum()) + 1   # + d
+        self.nU = int(self.hasU.sum()) + 1
+        self.m = self.S * self.n
+
+    # slacks to the bounds (1 where there is no bound, never used)
+    def sl(self, Z):
+        return np.where(self.hasL, Z - np.where(self.hasL, self.lo, 0.0), 1.0)
+
+    def su(self, Z):
+        return np.where(self.hasU, np.where(self.hasU, self.hi, 0.0) - Z, 1.0)
+
+
+def push_into_bounds(pr, opt, Z, d):
+    """Initial-point projection (Wachter & Biegler 2006, Section 3.6)."""
+    lo, hi = pr.lo, pr.hi
+    width = np.where(pr.hasL & pr.hasU, hi - lo, np.inf)
+    pL = np.minimum(opt.bound_push * np.maximum(1.0, np.abs(np.where(pr.hasL, lo, 0.0))),
+                    opt.bound_frac * width)
+    pU = np.minimum(opt.bound_push * np.maximum(1.0, np.abs(np.where(pr.hasU, hi, 0.0))),
+                    opt.bound_frac * width)
+    Z = np.where(pr.hasL, np.maximum(Z, np.where(pr.hasL, lo, 0.0) + pL), Z)
+    Z = np.where(pr.hasU, np.minimum(Z, np.where(pr.hasU, hi, 0.0) - pU), Z)
+    wd = pr.dhi - pr.dlo
+    pdl = min(opt.bound_push * max(1.0, abs(pr.dlo)), opt.bound_frac * wd)
+    pdu = min(opt.bound_push * max(1.0, abs(pr.dhi)), opt.bound_frac * wd)
+    d = min(max(d, pr.dlo + pdl), pr.dhi - pdu)
+    return Z, d
+
+
+def dual_residual(pr, st, J, Jd):
+    """grad f + J^T lam - z_L + z_U for z (S, n) and for d (scalar)."""
+    rz = np.einsum("src,sr->sc", J, st.lam) - st.zL + st.zU
+    rd = 1.0 + float(np.sum(Jd * st.lam)) - st.zLd + st.zUd
+    return rz, rd
+
+
+def optimality_error(pr, opt, st, C, J, Jd, mu):
+    """E_mu of Wachter & Biegler (2006), Eq. (5), with the s_d, s_c scalings."""
+    rz, rd = dual_residual(pr, st, J, Jd)
+    sl, su = pr.sl(st.Z), pr.su(st.Z)
+    cl = np.where(pr.hasL, st.zL * sl - mu, 0.0)
+    cu = np.where(pr.hasU, st.zU * su - mu, 0.0)
+    cld = st.zLd * (st.d - pr.dlo) - mu
+    cud = st.zUd * (pr.dhi - st.d) - mu
+    zsum = float(np.abs(st.zL).sum() + np.abs(st.zU).sum() + abs(st.zLd) + abs(st.zUd))
+    s_d = max(opt.s_max, (float(np.abs(st.lam).sum()) + zsum) / (pr.m + pr.nL + pr.nU)) / opt.s_max
+    s_c = max(opt.s_max, zsum / (pr.nL + pr.nU)) / opt.s_max
+    dual = max(float(np.abs(rz).max(initial=0.0)), abs(rd)) / s_d
+    primal = float(np.abs(C).max(initial=0.0))
+    compl = max(float(np.abs(cl).max(initial=0.0)), float(np.abs(cu).max(initial=0.0)),
+                abs(cld), abs(cud)) / s_c
+    return max(dual, primal, compl), dual, primal, compl
+
+
+def barrier_phi(pr, Z, d, mu):
+    sl, su = pr.sl(Z), pr.su(Z)
+    b = np.sum(np.log(sl[pr.hasL])) + np.sum(np.log(su[pr.hasU]))
+    b += math.log(d - pr.dlo) + math.log(pr.dhi - d)
+    return d - mu * b
+
+
+def fraction_to_boundary(pr, x, dx, lo_mask, lo, hi_mask, hi, tau):
+    """Largest alpha in (0, 1] with x + alpha dx >= (1 - tau)(x - lo) kept inside."""
+    a = 1.0
+    sl = np.where(lo_mask, x - np.where(lo_mask, lo, 0.0), 1.0)
+    neg = lo_mask & (dx < 0)
+    if np.any(neg):
+        a = min(a, float(np.min(-tau * sl[neg] / dx[neg])))
+    su = np.where(hi_mask, np.where(hi_mask, hi, 0.0) - x, 1.0)
+    pos = hi_mask & (dx > 0)
+    if np.any(pos):
+        a = min(a, float(np.min(tau * su[pos] / dx[pos])))
+    return a
+
+
+class IPM:
+    def __init__(self, P, F, opt: Options | None = None):
+        self.pr = Problem(P, F)
+        self.opt = opt or Options()
+        self.dw_last = 0.0
+
+    # ---- derivatives -------------------------------------------------------------
+    def evaluate(self, st, rows_only=False):
+        return model.derivatives(self.pr.P, self.pr.F, st.Z, st.d, st.lam, rows_only)
+
+    def sigma(self, st):
+        pr = self.pr
+        sig = (np.where(pr.hasL, st.zL / pr.sl(st.Z), 0.0)
+               + np.where(pr.hasU, st.zU / pr.su(st.Z), 0.0))
+        sigd = st.zLd / (st.d - pr.dlo) + st.zUd / (pr.dhi - st.d)
+        return sig, sigd
+
+    def barrier_gradient(self, st, mu):
+        pr = self.pr
+        gz = (np.where(pr.hasL, -mu / pr.sl(st.Z), 0.0)
+              + np.where(pr.hasU, mu / pr.su(st.Z), 0.0))
+        gd = 1.0 - mu / (st.d - pr.dlo) + mu / (pr.dhi - st.d)
+        return gz, gd
+
+    # ---- Newton direction with inertia correction -----------------------------------
+    def newton_direction(self, st, mu, C, J, Jd, W, Wdd, dw=None, dc=None):
+        """Solve the primal-dual system.  With dw/dc given, use them as is (no inertia
+        correction); else run Algorithm IC.  Returns (dZ, dd, dlam, dw, dc, fac)."""
+        pr, opt = self.pr, self.opt
+        sig, sigd = self.sigma(st)
+        gz, gd = self.barrier_gradient(st, mu)
+        rz = -(gz + np.einsum("src,sr->sc", J, st.lam))
+        rd = -(gd + float(np.sum(Jd * st.lam)))
+        rc = -C
+        Kdd = float(np.sum(Wdd)) + sigd
+        n_expect, m_expect = 1 + pr.S * pr.n, pr.S * pr.n
+
+        def factor(w, c):
+            return kkt.SchurKKT(W, sig, J, Jd, Kdd, w, c)
+
+        if dw is not None:
+            fac = factor(dw, dc)
+        else:
+            dw, dc = 0.0, 0.0
+            fac = factor(0.0, 0.0)
+            inert = fac.inertia()
+            if inert != (n_expect, m_expect, 0):
+                if inert[2] > 0:
+                    dc = opt.dc_bar * mu ** opt.kappa_c
+                dw = opt.dw0 if self.dw_last == 0.0 else max(opt.dw_min, opt.kw_minus * self.dw_last)
+                while True:
+                    fac = factor(dw, dc)
+                    if fac.inertia() == (n_expect, m_expect, 0):
+                        self.dw_last = dw
+                        break
+                    dw = (opt.kw_plus_bar if self.dw_last == 0.0 else opt.kw_plus) * dw
+                    if dw > opt.dw_max:
+                        raise RuntimeError("inertia")
+        dZ, dd, dlam = fac.solve(rz, rd, rc)
+        return dZ, dd, dlam, dw, dc, fac
+
+    def bound_dual_steps(self, st, mu, dZ, dd):
+        pr = self.pr
+        sl, su = pr.sl(st.Z), pr.su(st.Z)
+        dzL = np.where(pr.hasL, mu / sl - st.zL - (st.zL / sl) * dZ, 0.0)
+        dzU = np.where(pr.hasU, mu / su - st.zU + (st.zU / su) * dZ, 0.0)
+        sld, sud = st.d - pr.dlo, pr.dhi - st.d
+        dzLd = mu / sld - st.zLd - (st.zLd / sld) * dd
+        dzUd = mu / sud - st.zUd + (st.zUd / sud) * dd
+        return dzL, dzU, dzLd, dzUd
+
+    # ---- initial point ------------------------------------------------------------
+    def initial_state(self, Z0=None, d0=None, lam0=None):
+        pr, opt = self.pr, self.opt
+        Zi, di = model.initial_point(pr.P, pr.F)
+        Z = Zi if Z0 is None else Z0
+        d = di if d0 is None else d0
+        Z, d = push_into_bounds(pr, opt, Z, d)
+        zL = np.where(pr.hasL, 1.0, 0.0)
+        zU = np.where(pr.hasU, 1.0, 0.0)
+        st = State(d, Z, np.zeros((pr.S, pr.n)), zL, zU, 1.0, 1.0)
+        if lam0 is not None:
+            st.lam = lam0.copy()
+            return st
+        # least-squares multipliers: [I J^T; J 0][w; lam] = [-(grad f - zL + zU); 0]
+        C, J, Jd, _, _ = self.evaluate(st, rows_only=True)
+        S, n = pr.S, pr.n
+        Wid = np.broadcast_to(np.eye(n), (S, n, n))
+        fac = kkt.SchurKKT(Wid, np.zeros((S, n)), J, Jd, 1.0, 0.0, 0.0)
+        _, _, lam = fac.solve(-(-zL + zU), -(1.0 - st.zLd + st.zUd), np.zeros((S, n)))
+        if np.abs(lam).max() <= opt.lam_init_max:
+            st.lam = lam
+        return st
+
+    # ---- main loop ----------------------------------------------------------------
+    def solve(self, st=None):
+        pr, opt = self.pr, self.opt
+        st = st or self.initial_state()
+        mu = opt.mu_init
+        tau = max(opt.tau_min, 1.0 - mu)
+        filt = []
+        theta0 = None
+        hist = []
+        status = "maxiter"
+        E0 = float("inf")
+        k = 0
+        for k in range(opt.max_iter + 1):
+            C, J, Jd, W, Wdd = self.evaluate(st)
+            theta = float(np.abs(C).sum())
+            if theta0 is None:
+                theta0 = theta
+                theta_max = 1e4 * max(1.0, theta0)
+                theta_min = 1e-4 * max(1.0, theta0)
+            E0 = optimality_error(pr, opt, st, C, J, Jd, 0.0)[0]
+            if E0 <= opt.tol:
+                status = "ok"
+                break
+            if k == opt.max_iter:
+                break
+            # barrier parameter update (monotone)
+            while mu > opt.tol / 10.0:
+                Emu = optimality_error(pr, opt, st, C, J, Jd, mu)[0]
+                if Emu > opt.kappa_eps * mu:
+                    break
+                mu = max(opt.tol / 10.0, min(opt.kappa_mu * mu, mu ** opt.theta_mu))
+                tau = max(opt.tau_min, 1.0 - mu)
+                filt = []
+            try:
+                dZ, dd, dlam, dw, dc, fac = self.newton_direction(st, mu, C, J, Jd, W, Wdd)
+            except RuntimeError:
+                status = "inertia"
+                break
+            dzL, dzU, dzLd, dzUd = self.bound_dual_steps(st, mu, dZ, dd)
+            # fraction to the boundary
+            a_max = min(fraction_to_boundary(pr, st.Z, dZ, pr.hasL, pr.lo, pr.hasU, pr.hi, tau),
+                        fraction_to_boundary(pr, np.array([st.d]), np.array([dd]),
+                                             np.array([True]), np.array([pr.dlo]),
+                                             np.array([True]), np.array([pr.dhi]), tau))
+            zmask = pr.hasL
+            a_z = min(fraction_to_boundary(pr, st.zL, dzL, pr.hasL, np.zeros_like(st.zL),
+                                           np.zeros_like(pr.hasU), st.zL, tau),
+                      fraction_to_boundary(pr, st.zU, dzU, pr.hasU, np.zeros_like(st.zU),
+                                           np.zeros_like(pr.hasU), st.zU, tau),
+                      fraction_to_boundary(pr, np.array([st.zLd, st.zUd]), np.array([dzLd, dzUd]),
+                                           np.array([True, True]), np.zeros(2),
+                                           np.array([False, False]), np.zeros(2), tau))
+            del zmask
+            # filter line search
+            phi = barrier_phi(pr, st.Z, st.d, mu)
+            gz, gd = self.barrier_gradient(st, mu)
+            gphi = float(np.sum(gz * dZ)) + gd * dd
+            tiny = max(float(np.max(np.abs(dZ) / (1.0 + np.abs(st.Z)))),
+                       abs(dd) / (1.0 + abs(st.d))) < 10.0 * np.finfo(float).eps
+            alpha = a_max
+            accepted = False
+            ftype = False
+            n_ls = 0
+            if tiny:
+                accepted, alpha = True, a_max
+            else:
+                if gphi < 0:
+                    if theta <= theta_min:
+                        a_min = opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * theta / (-gphi),
+                                                      opt.delta * theta ** opt.s_theta / (-gphi) ** opt.s_phi)
+                    else:
+                        a_min = opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * theta / (-gphi))
+                else:
+                    a_min = opt.gamma_alpha * opt.gamma_theta
+                while n_ls < opt.max_ls:
+                    n_ls += 1
+                    Zt = st.Z + alpha * dZ
+                    dt = st.d + alpha * dd
+                    Ct = model.residuals(pr.P, pr.F, Zt, dt)
+                    th_t = float(np.abs(Ct).sum())
+                    ph_t = barrier_phi(pr, Zt, dt, mu)
+                    ok = np.isfinite(th_t) and np.isfinite(ph_t) and th_t <= theta_max
+                    if ok:
+                        for (tf, pf) in filt:
+                            if th_t >= tf and ph_t >= pf:
+                                ok = False
+                                break
+                    if ok:
+                        switching = gphi < 0 and alpha * (-gphi) ** opt.s_phi > opt.delta * theta ** opt.s_theta
+                        if theta <= theta_min and switching:
+                            ok = ph_t <= phi + opt.eta_phi * alpha * gphi
+                            ftype = ok
+                        else:
+                            ok = th_t <= (1 - opt.gamma_theta) * theta or ph_t <= phi - opt.gamma_phi * theta
+                    if ok:
+                        accepted = True
+                        break
+                    alpha *= 0.5
+                    if alpha < a_min:
+                        break
+            if not accepted:
+                status = "linesearch"
+                break
+            if not ftype and not tiny:
+                filt.append(((1 - opt.gamma_theta) * theta, phi - opt.gamma_phi * theta))
+            hist.append(dict(iter=k, mu=mu, E0=E0, theta=theta, alpha=alpha, alpha_z=a_z,
+                             dw=dw, dc=dc, ls=n_ls, d=st.d))
+            if opt.verbose:
+                print(f"{k:4d} E0={E0:.3e} th={theta:.3e} mu={mu:.2e} a={alpha:.3e} az={a_z:.3e} "
+                      f"dw={dw:.1e} ls={n_ls} d={st.d:.6f}")
+            # accept the step
+            st.Z = st.Z + alpha * dZ
+            st.d = st.d + alpha * dd
+            st.lam = st.lam + alpha * dlam
+            st.zL = st.zL + a_z * dzL
+            st.zU = st.zU + a_z * dzU
+            st.zLd = st.zLd + a_z * dzLd
+            st.zUd = st.zUd + a_z * dzUd
+            # kappa_Sigma safeguard of the bound multipliers (Eq. (16))
+            sl, su = pr.sl(st.Z), pr.su(st.Z)
+            ks = opt.kappa_sigma
+            st.zL = np.where(pr.hasL, np.clip(st.zL, mu / (ks * sl), ks * mu / sl), 0.0)
+            st.zU = np.where(pr.hasU, np.clip(st.zU, mu / (ks * su), ks * mu / su), 0.0)
+            sld, sud = st.d - pr.dlo, pr.dhi - st.d
+            st.zLd = min(max(st.zLd, mu / (ks * sld)), ks * mu / sld)
+            st.zUd = min(max(st.zUd, mu / (ks * sud)), ks * mu / sud)
+        return Result(status, k, st.d, st.Z, st.lam, st.zL, st.zU, st.zLd, st.zUd, E0, mu, hist)
+
+
+def solve(P, F, opt=None, **kw):
+    return IPM(P, F, opt).solve(**kw)
