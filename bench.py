@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark: Newton steps/s and solve time of the interior-point solve of the
+5000-scenario absorber design problem (seeded truncated-normal feeds, sigma 5 %, cut at
++-15 %, seed 2), on the GB300 path, at KKT tolerance E_0 <= 1e-8.
+
+One "step" is one full interior-point solve from the default start to E_0 <= 1e-8: every
+Newton iteration runs the whole hot path (fused evaluation, block-LU factorization,
+Schur complement on d, block solves, refinement, line search).  value = Newton
+iterations of the K timed solves / their device time.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp32|fp64] [--workload NAME]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Newton steps/s & solve time, 5000-scenario absorber, vs FP64 GPU path at 1e-8"
+UNIT = "Newton steps/s"
+DEFAULT_WORKLOAD = "absorber-S5000-tn5-seed2"
+# Algorithmic work per scenario and launch (derivations in DESIGN.md, "Roofline")
+EVAL_BYTES_PER_SCEN = 8 * (220 + 220 + 18 + 220 + 1497 + 661)    # read x, lambda, feed; write c, J, H
+TRIAL_BYTES_PER_SCEN = 8 * (2 * 220 + 18)                         # read x, dx, feed
+FACTOR_FLOPS_PER_SCEN = 10 * 7183 + 9 * 10406                     # stage LUs + G = At^-1 B
+SOLVE_FLOPS_PER_SCEN_RHS = 10 * (28 + 968 + 484)                  # coupling + LU apply + G product
+SOLVE_T_FLOPS_PER_SCEN = 10 * (2 * 968 + 2 * 28)                  # two LU^T applies + couplings
+
+
+def factor_bytes(es):
+    return es * (4840 + 9 * 242) + 8 * 1497 + 220
+
+
+def solve_bytes(es, nrhs):
+    return es * (4840 + 9 * 242) + 220 + 8 * 300 + nrhs * 8 * 2 * 220
+
+
+def solve_t_bytes(es):
+    return es * 4840 + 220 + 8 * 300 + 8 * 2 * 220
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(workload, sample_scen, iters, timeout=600):
+    """The oracle as it stands on the host cores: `iters` interior-point iterations on the
+    first `sample_scen` scenarios of the workload, one thread, in a fresh process."""
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+import absorber_inputs as ai
+from oracle import ipm
+F = ai.workload_feeds({workload!r})[:, :{sample_scen}]
+opt = ipm.Options(max_iter={iters})
+t = time.perf_counter()
+r = ipm.solve(ai.PARAMS, F, opt)
+el = time.perf_counter() - t
+print(json.dumps(dict(iters=r.iters, seconds=el)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=timeout)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args, S_full):
+    """Reference arm: the CPU oracle, timed on the host cores, one bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample, iters = 10, 2
+    times, its = [], []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(args.workload, sample, iters)
+        if k >= args.warmup:
+            times.append(r["seconds"])
+            its.append(r["iters"])
+    tot = sum(times)
+    value = sum(its) / tot * (sample / S_full)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / max(1, len(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded feeds)",
+        "config": {"workload": args.workload, "scenarios": S_full, "tol": 1e-8,
+                   "step": f"{iters} oracle IPM iterations on a {sample}-scenario sample, scaled by {sample}/{S_full}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{iters} IPM iterations on the first {sample} scenarios per step, "
+                                   f"per-iteration cost scaled linearly to {S_full} scenarios"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    import absorber_inputs as ai
+    S_full = ai.WORKLOADS[args.workload]["S"]
+    if args.impl == "reference":
+        run_reference(args, S_full)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2607_15420_gb300 import binding as B
+
+    P = ai.PARAMS
+    # replicas: every rank solves its own instance of the workload (independent problems)
+    F = ai.workload_feeds(args.workload)
+    prec = B.PREC_FP32 if args.precision == "fp32" else B.PREC_FP64
+    prob = B.Problem(P, F)
+    st = torch.cuda.current_stream()
+
+    def opts(profile=0, p=prec):
+        return B.default_options(precision=p, max_refine=(8 if p == B.PREC_FP32 else 0),
+                                 refine_tol=1e-12, profile=profile)
+
+    for _ in range(args.warmup):
+        r = prob.ipm_solve(opts())
+        assert r.status == 0, f"warm-up solve failed: {B.STATUS.get(r.status)}"
+
+    # ---- timed region: K full solves --------------------------------------------------
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    results = [prob.ipm_solve(opts(profile=1)) for _ in range(args.steps)]
+    e1.record(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    for r in results:
+        assert r.status == 0 and r.E0 <= 1e-8, (r.status, r.E0)
+    iters = sum(r.iters for r in results)
+    t_local = ms / 1e3
+    t = torch.tensor([t_local, float(iters)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        isum = t.clone()
+        dist.all_reduce(isum, op=dist.ReduceOp.SUM)
+        t_job, it_job = float(tmax[0]), float(isum[1])
+    else:
+        t_job, it_job = t_local, float(iters)
+    value = it_job / t_job
+
+    # ---- per-kernel roofline (CUDA events around each hot launch, inside the timed solves)
+    es = 4 if prec == B.PREC_FP32 else 8
+    hbm, hbm_src = load_peaks()
+    kms = [sum(r.kernel_ms[k] for r in results) for k in range(5)]
+    kn = [sum(r.kernel_launches[k] for r in results) for k in range(5)]
+    Sx = prob.S
+    work = {  # (flops, bytes) per launch
+        "eval": (None, EVAL_BYTES_PER_SCEN * Sx),
+        "eval_trial": (None, TRIAL_BYTES_PER_SCEN * Sx),
+        "factor": (FACTOR_FLOPS_PER_SCEN * Sx, factor_bytes(es) * Sx),
+        "solve": (SOLVE_FLOPS_PER_SCEN_RHS * Sx * 1.5, solve_bytes(es, 1.5) * Sx),
+        "solve_t": (SOLVE_T_FLOPS_PER_SCEN * Sx, solve_t_bytes(es) * Sx),
+    }
+    fma64 = B.measure_fma_peak(0)
+    fma32 = B.measure_fma_peak(1)
+    alu_peak = (fma32 if es == 4 else 1250.0)   # GFLOP/s: FP32 measured; FP64 nominal 1.25 TFLOP/s
+    kern = {}
+    for k, name in enumerate(B.KERNELS):
+        if kn[k] == 0:
+            continue
+        avg_s = kms[k] / kn[k] / 1e3
+        fl, by = work[name]
+        kern[name] = {"launches": kn[k], "avg_us": 1e6 * avg_s, "share_of_solve": kms[k] / ms,
+                      "GB_s": by / avg_s / 1e9, "GFLOP_s": (fl / avg_s / 1e9) if fl else None}
+    dom = max(kern, key=lambda n: kms[B.KERNELS.index(n)])
+    dk = kern[dom]
+    fl, by = work[dom]
+    intensity = (fl / by) if fl else 0.0
+    balance = alu_peak / hbm
+    if fl and intensity > balance:
+        roof = {"bound": "alu", "achieved": dk["GFLOP_s"] / 1e3, "peak": alu_peak / 1e3, "unit": "TFLOP/s",
+                "frac": dk["GFLOP_s"] / alu_peak,
+                "peak_source": ("measured FP32 FMA throughput" if es == 4 else
+                                "nominal FP64 1.25 TFLOP/s of the GB300 table")}
+    else:
+        roof = {"bound": "hbm", "achieved": dk["GB_s"], "peak": hbm, "unit": "GB/s", "frac": dk["GB_s"] / hbm,
+                "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json)"}
+    roof.update({"kernel": dom, "traffic": None, "algorithmic_bytes_per_launch": by,
+                 "algorithmic_flops_per_launch": fl})
+
+    # ---- end to end through the C ABI: pinned host feeds in, solution out ------------
+    e2e = None
+    if not args.no_e2e:
+        hf = torch.from_numpy(np.ascontiguousarray(F)).pin_memory()
+        xo = torch.empty(prob.n_primal, dtype=torch.float64, device="cuda")
+        xh = torch.empty(prob.n_primal, dtype=torch.float64).pin_memory()
+        dfe = torch.empty(F.shape, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eit = 0
+        for _ in range(args.steps):
+            dfe.copy_(hf, non_blocking=True)          # H2D of the step's inputs
+            prob.set_feeds(dfe)
+            r = prob.ipm_solve(opts(), x_out=xo)
+            xh.copy_(xo, non_blocking=True)           # D2H of the step's result
+            torch.cuda.synchronize()
+            assert r.status == 0
+            eit += r.iters
+        te = time.perf_counter() - t0
+        e2e = {"value": eit / te, "unit": UNIT, "h2d_bytes_per_step": int(F.nbytes),
+               "d2h_bytes_per_step": int(prob.n_primal * 8), "solve_time_s": te / args.steps}
+
+    # ---- the other precision path, for the comparison the metric names ------------------
+    other_p = B.PREC_FP64 if prec == B.PREC_FP32 else B.PREC_FP32
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(st)
+    ro = [prob.ipm_solve(opts(p=other_p)) for _ in range(2)]
+    e3.record(st)
+    torch.cuda.synchronize()
+    oms = e2.elapsed_time(e3)
+    other = {"precision": "fp64" if other_p == B.PREC_FP64 else "fp32+fp64-refinement",
+             "value": sum(r.iters for r in ro) / (oms / 1e3), "solve_time_s": oms / 2e3,
+             "iters": [r.iters for r in ro], "d": ro[0].d, "status": [r.status for r in ro]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample, its = 50, 6
+        rb = cpu_baseline(args.workload, sample, its)
+        cpu = {"value": rb["iters"] / rb["seconds"] * (sample / Sx), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{rb['iters']} IPM iterations of the oracle on the first {sample} of the {Sx} "
+                         f"scenarios ({rb['seconds']:.1f} s), per-iteration cost scaled linearly to {Sx}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == B.PREC_FP32 else "f64",
+            "data": "synthetic (seeded feeds; the paper's measured cases are not published)",
+            "config": {"workload": args.workload, "scenarios": Sx, "variables": int(prob.sizes.n_var_paper),
+                       "tol": 1e-8, "precision": args.precision,
+                       "step": "one full interior-point solve from the default start to E_0 <= 1e-8",
+                       "parallelism": f"replicas x{world}",
+                       "l2": "working set > L2 (factors + Jacobian values ~ 0.3-0.6 GB per iteration)"},
+            "solve_time_s": ms / 1e3 / args.steps,
+            "iters_per_solve": [r.iters for r in results],
+            "d_opt": results[0].d, "E0": max(r.E0 for r in results),
+            "phase_ms_per_solve": {n: sum(r.phase_ms[i] for r in results) / args.steps
+                                   for i, n in enumerate(B.PHASES)},
+            "kernels": kern, "roofline": roof,
+            "fma_peaks_gflops": {"fp64": fma64, "fp32": fma32},
+            "other_precision": other,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": int(sum(r.launches for r in results)),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

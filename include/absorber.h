@@ -1,0 +1,280 @@
+/*
+ * absorber.h -- C ABI of the GB300 (sm_103a) library for the scenario-based absorber
+ * diameter design problem of "Harnessing GPU Acceleration in Large-Scale Process
+ * Optimization" (Huang, Shu, Schanen, Anitescu, Gandhi, Shin).
+ *
+ * Problem (10) of the paper:  min d  s.t. for every scenario w and stage n the MESH
+ * equations (1) material, (3a) reaction equilibrium, (4) summation, (6) energy,
+ * (9a) Raoult / (9b) Henry phase equilibrium; the hydraulic rows (10b)
+ *     V_nw R T_nw / P_w - u_max pi d^2 / 4 <= 0;
+ * and the bounds (10c-d).  The shared diameter d is the only coupling between
+ * scenarios (Section "Replicated scenario structure").
+ *
+ * Unknown layout (per scenario, 220 = 10 stages x 22, stage-major, stage 0 = bottom):
+ *   j = 0..8   xt_i  scaled liquid mole fraction of MEA, MEAH+, H+, MEACOO-, HCO3-,
+ *                    OH-, CO3--, CO2, H2O   (x_i = sx_i * xt_i)
+ *   j = 9..12  yt_i  scaled vapour mole fraction of CO2, H2O, N2, O2
+ *   j = 13, 14 L, V  liquid / vapour molar flow leaving the stage [kmol/s]
+ *   j = 15     Tt    temperature / sT  (sT = 100 K)
+ *   j = 16..20 eps_r reaction extents of R1..R5 [kmol/s]
+ *   j = 21     s     slack of the stage's hydraulic row, s >= 0
+ * Row layout (per scenario, 220, stage-major):
+ *   r = 0..10 material balance per species (order above plus N2, O2); 11 (9a);
+ *   12 (9b); 13..17 (3a) for R1..R5; 18, 19 (4) liquid / vapour; 20 (6);
+ *   21 (10b) as  V R T / P - u_max pi d^2/4 + s = 0.
+ * The paper's 90 variable-fixings per scenario (y = 0 for the 7 non-volatile species,
+ * x = 0 for N2, O2) are eliminated; abs_sizes reports the paper's counts.
+ *
+ * Device vectors are structure-of-arrays over scenarios with leading dimension
+ * ld = S rounded up to a multiple of 32 (abs_sizes.ld): entry v of scenario s is at
+ * [v * ld + s]; padding entries s >= S are ignored on input and unspecified on output.
+ * A "primal vector" has 220*ld + 1 doubles, the last one being d.  A "row vector" has
+ * 220*ld doubles.
+ *
+ * Ownership: the library owns the opaque abs_problem and every workspace inside it
+ * (freed by absorber_destroy).  The caller owns every buffer passed by pointer.
+ * Pointers documented "device" must be CUDA device (or managed) memory on the
+ * handle's device; "host" pointers are ordinary host memory.
+ * Streams: calls are asynchronous on the given stream unless documented otherwise.
+ * Errors: no exception crosses the ABI; every call returns an abs_status, and
+ * abs_last_error(h) gives a static description of the last error on that handle.
+ * A handle is not thread-safe: serialise calls on one handle.
+ */
+#ifndef ABSORBER_H
+#define ABSORBER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct abs_problem abs_problem;
+typedef struct CUstream_st* abs_stream_t; /* same type as cudaStream_t; NULL = default */
+
+typedef int abs_status;
+#define ABS_OK              0
+#define ABS_ERR_ARG        -1   /* invalid argument (NULL pointer, S < 1, bad option) */
+#define ABS_ERR_CUDA       -2   /* a CUDA runtime call failed */
+#define ABS_ERR_OOM        -3   /* device allocation failed */
+#define ABS_ERR_INERTIA    -4   /* inertia correction exceeded delta_w_max */
+#define ABS_ERR_LINESEARCH -5   /* step size fell below alpha_min (no restoration) */
+#define ABS_ERR_MAXITER    -6   /* iteration limit reached */
+#define ABS_ERR_NUMERIC    -7   /* NaN/Inf, or a singular stage Jacobian block */
+#define ABS_ERR_TIMEOUT    -8   /* a device-side wait gave up */
+#define ABS_ERR_INFEASIBLE -9   /* bounds inconsistent (e.g. d_lo >= d_hi) */
+
+#define ABS_NV_STAGE 22
+#define ABS_N_STAGES 10
+#define ABS_NV_SCEN 220
+#define ABS_N_FEED 18
+
+/* Model parameter table (problem data).  Units: flows kmol/s, T K, P bar, enthalpy
+ * MJ/kmol, cp MJ/(kmol K), d m, u m/s, R bar m^3/(kmol K).  Each field is one
+ * constant of the case-study model (Section "Case study"): the Kent-Eisenberg
+ * correlation ln K_r = A + B/T + C ln T + D T, Antoine water Psat
+ * ln Psat = a - b/(T + c), Henry ln H = ha + hb/T + hm x_MEA^app + hw x_H2O^app
+ * with c_CO2 = rho_L x_CO2, ideal-mixture enthalpies
+ * h_i(T) = ref + cpa (T - Tref) + cpb/2 (T - Tref)^2 + dh. */
+typedef struct abs_params {
+    double R, u_max, d_lo, d_hi, T_lo, T_hi, T_ref;
+    double sx[9], sy[4], sT;
+    double KE_A[5], KE_B[5], KE_C[5], KE_D[5];
+    double psat_a, psat_b, psat_c;
+    double henry_a, henry_b, henry_m, henry_w, rho_L;
+    double hL_ref[9], hL_cpa[9], hL_cpb[9], hL_dh[9];
+    double hV_ref[4], hV_cpa[4], hV_cpb[4], hV_dh[4];
+} abs_params;
+
+typedef struct abs_sizes {
+    int64_t S, ld;
+    /* the paper's counts for this S (Section "Numerical results") */
+    int64_t n_var_paper, n_mesh, n_fix, n_hyd;
+    /* the solver's NLP after eliminating the fixings: n = 220 S + 1, m = 220 S */
+    int64_t n_unknowns, n_rows;
+    /* per-scenario sparsity (identical for every scenario) */
+    int32_t nnzJ_scen, nnzH_scen;
+} abs_sizes;
+
+/* Create a problem instance (Section "Problem setup"; Eq. (8) with (10)).
+ *   p      host; the parameter table (copied).
+ *   feeds  host or device; [18][S] doubles, field-major: V0, y0[CO2,H2O,N2,O2], T0,
+ *          Lin, xin[9 liquid species], Tin, P  (flue gas in at the bottom, lean
+ *          solvent in at the top, absorber pressure).  Copied.
+ *   prob   host, S probabilities p_w of (8a) or NULL (1/S each).  Problem (10a) has no
+ *          operating cost, so they do not enter the solution; they are validated and
+ *          kept for completeness.
+ *   S      number of scenarios, >= 1.
+ *   out    receives the handle.
+ * Uses the current CUDA device.  Synchronous.  Errors: ABS_ERR_ARG, ABS_ERR_OOM,
+ * ABS_ERR_CUDA, ABS_ERR_INFEASIBLE (bad bounds). */
+abs_status absorber_create(const abs_params* p, const double* feeds, const double* prob,
+                           int64_t S, abs_problem** out);
+
+/* Replace the feeds of an existing problem (same S), e.g. to re-solve with new scenario
+ * data without reallocating.  feeds: host or device, [18][S] as in absorber_create; a
+ * host array is copied synchronously, a device array asynchronously on the stream.
+ * Errors: ABS_ERR_ARG, ABS_ERR_NUMERIC (non-finite host value), ABS_ERR_CUDA. */
+abs_status absorber_set_feeds(abs_problem* h, const double* feeds, abs_stream_t stream);
+
+/* Release the handle and every workspace it owns.  NULL is a no-op. */
+void absorber_destroy(abs_problem* h);
+
+/* Static text describing the last error recorded on h (or a global one if h is NULL). */
+const char* abs_last_error(const abs_problem* h);
+
+/* Sizes: the paper's counts (1 + 300 S variables, 210 S MESH rows, 90 S fixings,
+ * 10 S hydraulic rows) and the solver's. */
+abs_status absorber_sizes(const abs_problem* h, abs_sizes* out);
+
+/* Host-only (no device needed): the per-scenario pattern sizes and patterns, as
+ * absorber_pattern returns them.  Any of the array pointers may be NULL. */
+abs_status abs_scenario_pattern(int32_t* nnzJ_scen, int32_t* nnzH_scen, int32_t* jrow,
+                                int32_t* jcol, int32_t* hrow, int32_t* hcol);
+
+/* Host-only: sizeof of the ABI structs, for binding checks.  which: 0 abs_params,
+ * 1 abs_sizes, 2 abs_kkt_diag, 3 abs_inertia, 4 abs_solve_info, 5 abs_options,
+ * 6 abs_result; -1 for an unknown index. */
+int64_t abs_struct_size(int which);
+
+/* Per-scenario sparsity patterns (host arrays), identical for every scenario.
+ *   jrow, jcol: nnzJ_scen entries of dc_s/d(z_s, d) in CSR order (row ascending, then
+ *               column ascending); columns 0..219 are z_s, column 220 is d.
+ *   hrow, hcol: nnzH_scen entries of the lower triangle (row >= col) of the
+ *               Lagrangian Hessian in CSR order; the last entry is (220, 220), the
+ *               scenario's contribution to d-d (entries over scenarios are summed).
+ * Value arrays of eval_grad_jac_hess hold entry k of scenario s at [k * ld + s]. */
+abs_status absorber_pattern(const abs_problem* h, int32_t* jrow, int32_t* jcol,
+                            int32_t* hrow, int32_t* hcol);
+
+/* Objective, gradient, constraints, Jacobian and Lagrangian-Hessian values in one
+ * fused pass over (scenario, stage) -- the replicated constraint families of Eqs.
+ * (1), (3a), (4), (6), (9a-b), (10b) with analytic derivatives.
+ *   x         device, primal vector (220*ld + 1).
+ *   lambda    device, row vector: equality multipliers (may be NULL if hess_vals is).
+ *   obj_factor  multiplies the objective (d) and its derivatives.
+ *   f         host, receives obj_factor * d (may be NULL).
+ *   grad      device primal vector or NULL: obj_factor * e_d.
+ *   c         device row vector or NULL: residuals.
+ *   jac_vals  device, nnzJ_scen * ld, or NULL.
+ *   hess_vals device, nnzH_scen * ld, or NULL: Hessian of sum_rows lambda c (the
+ *             objective is linear).
+ * Asynchronous except when f != NULL (reads d back). */
+abs_status eval_grad_jac_hess(abs_problem* h, const double* x, const double* lambda,
+                              double obj_factor, double* f, double* grad, double* c,
+                              double* jac_vals, double* hess_vals, abs_stream_t stream);
+
+#define ABS_PREC_FP64 0   /* stage-block LU and solves in FP64 */
+#define ABS_PREC_FP32 1   /* stage-block LU and solves in FP32, FP64 refinement */
+
+typedef struct abs_kkt_diag {
+    const double* sigma;  /* device primal vector: barrier diagonal Sigma (d last) */
+    double delta_w;       /* primal regularisation */
+    double delta_c;       /* dual regularisation; must be 0 (see kkt_factor) */
+} abs_kkt_diag;
+
+typedef struct abs_inertia {
+    int64_t n_pos, n_neg, n_zero;   /* inertia of the whole KKT matrix */
+    double schur_d;                 /* the scalar Schur complement on d */
+    int64_t n_singular;             /* scenarios whose stage-block LU met a tiny pivot */
+} abs_inertia;
+
+/* Factor the primal-dual matrix of one interior-point iteration (Wachter & Biegler
+ * 2006, Eq. (13); the paper's KKT step, Section "GPU-resident solution")
+ *     K = [ W + Sigma + dw I , J^T ; J , -dc I ]
+ * for the bordered block-diagonal structure of (10): every scenario block's
+ * constraint Jacobian J_s (220 x 220, block tridiagonal with 22 x 22 stage blocks) is
+ * factored by a block LU with partial pivoting inside each stage block, and the
+ * scenarios are eliminated onto d by a scalar Schur complement
+ *     S_d = K_dd + sum_s q_s^T (W_s + Sigma_s + dw I) q_s,   q_s = J_s^{-1} b_s.
+ * With J_s nonsingular each scenario block has inertia (220, 220, 0) whatever W_s is,
+ * so the inertia of K is that plus the sign of S_d (Haynsworth).
+ *   x, jac_vals, hess_vals  device, as produced by eval_grad_jac_hess at the iterate.
+ *   diag       host struct; delta_c must be 0 (a singular J_s is reported in
+ *              n_singular and by ABS_ERR_NUMERIC instead of regularised).
+ *   precision  ABS_PREC_FP64 or ABS_PREC_FP32.
+ *   inertia    host, receives the inertia (the call synchronises the stream).
+ * The factorization stays in the handle for kkt_solve. */
+abs_status kkt_factor(abs_problem* h, const double* x, const double* jac_vals,
+                      const double* hess_vals, const abs_kkt_diag* diag, int precision,
+                      abs_inertia* inertia, abs_stream_t stream);
+
+typedef struct abs_solve_info {
+    int32_t refine_steps;       /* FP64 refinement steps taken */
+    double residual;            /* final scaled residual ||r - K s||_inf / (||r||_inf + tiny) */
+} abs_solve_info;
+
+/* Solve K sol = rhs with the last kkt_factor: per-scenario forward/backward block
+ * solves, the Schur step on d, back-substitution, then FP64 iterative refinement on
+ * the full residual (computed from the FP64 jac/hess values) until the scaled residual
+ * is <= refine_tol or max_refine steps were taken.
+ *   rhs_x, sol_x  device primal vectors (220*ld + 1).
+ *   rhs_c, sol_c  device row vectors (220*ld).
+ *   info          host or NULL (if non-NULL the call synchronises).          */
+abs_status kkt_solve(abs_problem* h, const double* rhs_x, const double* rhs_c,
+                     double* sol_x, double* sol_c, int max_refine, double refine_tol,
+                     abs_solve_info* info, abs_stream_t stream);
+
+/* Options of the interior-point solve.  abs_default_options fills the published
+ * defaults of Wachter & Biegler (2006) and tol = 1e-8 (the paper's tolerance). */
+typedef struct abs_options {
+    double tol;            /* stop when E_0 <= tol */
+    int32_t max_iter;
+    int32_t precision;     /* ABS_PREC_FP64 / ABS_PREC_FP32 */
+    int32_t max_refine;    /* refinement steps per Newton solve */
+    double refine_tol;     /* scaled residual target of the refinement */
+    double mu_init, kappa_eps, kappa_mu, theta_mu, tau_min, s_max, kappa_sigma;
+    double bound_push, bound_frac;
+    double gamma_theta, gamma_phi, delta, s_theta, s_phi, eta_phi, gamma_alpha;
+    double lam_init_max;
+    double dw0, dw_min, dw_max, kw_minus, kw_plus, kw_plus_bar;
+    int32_t max_ls;        /* maximum line-search trials per iteration */
+    int32_t verbose;       /* 1: print one line per iteration to stdout */
+    int32_t profile;       /* 1: time the hot kernels with CUDA events (abs_result.kernel_*) */
+} abs_options;
+
+void abs_default_options(abs_options* o);
+
+#define ABS_N_PHASES 6   /* eval, factor, solve, linesearch, step, other */
+#define ABS_N_KERNELS 5  /* eval (residual+Jacobian+Hessian), eval (line-search trial),
+                            stage-block LU, block solve J x = r, block solve J^T y = g */
+
+typedef struct abs_result {
+    abs_status status;
+    int32_t iters;
+    int32_t ls_trials;           /* line-search trial evaluations in total */
+    int32_t inertia_corrections; /* iterations that needed delta_w > 0 */
+    int32_t refine_steps;        /* refinement steps in total */
+    double d, obj, E0, mu;
+    double inf_pr, inf_du;
+    double solve_ms;             /* wall time of ipm_solve (host clock) */
+    double phase_ms[ABS_N_PHASES];  /* CUDA-event time per phase */
+    double kernel_ms[ABS_N_KERNELS];        /* with options.profile: summed kernel time */
+    int32_t kernel_launches[ABS_N_KERNELS]; /* ... and launch counts */
+    int64_t launches;            /* every kernel this library launched during the solve */
+} abs_result;
+
+/* Diagnostic: measured throughput of dependent-free fused multiply-adds on the current
+ * device, in GFLOP/s (2 flops per FMA).  kind 0: FP64, kind 1: FP32.  Synchronous. */
+abs_status abs_measure_fma_peak(int kind, double* gflops);
+
+/* Interior-point solve of problem (10) on the device (the paper's GPU-resident
+ * solution, Section "GPU-resident solution with MadNLP.jl"): filter line-search
+ * primal-dual method after Wachter & Biegler (2006), with the eval kernel, the
+ * block-LU + Schur KKT factorization and solve, and every vector update running in this
+ * library's kernels; the host only sequences launches and reads a few scalars per
+ * iteration.  Starts from the documented default point (every stage copies the inlet
+ * streams, d = (d_lo + d_hi)/2) unless warm_x is given.
+ *   opt     host (NULL = defaults).
+ *   warm_x  device primal vector or NULL; warm_y device row vector or NULL.
+ *   res     host, required.
+ *   x_out   device primal vector or NULL;  y_out device row vector or NULL.
+ * Synchronous (returns when the solve has finished). */
+abs_status ipm_solve(abs_problem* h, const abs_options* opt, const double* warm_x,
+                     const double* warm_y, abs_result* res, double* x_out, double* y_out,
+                     abs_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABSORBER_H */

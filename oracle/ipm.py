@@ -5,7 +5,11 @@ The method is the filter line-search interior-point algorithm of Wachter & Biegl
 nonlinear programming", Math. Program. 106 (2006) (the published method of Ipopt, the
 solver family the paper's MadNLP belongs to), with that paper's default constants:
 
-  * barrier problem min phi_mu = d - mu sum ln(x - x^L) - mu sum ln(x^U - x), c(x) = 0;
+  * barrier problem min phi_mu = w d - mu sum ln(x - x^L) - mu sum ln(x^U - x), c(x) = 0,
+    with the objective scaled by w = S (Ipopt's objective scaling factor; the solution is
+    unchanged): unscaled, the barrier terms of the 10 S hydraulic slacks outweigh the
+    single objective d until mu << d*/(20 S), so the early central path sits at d's upper
+    bound for large S; with w = S it tracks d* for every S;
   * optimality error E_mu with the s_max = 100 scaling, stop when E_0 <= tol = 1e-8 (the
     paper's solver tolerance, Section "Numerical results");
   * monotone barrier update mu <- max(tol/10, min(kappa_mu mu, mu^theta_mu)) while
@@ -15,9 +19,16 @@ solver family the paper's MadNLP belongs to), with that paper's default constant
   * fraction-to-the-boundary step sizes, backtracking filter line search with the
     switching condition and Armijo rule, filter augmentation, the kappa_Sigma reset of
     the bound multipliers.
-Not included (as in the GPU path): second-order corrections, the watchdog and the
-feasibility-restoration phase; a line search that falls below alpha_min stops with
-status "linesearch".
+  * second-order corrections (their Section 2.4): when the first trial point is rejected
+    and increases theta, up to p_max = 4 corrected steps from the same factorization with
+    right-hand side c_soc = alpha c(x) + c(x + alpha dx), accepted by the same tests.
+Not included (as in the GPU path): the watchdog and the feasibility-restoration phase; a
+line search that falls below alpha_min stops with status "linesearch".
+
+Starting point (the paper says only that all configurations used the same one): for
+S > 1 the stage states of the expected-value problem's solution (one scenario with the
+mean feed, itself solved from the inlet-copy start), see IPM.basecase_start; for S = 1
+the inlet-copy start of model.initial_point.
 
 Unknowns: the diameter d (bounds (10c)) and the per-scenario z (S, 220) of model.py with
 bounds (10d).  The KKT systems are solved by kkt.SchurKKT (dense per-scenario
@@ -63,6 +74,10 @@ class Options:
     dc_bar: float = 1e-8
     kappa_c: float = 0.25
     max_ls: int = 60
+    soc_max: int = 4
+    kappa_soc: float = 0.99
+    obj_scaling: float | None = None   # None: the number of scenarios S
+    init: str = "basecase"             # "basecase" (S > 1) or "inlet"
     verbose: bool = False
 
 
@@ -91,13 +106,15 @@ class Result:
     E0: float
     mu: float
     history: list = field(default_factory=list)
+    base_iters: int = 0
 
 
 class Problem:
     """Data of one instance: parameters P, feeds F (18, S), bounds."""
 
-    def __init__(self, P, F):
+    def __init__(self, P, F, w=1.0):
         self.P, self.F = P, F
+        self.w = w                   # objective scaling: the solver minimises w * d
         self.S = F.shape[1]
         self.n = model.NS
         self.lo, self.hi, self.dlo, self.dhi = model.bounds(P, self.S)
@@ -135,7 +152,7 @@ def push_into_bounds(pr, opt, Z, d):
 def dual_residual(pr, st, J, Jd):
     """grad f + J^T lam - z_L + z_U for z (S, n) and for d (scalar)."""
     rz = np.einsum("src,sr->sc", J, st.lam) - st.zL + st.zU
-    rd = 1.0 + float(np.sum(Jd * st.lam)) - st.zLd + st.zUd
+    rd = pr.w + float(np.sum(Jd * st.lam)) - st.zLd + st.zUd
     return rz, rd
 
 
@@ -161,7 +178,7 @@ def barrier_phi(pr, Z, d, mu):
     sl, su = pr.sl(Z), pr.su(Z)
     b = np.sum(np.log(sl[pr.hasL])) + np.sum(np.log(su[pr.hasU]))
     b += math.log(d - pr.dlo) + math.log(pr.dhi - d)
-    return d - mu * b
+    return pr.w * d - mu * b
 
 
 def fraction_to_boundary(pr, x, dx, lo_mask, lo, hi_mask, hi, tau):
@@ -180,8 +197,9 @@ def fraction_to_boundary(pr, x, dx, lo_mask, lo, hi_mask, hi, tau):
 
 class IPM:
     def __init__(self, P, F, opt: Options | None = None):
-        self.pr = Problem(P, F)
         self.opt = opt or Options()
+        w = float(F.shape[1]) if self.opt.obj_scaling is None else float(self.opt.obj_scaling)
+        self.pr = Problem(P, F, w)
         self.dw_last = 0.0
 
     # ---- derivatives -------------------------------------------------------------
@@ -199,7 +217,7 @@ class IPM:
         pr = self.pr
         gz = (np.where(pr.hasL, -mu / pr.sl(st.Z), 0.0)
               + np.where(pr.hasU, mu / pr.su(st.Z), 0.0))
-        gd = 1.0 - mu / (st.d - pr.dlo) + mu / (pr.dhi - st.d)
+        gd = pr.w - mu / (st.d - pr.dlo) + mu / (pr.dhi - st.d)
         return gz, gd
 
     # ---- Newton direction with inertia correction -----------------------------------
@@ -267,15 +285,46 @@ class IPM:
         S, n = pr.S, pr.n
         Wid = np.broadcast_to(np.eye(n), (S, n, n))
         fac = kkt.SchurKKT(Wid, np.zeros((S, n)), J, Jd, 1.0, 0.0, 0.0)
-        _, _, lam = fac.solve(-(-zL + zU), -(1.0 - st.zLd + st.zUd), np.zeros((S, n)))
+        _, _, lam = fac.solve(-(-zL + zU), -(pr.w - st.zLd + st.zUd), np.zeros((S, n)))
         if np.abs(lam).max() <= opt.lam_init_max:
             st.lam = lam
         return st
 
+    def state_from_result(self, r):
+        """The solver's internal iterate (multipliers of the scaled problem) for a Result."""
+        w = self.pr.w
+        return State(r.d, r.Z.copy(), r.lam * w, r.zL * w, r.zU * w, r.zLd * w, r.zUd * w)
+
+    def basecase_start(self):
+        """Starting states from the expected-value problem (reading of the paper's "same
+        initial point"): solve the single scenario whose feed is the mean of the S feeds
+        from the inlet-copy start, copy its stage states to every scenario, keep
+        d = (d^L + d^U)/2 and set each hydraulic slack from its row.  None when S = 1,
+        when init = "inlet", or when the base case does not converge."""
+        pr, opt = self.pr, self.opt
+        if pr.S == 1 or opt.init != "basecase":
+            return None
+        from dataclasses import replace
+        r1 = IPM(pr.P, pr.F.mean(axis=1, keepdims=True), replace(opt, init="inlet", verbose=False)).solve()
+        if r1.status != "ok":
+            return None
+        Z0 = np.repeat(r1.Z, pr.S, axis=0).reshape(pr.S, model.N, model.NV)
+        d0 = 0.5 * (pr.dlo + pr.dhi)
+        vol = model.hydraulic_volume(pr.P, pr.F, Z0.reshape(pr.S, -1))
+        Z0[:, :, model.IS] = pr.P["u_max"] * math.pi * d0 * d0 / 4.0 - vol
+        return Z0.reshape(pr.S, -1), d0, r1.iters
+
     # ---- main loop ----------------------------------------------------------------
     def solve(self, st=None):
         pr, opt = self.pr, self.opt
-        st = st or self.initial_state()
+        base_iters = 0
+        if st is None:
+            bc = self.basecase_start()
+            if bc is not None:
+                st = self.initial_state(Z0=bc[0], d0=bc[1])
+                base_iters = bc[2]
+            else:
+                st = self.initial_state()
         mu = opt.mu_init
         tau = max(opt.tau_min, 1.0 - mu)
         filt = []
@@ -335,6 +384,7 @@ class IPM:
             accepted = False
             ftype = False
             n_ls = 0
+            n_soc = 0
             if tiny:
                 accepted, alpha = True, a_max
             else:
@@ -346,29 +396,67 @@ class IPM:
                         a_min = opt.gamma_alpha * min(opt.gamma_theta, opt.gamma_phi * theta / (-gphi))
                 else:
                     a_min = opt.gamma_alpha * opt.gamma_theta
-                while n_ls < opt.max_ls:
-                    n_ls += 1
-                    Zt = st.Z + alpha * dZ
-                    dt = st.d + alpha * dd
+                def acceptable(Zt, dt, a_sw):
+                    """filter + sufficient-decrease tests of a trial point; a_sw is the
+                    step size used in the switching condition and the Armijo rule."""
                     Ct = model.residuals(pr.P, pr.F, Zt, dt)
                     th_t = float(np.abs(Ct).sum())
                     ph_t = barrier_phi(pr, Zt, dt, mu)
                     ok = np.isfinite(th_t) and np.isfinite(ph_t) and th_t <= theta_max
+                    f_t = False
                     if ok:
                         for (tf, pf) in filt:
                             if th_t >= tf and ph_t >= pf:
                                 ok = False
                                 break
                     if ok:
-                        switching = gphi < 0 and alpha * (-gphi) ** opt.s_phi > opt.delta * theta ** opt.s_theta
+                        switching = gphi < 0 and a_sw * (-gphi) ** opt.s_phi > opt.delta * theta ** opt.s_theta
                         if theta <= theta_min and switching:
-                            ok = ph_t <= phi + opt.eta_phi * alpha * gphi
-                            ftype = ok
+                            ok = ph_t <= phi + opt.eta_phi * a_sw * gphi
+                            f_t = ok
                         else:
                             ok = th_t <= (1 - opt.gamma_theta) * theta or ph_t <= phi - opt.gamma_phi * theta
+                    return ok, f_t, th_t, Ct
+
+                while n_ls < opt.max_ls:
+                    n_ls += 1
+                    ok, ftype, th_t, Ct = acceptable(st.Z + alpha * dZ, st.d + alpha * dd, alpha)
                     if ok:
                         accepted = True
                         break
+                    if n_ls == 1 and opt.soc_max > 0 and not (th_t < theta):
+                        # second-order correction (Section 2.4)
+                        a0 = alpha
+                        csoc = a0 * C + Ct
+                        th_old = theta
+                        for p in range(opt.soc_max):
+                            sZ, sd, sl = fac.solve(-(gz + np.einsum("src,sr->sc", J, st.lam)),
+                                                   -(gd + float(np.sum(Jd * st.lam))), -csoc)
+                            a_soc = min(fraction_to_boundary(pr, st.Z, sZ, pr.hasL, pr.lo, pr.hasU, pr.hi, tau),
+                                        fraction_to_boundary(pr, np.array([st.d]), np.array([sd]),
+                                                             np.array([True]), np.array([pr.dlo]),
+                                                             np.array([True]), np.array([pr.dhi]), tau))
+                            ok, ftype, th_s, Cs = acceptable(st.Z + a_soc * sZ, st.d + a_soc * sd, a0)
+                            n_soc += 1
+                            if ok:
+                                dZ, dd, dlam, alpha = sZ, sd, sl, a_soc
+                                dzL, dzU, dzLd, dzUd = self.bound_dual_steps(st, mu, dZ, dd)
+                                a_z = min(fraction_to_boundary(pr, st.zL, dzL, pr.hasL, np.zeros_like(st.zL),
+                                                               np.zeros_like(pr.hasU), st.zL, tau),
+                                          fraction_to_boundary(pr, st.zU, dzU, pr.hasU, np.zeros_like(st.zU),
+                                                               np.zeros_like(pr.hasU), st.zU, tau),
+                                          fraction_to_boundary(pr, np.array([st.zLd, st.zUd]),
+                                                               np.array([dzLd, dzUd]), np.array([True, True]),
+                                                               np.zeros(2), np.array([False, False]), np.zeros(2),
+                                                               tau))
+                                accepted = True
+                                break
+                            if th_s > opt.kappa_soc * th_old:
+                                break
+                            th_old = th_s
+                            csoc = a_soc * csoc + Cs
+                        if accepted:
+                            break
                     alpha *= 0.5
                     if alpha < a_min:
                         break
@@ -378,10 +466,10 @@ class IPM:
             if not ftype and not tiny:
                 filt.append(((1 - opt.gamma_theta) * theta, phi - opt.gamma_phi * theta))
             hist.append(dict(iter=k, mu=mu, E0=E0, theta=theta, alpha=alpha, alpha_z=a_z,
-                             dw=dw, dc=dc, ls=n_ls, d=st.d))
+                             dw=dw, dc=dc, ls=n_ls, soc=n_soc, d=st.d))
             if opt.verbose:
                 print(f"{k:4d} E0={E0:.3e} th={theta:.3e} mu={mu:.2e} a={alpha:.3e} az={a_z:.3e} "
-                      f"dw={dw:.1e} ls={n_ls} d={st.d:.6f}")
+                      f"dw={dw:.1e} ls={n_ls} soc={n_soc} d={st.d:.6f}")
             # accept the step
             st.Z = st.Z + alpha * dZ
             st.d = st.d + alpha * dd
@@ -398,7 +486,10 @@ class IPM:
             sld, sud = st.d - pr.dlo, pr.dhi - st.d
             st.zLd = min(max(st.zLd, mu / (ks * sld)), ks * mu / sld)
             st.zUd = min(max(st.zUd, mu / (ks * sud)), ks * mu / sud)
-        return Result(status, k, st.d, st.Z, st.lam, st.zL, st.zU, st.zLd, st.zUd, E0, mu, hist)
+        # report the multipliers of the unscaled problem (min d): those of min w d over w
+        w = pr.w
+        return Result(status, k, st.d, st.Z, st.lam / w, st.zL / w, st.zU / w, st.zLd / w, st.zUd / w,
+                      E0, mu, hist, base_iters)
 
 
 def solve(P, F, opt=None, **kw):

@@ -12,7 +12,7 @@ def _iterate(S, seed, iters):
     F = ai.make_feeds(S, seed)
     solver = ipm.IPM(P, F, ipm.Options(max_iter=iters))
     r = solver.solve()
-    st = ipm.State(r.d, r.Z, r.lam, r.zL, r.zU, r.zLd, r.zUd)
+    st = solver.state_from_result(r)
     C, J, Jd, W, Wdd = solver.evaluate(st)
     sig, sigd = solver.sigma(st)
     return solver, st, C, J, Jd, W, Wdd, sig, sigd
