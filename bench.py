@@ -113,7 +113,7 @@ sys.path.insert(0, {ROOT!r})
 import absorber_inputs as ai
 from oracle import ipm
 F = ai.workload_feeds({workload!r})[:, :{sample_scen}]
-opt = ipm.Options(max_iter={iters})
+opt = ipm.Options(max_iter={iters}, init="inlet")
 t = time.perf_counter()
 r = ipm.solve(ai.PARAMS, F, opt)
 el = time.perf_counter() - t

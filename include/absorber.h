@@ -231,6 +231,10 @@ typedef struct abs_options {
     int32_t max_ls;        /* maximum line-search trials per iteration */
     int32_t verbose;       /* 1: print one line per iteration to stdout */
     int32_t profile;       /* 1: time the hot kernels with CUDA events (abs_result.kernel_*) */
+    int32_t init;          /* 0: expected-value start (S > 1, see ipm_solve), 1: inlet copy */
+    int32_t soc_max;       /* second-order corrections per iteration (0 disables) */
+    double kappa_soc;      /* required theta reduction between corrections */
+    double obj_scaling;    /* the solver minimises obj_scaling * d; <= 0 means S */
 } abs_options;
 
 void abs_default_options(abs_options* o);
@@ -252,6 +256,10 @@ typedef struct abs_result {
     double kernel_ms[ABS_N_KERNELS];        /* with options.profile: summed kernel time */
     int32_t kernel_launches[ABS_N_KERNELS]; /* ... and launch counts */
     int64_t launches;            /* every kernel this library launched during the solve */
+    int32_t base_iters;          /* iterations of the expected-value start solve */
+    int32_t soc_steps;           /* second-order correction steps taken */
+    int32_t fp64_fallbacks;      /* FP32 iterations refactored in FP64 (refinement stalled) */
+    double base_ms;              /* host time of the expected-value start solve */
 } abs_result;
 
 /* Diagnostic: measured throughput of dependent-free fused multiply-adds on the current
@@ -260,11 +268,16 @@ abs_status abs_measure_fma_peak(int kind, double* gflops);
 
 /* Interior-point solve of problem (10) on the device (the paper's GPU-resident
  * solution, Section "GPU-resident solution with MadNLP.jl"): filter line-search
- * primal-dual method after Wachter & Biegler (2006), with the eval kernel, the
- * block-LU + Schur KKT factorization and solve, and every vector update running in this
- * library's kernels; the host only sequences launches and reads a few scalars per
- * iteration.  Starts from the documented default point (every stage copies the inlet
- * streams, d = (d_lo + d_hi)/2) unless warm_x is given.
+ * primal-dual method after Wachter & Biegler (2006) with second-order corrections and
+ * the objective scaled by S, with the eval kernel, the block-LU + Schur KKT
+ * factorization and solve, and every vector update running in this library's kernels;
+ * the host only sequences launches and reads a few scalars per iteration.
+ * Starting point (unless warm_x is given): for S > 1 and init = 0 the stage states of
+ * the expected-value problem -- one scenario whose feed is the mean of the S feeds,
+ * solved first by this same method from the inlet-copy start -- copied to every
+ * scenario, d = (d_lo + d_hi)/2 and each hydraulic slack from its row; otherwise every
+ * stage copies the inlet streams.  The returned multipliers (y_out) are those of the
+ * unscaled problem min d.
  *   opt     host (NULL = defaults).
  *   warm_x  device primal vector or NULL; warm_y device row vector or NULL.
  *   res     host, required.

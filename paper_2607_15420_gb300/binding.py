@@ -67,7 +67,9 @@ class AbsOptions(C.Structure):
                 ("gamma_alpha", C.c_double), ("lam_init_max", C.c_double),
                 ("dw0", C.c_double), ("dw_min", C.c_double), ("dw_max", C.c_double),
                 ("kw_minus", C.c_double), ("kw_plus", C.c_double), ("kw_plus_bar", C.c_double),
-                ("max_ls", C.c_int32), ("verbose", C.c_int32), ("profile", C.c_int32)]
+                ("max_ls", C.c_int32), ("verbose", C.c_int32), ("profile", C.c_int32),
+                ("init", C.c_int32), ("soc_max", C.c_int32), ("kappa_soc", C.c_double),
+                ("obj_scaling", C.c_double)]
 
 
 class AbsResult(C.Structure):
@@ -76,7 +78,9 @@ class AbsResult(C.Structure):
                 ("d", C.c_double), ("obj", C.c_double), ("E0", C.c_double), ("mu", C.c_double),
                 ("inf_pr", C.c_double), ("inf_du", C.c_double), ("solve_ms", C.c_double),
                 ("phase_ms", C.c_double * 6), ("kernel_ms", C.c_double * 5),
-                ("kernel_launches", C.c_int32 * 5), ("launches", C.c_int64)]
+                ("kernel_launches", C.c_int32 * 5), ("launches", C.c_int64),
+                ("base_iters", C.c_int32), ("soc_steps", C.c_int32), ("fp64_fallbacks", C.c_int32),
+                ("base_ms", C.c_double)]
 
 KERNELS = ("eval", "eval_trial", "factor", "solve", "solve_t")
 PHASES = ("eval", "factor", "solve", "linesearch", "step", "other")

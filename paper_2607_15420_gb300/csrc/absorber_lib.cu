@@ -259,25 +259,30 @@ __global__ void __launch_bounds__(128) accept_kernel(const Params P, int S, int6
 
 // default starting point (every stage copies the inlet streams, T the mean inlet
 // temperature, eps = 0, the slack from the hydraulic row at d), pushed into the bounds
+// (base != null: stage states from the expected-value solution, entry v at base[v * ldb])
 __global__ void __launch_bounds__(128) init_kernel(const Params P, int S, int64_t ld, const double* __restrict__ feed,
-                                                   double d, double push, double frac, double* __restrict__ x,
-                                                   double* __restrict__ zL, double* __restrict__ zU,
-                                                   double* __restrict__ lam) {
+                                                   const double* __restrict__ base, int64_t ldb, double d, double push,
+                                                   double frac, double* __restrict__ x, double* __restrict__ zL,
+                                                   double* __restrict__ zU, double* __restrict__ lam) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
     if (s >= S) return;
     double q[NV];
+    if (base) {
 #pragma unroll
-    for (int l = 0; l < 9; ++l) q[LX + l] = feed[(int64_t)(F_XIN + l) * ld + s] / P.sx[l];
+        for (int j = 0; j < NV; ++j) q[j] = base[(int64_t)(NV * n + j) * ldb];
+    } else {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) q[LY + j] = feed[(int64_t)(F_Y0 + j) * ld + s] / P.sy[j];
-    q[LL] = feed[(int64_t)F_LIN * ld + s];
-    q[LV] = feed[(int64_t)F_V0 * ld + s];
-    const double T = 0.5 * (feed[(int64_t)F_T0 * ld + s] + feed[(int64_t)F_TIN * ld + s]);
-    q[LT] = T / P.sT;
+        for (int l = 0; l < 9; ++l) q[LX + l] = feed[(int64_t)(F_XIN + l) * ld + s] / P.sx[l];
 #pragma unroll
-    for (int r = 0; r < 5; ++r) q[LE + r] = 0.0;
-    q[LS] = P.u_max * M_PI * d * d * 0.25 - q[LV] * P.R * T / feed[(int64_t)F_P * ld + s];
+        for (int j = 0; j < 4; ++j) q[LY + j] = feed[(int64_t)(F_Y0 + j) * ld + s] / P.sy[j];
+        q[LL] = feed[(int64_t)F_LIN * ld + s];
+        q[LV] = feed[(int64_t)F_V0 * ld + s];
+        q[LT] = 0.5 * (feed[(int64_t)F_T0 * ld + s] + feed[(int64_t)F_TIN * ld + s]) / P.sT;
+#pragma unroll
+        for (int r = 0; r < 5; ++r) q[LE + r] = 0.0;
+    }
+    q[LS] = P.u_max * M_PI * d * d * 0.25 - q[LV] * P.R * (P.sT * q[LT]) / feed[(int64_t)F_P * ld + s];
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const int64_t o = (int64_t)(NV * n + j) * ld + s;
@@ -309,6 +314,39 @@ __global__ void ls_rhs_kernel(int S, int64_t ld, const double* __restrict__ zL, 
         const int64_t o = (int64_t)(NV * n + j) * ld + s;
         rz[o] = zL[o] - zU[o];
         one[o] = 1.0;
+    }
+}
+
+// primal fraction-to-the-boundary limit of a direction: partial [0] = min ratio
+__global__ void __launch_bounds__(128) ftb_kernel(const Params P, int S, int64_t ld, double tau,
+                                                  const double* __restrict__ x, const double* __restrict__ dz,
+                                                  double* part) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    double v[1] = {1.0};
+    if (s < S) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            const int64_t o = (int64_t)(NV * n + j) * ld + s;
+            const double xv = x[o], d = dz[o];
+            if (has_lo(j) && d < 0.0) v[0] = fmin(v[0], -tau * (xv - lo_of(P, j)) / d);
+            if (has_hi(j) && d > 0.0) v[0] = fmin(v[0], tau * (hi_of(P, j) - xv) / d);
+            if (d != d) v[0] = NAN;
+        }
+    }
+    const int ops[1] = {RMIN};
+    block_reduce_store<1>(v, ops, part, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// y = a * x + b * y on the per-scenario part of row/primal vectors
+__global__ void axpby_kernel(int S, int64_t ld, double a, const double* xv, double b, double* y) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (s >= S) return;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        y[o] = a * xv[o] + b * y[o];
     }
 }
 
@@ -573,8 +611,10 @@ struct abs_problem {
     double* hes = nullptr;           // nnzH * ld
     double* vec = nullptr;           // pool of primal-size vectors
     int nvec = 0;
-    void* LU = nullptr;
+    void* LU = nullptr;              // factors of the current precision (points at one of below)
     void* G = nullptr;
+    void* LUp[2] = {nullptr, nullptr};   // [ABS_PREC_FP64], [ABS_PREC_FP32]
+    void* Gp[2] = {nullptr, nullptr};
     unsigned char* piv = nullptr;
     int* sing = nullptr;
     int* count = nullptr;
@@ -601,6 +641,9 @@ struct abs_problem {
         size_t used = 0;
     } prof;
     int64_t nlaunch = 0;   // kernels launched (every launch is followed by launch_check)
+    abs_params aparams;              // the caller's table (for the expected-value sub-problem)
+    std::vector<double> hfeed;       // host copy of the feeds [18][S]
+    abs_problem* base = nullptr;     // one-scenario sub-problem for the expected-value start
 };
 
 namespace {
@@ -608,7 +651,7 @@ namespace {
 // vector pool indices (each NSC * ld + ld doubles, the d slot at NSC * ld)
 enum {
     V_X, V_LAM, V_ZL, V_ZU, V_C, V_JTL, V_SIG, V_RZ, V_RC, V_P, V_Q, V_DZ, V_DL, V_DZL, V_DZU,
-    V_G, V_RHOZ, V_RHOC, V_P2, V_CZ, V_CL, V_ONE, V_COUNT
+    V_G, V_RHOZ, V_RHOC, V_P2, V_CZ, V_CL, V_ONE, V_CT, V_RCS, V_SZ, V_SL, V_COUNT
 };
 
 abs_status fail(abs_problem* h, abs_status st, const std::string& msg) {
@@ -649,13 +692,13 @@ abs_status ensure_buffers(abs_problem* h) {
 }
 
 abs_status ensure_factor(abs_problem* h, int prec) {
-    if (h->fac_prec == prec) return ABS_OK;
-    if (h->LU) cudaFree(h->LU);
-    if (h->G) cudaFree(h->G);
-    h->LU = h->G = nullptr;
-    const size_t es = prec == ABS_PREC_FP32 ? sizeof(float) : sizeof(double);
-    CK(cudaMalloc(&h->LU, es * (size_t)N_STAGES * NV * NV * h->ld));
-    CK(cudaMalloc(&h->G, es * (size_t)N_STAGES * NV * NABV * h->ld));
+    if (!h->LUp[prec]) {
+        const size_t es = prec == ABS_PREC_FP32 ? sizeof(float) : sizeof(double);
+        CK(cudaMalloc(&h->LUp[prec], es * (size_t)N_STAGES * NV * NV * h->ld));
+        CK(cudaMalloc(&h->Gp[prec], es * (size_t)N_STAGES * NV * NABV * h->ld));
+    }
+    h->LU = h->LUp[prec];
+    h->G = h->Gp[prec];
     h->fac_prec = prec;
     return ABS_OK;
 }
@@ -773,7 +816,10 @@ abs_status kkt_factor_core(abs_problem* h, KKTSys& K, const double* xd, int64_t*
     abs_status r;
     if ((r = ensure_factor(h, K.prec)) != ABS_OK) return r;
     CK(cudaMemsetAsync(h->count, 0, sizeof(int), st));
-    const double pivtol = K.prec == ABS_PREC_FP32 ? 1e-6 : 1e-14;
+    // FP64: a pivot below 1e-14 of the block's largest entry marks the stage block
+    // singular; FP32: only (numerically) zero pivots do -- accuracy is guarded by the FP64
+    // refinement instead, with an FP64 refactorization when it stalls
+    const double pivtol = K.prec == ABS_PREC_FP32 ? 1e-30 : 1e-14;
     if (K.prec == ABS_PREC_FP32) r = factor_launch<float>(h, K.jac, pivtol, st);
     else r = factor_launch<double>(h, K.jac, pivtol, st);
     if (r != ABS_OK) return r;
@@ -883,9 +929,13 @@ abs_status upload_feeds(abs_problem* h, const double* feeds, cudaStream_t st) {
     if (on_dev) {
         // device source: pad on the device (values are the caller's responsibility)
         const int64_t n = (int64_t)NFEED * ld;
+        h->hfeed.resize((size_t)NFEED * S);
+        CK(cudaMemcpyAsync(h->hfeed.data(), feeds, sizeof(double) * h->hfeed.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
         pad_feed_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((int)S, ld, feeds, h->feed);
         return launch_check(h);
     }
+    h->hfeed.assign(feeds, feeds + (size_t)NFEED * S);
     std::vector<double> hf((size_t)NFEED * ld, 0.0);
     for (int f = 0; f < NFEED; ++f)
         for (int64_t s = 0; s < ld; ++s) {
@@ -940,6 +990,11 @@ void abs_default_options(abs_options* o) {
     o->kw_plus_bar = 100.0;
     o->max_ls = 60;
     o->verbose = 0;
+    o->profile = 0;
+    o->init = 0;
+    o->soc_max = 4;
+    o->kappa_soc = 0.99;
+    o->obj_scaling = 0.0;
 }
 
 abs_status absorber_create(const abs_params* p, const double* feeds, const double* prob, int64_t S,
@@ -957,6 +1012,7 @@ abs_status absorber_create(const abs_params* p, const double* feeds, const doubl
     h->S = S;
     h->ld = (S + 31) / 32 * 32;
     std::memcpy(&h->P, p, sizeof(abs_params));
+    h->aparams = *p;
     for (int l = 0; l < 9; ++l) {
         if (!(p->sx[l] > 0.0)) {
             delete h;
@@ -1003,12 +1059,16 @@ abs_status absorber_set_feeds(abs_problem* h, const double* feeds, abs_stream_t 
 
 void absorber_destroy(abs_problem* h) {
     if (!h) return;
+    absorber_destroy(h->base);
+    for (auto e : h->prof.pool) cudaEventDestroy(e);
     cudaFree(h->feed);
     cudaFree(h->jac);
     cudaFree(h->hes);
     cudaFree(h->vec);
-    cudaFree(h->LU);
-    cudaFree(h->G);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(h->LUp[k]);
+        cudaFree(h->Gp[k]);
+    }
     cudaFree(h->piv);
     cudaFree(h->sing);
     cudaFree(h->count);

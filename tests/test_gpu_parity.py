@@ -145,7 +145,10 @@ def test_newton_direction_parity(B, prec):
     assert inert.n_singular == 0
     o_in = fac.inertia()
     assert (inert.n_pos, inert.n_neg, inert.n_zero) == o_in
-    assert abs(inert.schur_d - fac.Sd) <= 1e-9 * abs(fac.Sd)
+    # FP64: the Schur scalar to 1e-9; FP32: q = J^-1 b comes from FP32 factors (a few
+    # ulps of float times the block condition number ~1e5); the refined direction below
+    # must still meet 1e-10
+    assert abs(inert.schur_d - fac.Sd) <= (1e-9 if prec == 0 else 1e-2) * abs(fac.Sd)
     rx = dev(prob.to_soa(rz, rd))
     rcd = dev(prob.to_soa(rc))
     sx = torch.zeros_like(rx)
