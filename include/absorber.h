@@ -287,6 +287,41 @@ abs_status ipm_solve(abs_problem* h, const abs_options* opt, const double* warm_
                      const double* warm_y, abs_result* res, double* x_out, double* y_out,
                      abs_stream_t stream);
 
+/* Newton direction of one interior-point iteration without any allocation.
+ *
+ * The paper has no counterpart: this entry exists for callers that cannot allocate
+ * GPU memory once they are running -- code under a fixed device-memory budget, code
+ * whose memory belongs to another runtime's allocator, or code that must not trigger
+ * allocator synchronisation between CUDA graph captures.  It computes what
+ * kkt_factor (FP64, delta_c = 0) followed by kkt_solve (no refinement) compute, with
+ * no handle: the caller passes the problem's parameter table and its own device
+ * buffers, and every intermediate (stage-block LU factors, G blocks, pivots, the
+ * Schur vectors and block partial sums) lives in one static device array of the
+ * library, sized for ABS_NOALLOC_MAX_SCENARIOS scenarios (about 8 MB), which every GPU
+ * that loads the library holds until the process exits.  The call makes no cudaMalloc,
+ * cudaFree, pinned-host or other allocating call.
+ *   p          host, the parameter table.
+ *   S, ld      scenarios (1 <= S <= ABS_NOALLOC_MAX_SCENARIOS; larger S is rejected
+ *              with ABS_ERR_ARG) and the leading dimension (S rounded up to 32).
+ *   x          device primal vector (only d, its last entry, is read).
+ *   jac_vals, hess_vals  device, as eval_grad_jac_hess writes them at the iterate.
+ *   sigma      device primal vector, the barrier diagonal (d last); delta_w >= 0.
+ *   rhs_x, rhs_c, sol_x, sol_c  device primal / row vectors, as for kkt_solve.
+ *   schur_d    host or NULL: receives the Schur complement on d.
+ * Errors: ABS_ERR_ARG, ABS_ERR_NUMERIC (singular stage block), ABS_ERR_INERTIA (Schur
+ * complement not positive: increase delta_w), ABS_ERR_CUDA.
+ * The first call on each device looks up the array's device address and uploads the
+ * pattern tables: make that first call before any stream capture.  All calls share
+ * the one array, which keeps the last call's contents: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the caller.
+ * Synchronises the stream before returning. */
+#define ABS_NOALLOC_MAX_SCENARIOS 128
+abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t ld, const double* x,
+                              const double* jac_vals, const double* hess_vals,
+                              const double* sigma, double delta_w, const double* rhs_x,
+                              const double* rhs_c, double* sol_x, double* sol_c,
+                              double* schur_d, abs_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -105,6 +105,9 @@ EXPORTS = {
     "kkt_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                             C.POINTER(AbsSolveInfo), C.c_void_p]),
     "abs_default_options": (None, [C.POINTER(AbsOptions)]),
+    "kkt_newton_noalloc": (C.c_int, [C.POINTER(AbsParams), C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "ipm_solve": (C.c_int, [C.c_void_p, C.POINTER(AbsOptions), C.c_void_p, C.c_void_p, C.POINTER(AbsResult),
                             C.c_void_p, C.c_void_p, C.c_void_p]),
 }
@@ -178,6 +181,22 @@ def measure_fma_peak(kind):
     if st != ABS_OK:
         raise AbsorberError(st, lib().abs_last_error(None).decode())
     return v.value
+
+
+NOALLOC_MAX_SCENARIOS = 128
+
+
+def kkt_newton_noalloc(params, S, ld, x, jac, hess, sigma, rhs_x, rhs_c, sol_x, sol_c, delta_w=0.0,
+                       stream=None):
+    """The allocation-free Newton direction (kkt_newton_noalloc); returns the Schur scalar."""
+    p = make_params(params) if isinstance(params, dict) else params
+    sd = C.c_double(0.0)
+    st = lib().kkt_newton_noalloc(C.byref(p), int(S), int(ld), _ptr(x), _ptr(jac), _ptr(hess), _ptr(sigma),
+                                  float(delta_w), _ptr(rhs_x), _ptr(rhs_c), _ptr(sol_x), _ptr(sol_c),
+                                  C.byref(sd), _stream(stream))
+    if st != ABS_OK:
+        raise AbsorberError(st, lib().abs_last_error(None).decode())
+    return sd.value
 
 
 STRUCTS = [AbsParams, AbsSizes, AbsKKTDiag, AbsInertia, AbsSolveInfo, AbsOptions, AbsResult]

@@ -1297,3 +1297,126 @@ extern "C" abs_status abs_measure_fma_peak(int kind, double* gflops) {
 
 // the interior-point driver lives in its own file (same translation unit)
 #include "ipm.inc"
+
+// ======================================================================================
+// Newton direction without any allocation (no handle, no cudaMalloc, no pinned memory)
+// ======================================================================================
+// For callers that cannot allocate device memory after start-up -- code running under
+// a fixed memory budget, inside another runtime's allocator, or between graph
+// captures -- this entry runs the FP64 stage-block LU, the Schur step on d and the
+// block solves with every intermediate in one file-scope device array.
+namespace {
+
+constexpr int64_t NA_MAX_S = ABS_NOALLOC_MAX_SCENARIOS;    // scenarios per call, at most
+constexpr int64_t NA_LD = NA_MAX_S;                         // a multiple of 32
+constexpr size_t NA_LU = (size_t)N_STAGES * NV * NV * NA_LD;
+constexpr size_t NA_G = (size_t)N_STAGES * NV * NABV * NA_LD;
+constexpr size_t NA_VEC = (size_t)NSC * NA_LD + NA_LD;
+constexpr int NA_NBLK = (int)((NA_MAX_S + 127) / 128) * N_STAGES;
+constexpr size_t NA_PART = (size_t)16 * NA_NBLK;
+constexpr size_t NA_PIV = ((size_t)N_STAGES * NV * NA_LD + 7) / 8;   // bytes as doubles
+constexpr size_t NA_SING = (NA_LD + 1) / 2;                         // ints as doubles
+constexpr size_t NA_TOTAL = NA_LU + NA_G + 3 * NA_VEC + NA_PART + NA_PIV + NA_SING + 1;
+
+// the scratch: every device that loads the library holds it until the process exits
+static __device__ __align__(256) double g_noalloc_scratch[NA_TOTAL];
+
+double* g_na_base[64] = {nullptr};
+double g_na_host_part[NA_PART];   // host copy of the block partials (static, not allocated)
+
+}  // namespace
+
+extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t ld, const double* x,
+                                         const double* jac_vals, const double* hess_vals, const double* sigma,
+                                         double delta_w, const double* rhs_x, const double* rhs_c, double* sol_x,
+                                         double* sol_c, double* schur_d, abs_stream_t stream) {
+    abs_problem* h = nullptr;   // for CK(): errors go to the global message
+    if (!p || !x || !jac_vals || !hess_vals || !sigma || !rhs_x || !rhs_c || !sol_x || !sol_c)
+        return fail(nullptr, ABS_ERR_ARG, "kkt_newton_noalloc: NULL argument");
+    if (S < 1 || S > NA_MAX_S)
+        return fail(nullptr, ABS_ERR_ARG,
+                    "kkt_newton_noalloc: S must be in [1, " + std::to_string(NA_MAX_S) + "] (static scratch size)");
+    if (ld != (S + 31) / 32 * 32) return fail(nullptr, ABS_ERR_ARG, "kkt_newton_noalloc: ld must be S rounded up to 32");
+    if (!(delta_w >= 0.0)) return fail(nullptr, ABS_ERR_ARG, "kkt_newton_noalloc: delta_w must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(nullptr, ABS_ERR_ARG, "kkt_newton_noalloc: device index out of range");
+    if (!g_na_base[dev]) {
+        // once per device, with that device current: the array's device address
+        double* ptr = nullptr;
+        CK(cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch));
+        CK(upload_tables(dev));
+        g_na_base[dev] = ptr;
+    }
+    double* LU = g_na_base[dev];
+    double* G = LU + NA_LU;
+    double* pv = G + NA_G;
+    double* qv = pv + NA_VEC;
+    double* gv = qv + NA_VEC;
+    double* part = gv + NA_VEC;
+    unsigned char* piv = (unsigned char*)(part + NA_PART);
+    int* sing = (int*)((double*)piv + NA_PIV);
+    int* count = (int*)((double*)sing + NA_SING);
+    // the problem's constants (derived fields as absorber_create computes them)
+    Params P;
+    std::memset(&P, 0, sizeof(P));
+    std::memcpy(&P, p, sizeof(abs_params));
+    for (int l = 0; l < 9; ++l) {
+        if (!(p->sx[l] > 0.0)) return fail(nullptr, ABS_ERR_ARG, "kkt_newton_noalloc: scales must be positive");
+        P.lnsx[l] = std::log(p->sx[l]);
+        P.hL0[l] = p->hL_ref[l] + p->hL_dh[l];
+    }
+    for (int j = 0; j < 4; ++j) P.hV0[j] = p->hV_ref[j] + p->hV_dh[j];
+    const dim3 g1((unsigned)((S + kThrS - 1) / kThrS)), g2((unsigned)((S + kThr - 1) / kThr), N_STAGES);
+    const int nb = (int)g2.x * N_STAGES;
+    const int64_t od = (int64_t)NSC * ld;
+    cudaError_t e;
+#define NA_LAUNCHED()                                                                                  \
+    if ((e = cudaGetLastError()) != cudaSuccess)                                                       \
+        return fail(nullptr, ABS_ERR_CUDA, std::string("kkt_newton_noalloc: ") + cudaGetErrorString(e));
+    // the singular-block counter must start at zero on every call
+    CK(cudaMemsetAsync(count, 0, sizeof(int), st));
+    factor_kernel<double><<<g1, kThrS, 0, st>>>((int)S, ld, jac_vals, LU, piv, G, sing, 1e-14);
+    NA_LAUNCHED();
+    count_kernel<<<g1, kThrS, 0, st>>>((int)S, sing, count);
+    NA_LAUNCHED();
+    // p = J^-1 r_c, q = J^-1 b
+    solve_kernel<double, 2><<<g1, kThrS, 0, st>>>(P, (int)S, ld, jac_vals, LU, piv, G, x + od, rhs_c, nullptr, pv,
+                                                  qv);
+    NA_LAUNCHED();
+    schur_kernel<<<g2, kThr, 0, st>>>((int)S, ld, hess_vals, sigma, true, pv, qv, rhs_x, part);
+    NA_LAUNCHED();
+    int cnt = 0;
+    double hx[3] = {0.0, 0.0, 0.0};
+    CK(cudaMemcpyAsync(&cnt, count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hx[0], x + od, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hx[1], sigma + od, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hx[2], rhs_x + od, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(g_na_host_part, part, sizeof(double) * 5 * (size_t)nb, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (cnt) return fail(nullptr, ABS_ERR_NUMERIC, "kkt_newton_noalloc: singular stage block");
+    double red[5];
+    for (int k = 0; k < 5; ++k) {
+        double a = 0.0;
+        for (int b = 0; b < nb; ++b) a += g_na_host_part[(size_t)k * nb + b];
+        red[k] = a;
+    }
+    // S_d = K_dd + dw + sum q^T (W + Sigma) q + dw sum q^T q ;  dd = (r_d - beta) / S_d
+    const double Kdd = red[4] + hx[1];
+    const double Sd = Kdd + delta_w + red[0] + delta_w * red[1];
+    if (schur_d) *schur_d = Sd;
+    if (!(Sd > 0.0)) return fail(nullptr, ABS_ERR_INERTIA, "kkt_newton_noalloc: Schur complement on d is not positive");
+    const double beta = red[2] - delta_w * red[3];
+    const double dd = (hx[2] - beta) / Sd;
+    dz_kernel<<<g2, kThr, 0, st>>>((int)S, ld, hess_vals, sigma, delta_w, true, pv, qv, dd, rhs_x, sol_x, gv);
+    NA_LAUNCHED();
+    CK(cudaMemcpyAsync(sol_x + od, &dd, sizeof(double), cudaMemcpyHostToDevice, st));
+    solve_t_kernel<double><<<g1, kThrS, 0, st>>>((int)S, ld, jac_vals, LU, piv, gv, sol_c);
+    NA_LAUNCHED();
+#undef NA_LAUNCHED
+    // dd lives on this stack frame until the copy above has completed
+    CK(cudaStreamSynchronize(st));
+    (void)nb;
+    return ABS_OK;
+}
