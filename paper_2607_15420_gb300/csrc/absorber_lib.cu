@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -13,6 +14,7 @@
 
 #include "absorber.h"
 #include "kernels.cuh"
+#include "kernels_warp.cuh"
 
 using namespace absorber;
 
@@ -124,15 +126,16 @@ __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const dou
     block_reduce_store<5>(v, ops, part, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
-// dz = p - q dd ;  g = r - (W + Sigma + dw I) dz
+// dz = p - q dd ;  g = r - (W + Sigma + dw I) dz ;  dd is read from ddp (the d slot of dz)
 __global__ void __launch_bounds__(128) dz_kernel(int S, int64_t ld, const double* __restrict__ hes,
                                                  const double* __restrict__ sig, double dw, bool use_w,
                                                  const double* __restrict__ p, const double* __restrict__ q,
-                                                 double dd, const double* __restrict__ r, double* __restrict__ dz,
+                                                 const double* ddp, const double* __restrict__ r, double* dz,
                                                  double* __restrict__ g) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
     if (s >= S) return;
+    const double dd = *ddp;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const int64_t o = (int64_t)(NV * n + j) * ld + s;
@@ -153,7 +156,7 @@ __global__ void __launch_bounds__(128) dz_kernel(int S, int64_t ld, const double
 __global__ void __launch_bounds__(128) kkt_residual_kernel(int S, int64_t ld, const double* __restrict__ jac,
                                                            const double* __restrict__ hes, const double* __restrict__ sig,
                                                            double dw, bool use_w, const double* __restrict__ dz,
-                                                           double dd, const double* __restrict__ dl,
+                                                           const double* __restrict__ ddp, const double* __restrict__ dl,
                                                            const double* __restrict__ rz, const double* __restrict__ rc,
                                                            double* __restrict__ rhoz, double* __restrict__ rhoc,
                                                            double* part) {
@@ -161,6 +164,7 @@ __global__ void __launch_bounds__(128) kkt_residual_kernel(int S, int64_t ld, co
     const int n = blockIdx.y;
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (s < S) {
+        const double dd = *ddp;
         double h[NV], jt[NV], jv[NR];
         hv_stage(ld, hes, sig, dw, use_w, dz, s, n, h);
         jt_stage(ld, jac, dl, s, n, jt);
@@ -230,7 +234,7 @@ __global__ void __launch_bounds__(128) step_kernel(const Params P, int S, int64_
 
 // accept the step and apply the kappa_Sigma safeguard to the bound multipliers
 __global__ void __launch_bounds__(128) accept_kernel(const Params P, int S, int64_t ld, double alpha, double alpha_z,
-                                                     double mu, double ksig, double* __restrict__ x,
+                                                     double mu, double ksig, double d_new, double* __restrict__ x,
                                                      const double* __restrict__ dz, double* __restrict__ lam,
                                                      const double* __restrict__ dl, double* __restrict__ zL,
                                                      const double* __restrict__ dzL, double* __restrict__ zU,
@@ -238,6 +242,7 @@ __global__ void __launch_bounds__(128) accept_kernel(const Params P, int S, int6
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
     if (s >= S) return;
+    if (s == 0 && n == 0) x[(int64_t)NSC * ld] = d_new;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const int64_t o = (int64_t)(NV * n + j) * ld + s;
@@ -283,6 +288,7 @@ __global__ void __launch_bounds__(128) init_kernel(const Params P, int S, int64_
         for (int r = 0; r < 5; ++r) q[LE + r] = 0.0;
     }
     q[LS] = P.u_max * M_PI * d * d * 0.25 - q[LV] * P.R * (P.sT * q[LT]) / feed[(int64_t)F_P * ld + s];
+    if (s == 0 && n == 0) x[(int64_t)NSC * ld] = d;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const int64_t o = (int64_t)(NV * n + j) * ld + s;
@@ -350,6 +356,41 @@ __global__ void axpby_kernel(int S, int64_t ld, double a, const double* xv, doub
     }
 }
 
+// dd = (rd - (sum_b part[2][b] - dw sum_b part[3][b])) / Sd  (one block, fixed-order tree)
+__global__ void __launch_bounds__(256) finalize_dd_kernel(const double* __restrict__ part, int nb, double rd, double dw,
+                                                          double Sd, double* out) {
+    __shared__ double s2[256], s3[256];
+    double a2 = 0.0, a3 = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        a2 += part[2 * (int64_t)nb + b];
+        a3 += part[3 * (int64_t)nb + b];
+    }
+    s2[threadIdx.x] = a2;
+    s3[threadIdx.x] = a3;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s2[threadIdx.x] += s2[threadIdx.x + o];
+            s3[threadIdx.x] += s3[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = (rd - (s2[0] - dw * s3[0])) / Sd;
+}
+
+// y += x on the per-scenario part and on the d slot of primal vectors (d_slot true)
+__global__ void axpy_d_kernel(int S, int64_t ld, const double* __restrict__ xv, double* __restrict__ y, bool d_slot) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (s >= S) return;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        y[o] += xv[o];
+    }
+    if (d_slot && s == 0 && n == 0) y[(int64_t)NSC * ld] += xv[(int64_t)NSC * ld];
+}
+
 __global__ void max_abs_kernel(int S, int64_t ld, const double* __restrict__ v, double* part) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
@@ -376,10 +417,6 @@ __global__ void axpy_kernel(int S, int64_t ld, double a, const double* __restric
     }
 }
 
-__global__ void count_kernel(int S, const int* __restrict__ flag, int* out) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < S && flag[s]) atomicAdd(out, 1);
-}
 
 }  // namespace absorber
 
@@ -671,7 +708,6 @@ abs_status fail(abs_problem* h, abs_status st, const std::string& msg) {
 int64_t vsize(const abs_problem* h) { return (int64_t)NSC * h->ld + h->ld; }
 double* V(abs_problem* h, int k) { return h->vec + (int64_t)k * vsize(h); }
 dim3 grid2(const abs_problem* h) { return dim3((unsigned)((h->S + kThr - 1) / kThr), N_STAGES); }
-dim3 grid1(const abs_problem* h) { return dim3((unsigned)((h->S + kThrS - 1) / kThrS)); }
 
 abs_status ensure_buffers(abs_problem* h) {
     if (h->vec) return ABS_OK;
@@ -685,7 +721,7 @@ abs_status ensure_buffers(abs_problem* h) {
     CK(cudaMalloc(&h->sing, sizeof(int) * (size_t)ld));
     CK(cudaMalloc(&h->count, sizeof(int)));
     h->nblk2 = (int)(((h->S + kThr - 1) / kThr) * N_STAGES);
-    const size_t np = (size_t)16 * h->nblk2;
+    const size_t np = (size_t)16 * h->nblk2 + 64;
     CK(cudaMalloc(&h->part, sizeof(double) * np));
     CK(cudaMallocHost(&h->hpart, sizeof(double) * np));
     return ABS_OK;
@@ -703,11 +739,21 @@ abs_status ensure_factor(abs_problem* h, int prec) {
     return ABS_OK;
 }
 
-// reduce K partial arrays written by a (scenario, stage) launch, in fixed order on the host
-abs_status fetch_partials(abs_problem* h, cudaStream_t st, int K, const int* ops, double* out) {
+// reduce K partial arrays written by a (scenario, stage) launch, in fixed order on the
+// host; the device scalars in `extra` (doubles) and `icount` (an int) are fetched in the
+// same round trip through the pinned tail of hpart
+abs_status fetch_partials(abs_problem* h, cudaStream_t st, int K, const int* ops, double* out,
+                          std::initializer_list<const double*> extra = {}, double* extra_out = nullptr,
+                          const int* icount = nullptr, int* icount_out = nullptr) {
     const int nb = h->nblk2;
-    CK(cudaMemcpyAsync(h->hpart, h->part, sizeof(double) * (size_t)K * nb, cudaMemcpyDeviceToHost, st));
+    double* tail = h->hpart + (size_t)16 * nb;
+    if (K > 0) CK(cudaMemcpyAsync(h->hpart, h->part, sizeof(double) * (size_t)K * nb, cudaMemcpyDeviceToHost, st));
+    int i = 0;
+    for (const double* e : extra) CK(cudaMemcpyAsync(tail + i++, e, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (icount) CK(cudaMemcpyAsync((int*)(tail + 60), icount, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    for (int k = 0; k < i; ++k) extra_out[k] = tail[k];
+    if (icount) *icount_out = *(int*)(tail + 60);
     for (int k = 0; k < K; ++k) {
         double a = ops[k] == RSUM ? 0.0 : (ops[k] == RMAX ? -INFINITY : INFINITY);
         const double* p = h->hpart + (size_t)k * nb;
@@ -767,10 +813,13 @@ struct KKTSys {
     int prec;
 };
 
+dim3 gridw(const abs_problem* h, int wpb) { return dim3((unsigned)((h->S + wpb - 1) / wpb)); }
+
 template <class T>
 abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaStream_t st) {
     prof_begin(h, K_FACTOR, st);
-    factor_kernel<T><<<grid1(h), kThrS, 0, st>>>((int)h->S, h->ld, jac, (T*)h->LU, h->piv, (T*)h->G, h->sing, pivtol);
+    factor_warp_kernel<T><<<gridw(h, WPB_F), 32 * WPB_F, 0, st>>>((int)h->S, h->ld, jac, (T*)h->LU, h->piv, (T*)h->G,
+                                                                h->sing, h->count, pivtol);
     prof_end(h, st);
     return launch_check(h);
 }
@@ -779,8 +828,8 @@ template <class T, int NR_>
 abs_status solve_launch(abs_problem* h, const double* jac, const double* xd, const double* r0, const double* r1,
                         double* o0, double* o1, cudaStream_t st) {
     prof_begin(h, K_SOLVE, st);
-    solve_kernel<T, NR_><<<grid1(h), kThrS, 0, st>>>(h->P, (int)h->S, h->ld, jac, (const T*)h->LU, h->piv,
-                                                     (const T*)h->G, xd, r0, r1, o0, o1);
+    solve_warp_kernel<T, NR_><<<gridw(h, WPB_S), 32 * WPB_S, 0, st>>>(h->P, (int)h->S, h->ld, jac, (const T*)h->LU,
+                                                                       h->piv, (const T*)h->G, xd, r0, r1, o0, o1);
     prof_end(h, st);
     return launch_check(h);
 }
@@ -803,9 +852,11 @@ abs_status solve_jt(abs_problem* h, int prec, const double* jac, const double* g
         ~End() { prof_end(h, st); }
     } end{h, st};
     if (prec == ABS_PREC_FP32)
-        solve_t_kernel<float><<<grid1(h), kThrS, 0, st>>>((int)h->S, h->ld, jac, (const float*)h->LU, h->piv, g, out);
+        solve_t_warp_kernel<float><<<gridw(h, WPB_S), 32 * WPB_S, 0, st>>>((int)h->S, h->ld, jac, (const float*)h->LU,
+                                                                            h->piv, g, out);
     else
-        solve_t_kernel<double><<<grid1(h), kThrS, 0, st>>>((int)h->S, h->ld, jac, (const double*)h->LU, h->piv, g, out);
+        solve_t_warp_kernel<double><<<gridw(h, WPB_S), 32 * WPB_S, 0, st>>>((int)h->S, h->ld, jac,
+                                                                             (const double*)h->LU, h->piv, g, out);
     return launch_check(h);
 }
 
@@ -823,17 +874,14 @@ abs_status kkt_factor_core(abs_problem* h, KKTSys& K, const double* xd, int64_t*
     if (K.prec == ABS_PREC_FP32) r = factor_launch<float>(h, K.jac, pivtol, st);
     else r = factor_launch<double>(h, K.jac, pivtol, st);
     if (r != ABS_OK) return r;
-    count_kernel<<<grid1(h), kThrS, 0, st>>>((int)h->S, h->sing, h->count);
-    if ((r = launch_check(h)) != ABS_OK) return r;
     if ((r = solve_j(h, K.prec, K.jac, xd, nullptr, nullptr, V(h, V_Q), nullptr, st)) != ABS_OK) return r;
     schur_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, K.hes, K.sig, K.use_w, nullptr, V(h, V_Q), nullptr,
                                              h->part);
     if ((r = launch_check(h)) != ABS_OK) return r;
     int cnt = 0;
-    CK(cudaMemcpyAsync(&cnt, h->count, sizeof(int), cudaMemcpyDeviceToHost, st));
     const int ops[5] = {RSUM, RSUM, RSUM, RSUM, RSUM};
     double red[5];
-    if ((r = fetch_partials(h, st, 5, ops, red)) != ABS_OK) return r;
+    if ((r = fetch_partials(h, st, 5, ops, red, {}, nullptr, h->count, &cnt)) != ABS_OK) return r;
     K.A0 = red[0];
     K.Q2 = red[1];
     if (wdd) *wdd = red[4];
@@ -852,18 +900,14 @@ abs_status kkt_solve_once(abs_problem* h, const KKTSys& K, const double* xd, con
     schur_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q), rz,
                                              h->part);
     if ((r = launch_check(h)) != ABS_OK) return r;
-    const int ops[4] = {RSUM, RSUM, RSUM, RSUM};
-    double red[4];
-    if ((r = fetch_partials(h, st, 4, ops, red)) != ABS_OK) return r;
-    const double beta = red[2] - K.dw * red[3];
-    const double dd = (rd - beta) / K.Sd;
-    dz_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, K.hes, K.sig, K.dw, K.use_w, V(h, V_P), V(h, V_Q), dd, rz,
+    // dd = (rd - beta) / S_d on the device, into the d slot of dz: no host round trip
+    double* ddp = dz + (int64_t)NSC * h->ld;
+    finalize_dd_kernel<<<1, 256, 0, st>>>(h->part, h->nblk2, rd, K.dw, K.Sd, ddp);
+    if ((r = launch_check(h)) != ABS_OK) return r;
+    dz_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, K.hes, K.sig, K.dw, K.use_w, V(h, V_P), V(h, V_Q), ddp, rz,
                                           dz, V(h, V_G));
     if ((r = launch_check(h)) != ABS_OK) return r;
-    CK(cudaMemcpyAsync(dz + (int64_t)NSC * h->ld, &dd, sizeof(double), cudaMemcpyHostToDevice, st));
     if ((r = solve_jt(h, K.prec, K.jac, V(h, V_G), dl, st)) != ABS_OK) return r;
-    // the pageable copy of dd above must complete before dd goes out of scope
-    CK(cudaStreamSynchronize(st));
     return ABS_OK;
 }
 
@@ -875,15 +919,15 @@ abs_status kkt_solve_refined(abs_problem* h, const KKTSys& K, const double* xd, 
     if ((r = kkt_solve_once(h, K, xd, rz, rd, rc, dz, dl, st)) != ABS_OK) return r;
     int k = 0;
     double sc = 0.0;
+    double* ddp = dz + (int64_t)NSC * h->ld;
     for (;;) {
-        double dd = 0.0;
-        CK(cudaMemcpyAsync(&dd, dz + (int64_t)NSC * h->ld, sizeof(double), cudaMemcpyDeviceToHost, st));
-        kkt_residual_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, K.jac, K.hes, K.sig, K.dw, K.use_w, dz, dd,
+        if (max_refine == 0 && !resid) break;   // nothing to refine and no residual asked for
+        kkt_residual_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, K.jac, K.hes, K.sig, K.dw, K.use_w, dz, ddp,
                                                         dl, rz, rc, V(h, V_RHOZ), V(h, V_RHOC), h->part);
         if ((r = launch_check(h)) != ABS_OK) return r;
         const int ops[5] = {RMAX, RMAX, RSUM, RMAX, RMAX};
-        double red[5];
-        if ((r = fetch_partials(h, st, 5, ops, red)) != ABS_OK) return r;
+        double red[5], dd = 0.0;
+        if ((r = fetch_partials(h, st, 5, ops, red, {ddp}, &dd)) != ABS_OK) return r;
         const double b = -h->P.u_max * M_PI * 0.5 * K.d;
         const double rhod = rd - ((K.Kdd + K.dw) * dd + b * red[2]);
         const double rn = std::max(std::max(red[0], red[1]), std::fabs(rhod));
@@ -891,19 +935,13 @@ abs_status kkt_solve_refined(abs_problem* h, const KKTSys& K, const double* xd, 
         sc = rn / (bn + 1e-300);
         if (!(sc == sc)) return fail(h, ABS_ERR_NUMERIC, "NaN in the KKT solve");
         if (sc <= tol || k >= max_refine) break;
-        // correction
+        // correction, then add it (including the d slot) to the solution
         if ((r = kkt_solve_once(h, K, xd, V(h, V_RHOZ), rhod, V(h, V_RHOC), V(h, V_CZ), V(h, V_CL), st)) != ABS_OK)
             return r;
-        axpy_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, 1.0, V(h, V_CZ), dz);
+        axpy_d_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, V(h, V_CZ), dz, true);
         if ((r = launch_check(h)) != ABS_OK) return r;
-        axpy_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, 1.0, V(h, V_CL), dl);
+        axpy_d_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, V(h, V_CL), dl, false);
         if ((r = launch_check(h)) != ABS_OK) return r;
-        double cd = 0.0;
-        CK(cudaMemcpyAsync(&cd, V(h, V_CZ) + (int64_t)NSC * h->ld, sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        dd += cd;
-        CK(cudaMemcpyAsync(dz + (int64_t)NSC * h->ld, &dd, sizeof(double), cudaMemcpyHostToDevice, st));
-        CK(cudaStreamSynchronize(st));
         ++k;
     }
     if (steps) *steps = k;
@@ -1234,7 +1272,8 @@ abs_status kkt_solve(abs_problem* h, const double* rhs_x, const double* rhs_c, d
     CK(cudaMemcpyAsync(xd, &K.d, sizeof(double), cudaMemcpyHostToDevice, st));
     int steps = 0;
     double resid = 0.0;
-    abs_status r = kkt_solve_refined(h, K, xd, rhs_x, rd, rhs_c, sol_x, sol_c, max_refine, refine_tol, &steps, &resid, st);
+    abs_status r = kkt_solve_refined(h, K, xd, rhs_x, rd, rhs_c, sol_x, sol_c, max_refine, refine_tol, &steps,
+                                     (info || max_refine > 0) ? &resid : nullptr, st);
     if (r != ABS_OK) return r;
     if (info) {
         info->refine_steps = steps;
@@ -1377,13 +1416,12 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
         return fail(nullptr, ABS_ERR_CUDA, std::string("kkt_newton_noalloc: ") + cudaGetErrorString(e));
     // the singular-block counter must start at zero on every call
     CK(cudaMemsetAsync(count, 0, sizeof(int), st));
-    factor_kernel<double><<<g1, kThrS, 0, st>>>((int)S, ld, jac_vals, LU, piv, G, sing, 1e-14);
-    NA_LAUNCHED();
-    count_kernel<<<g1, kThrS, 0, st>>>((int)S, sing, count);
+    const dim3 gf((unsigned)((S + WPB_F - 1) / WPB_F)), gs((unsigned)((S + WPB_S - 1) / WPB_S));
+    factor_warp_kernel<double><<<gf, 32 * WPB_F, 0, st>>>((int)S, ld, jac_vals, LU, piv, G, sing, count, 1e-14);
     NA_LAUNCHED();
     // p = J^-1 r_c, q = J^-1 b
-    solve_kernel<double, 2><<<g1, kThrS, 0, st>>>(P, (int)S, ld, jac_vals, LU, piv, G, x + od, rhs_c, nullptr, pv,
-                                                  qv);
+    solve_warp_kernel<double, 2><<<gs, 32 * WPB_S, 0, st>>>(P, (int)S, ld, jac_vals, LU, piv, G, x + od, rhs_c,
+                                                            nullptr, pv, qv);
     NA_LAUNCHED();
     schur_kernel<<<g2, kThr, 0, st>>>((int)S, ld, hess_vals, sigma, true, pv, qv, rhs_x, part);
     NA_LAUNCHED();
@@ -1409,10 +1447,10 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
     if (!(Sd > 0.0)) return fail(nullptr, ABS_ERR_INERTIA, "kkt_newton_noalloc: Schur complement on d is not positive");
     const double beta = red[2] - delta_w * red[3];
     const double dd = (hx[2] - beta) / Sd;
-    dz_kernel<<<g2, kThr, 0, st>>>((int)S, ld, hess_vals, sigma, delta_w, true, pv, qv, dd, rhs_x, sol_x, gv);
-    NA_LAUNCHED();
     CK(cudaMemcpyAsync(sol_x + od, &dd, sizeof(double), cudaMemcpyHostToDevice, st));
-    solve_t_kernel<double><<<g1, kThrS, 0, st>>>((int)S, ld, jac_vals, LU, piv, gv, sol_c);
+    dz_kernel<<<g2, kThr, 0, st>>>((int)S, ld, hess_vals, sigma, delta_w, true, pv, qv, sol_x + od, rhs_x, sol_x, gv);
+    NA_LAUNCHED();
+    solve_t_warp_kernel<double><<<gs, 32 * WPB_S, 0, st>>>((int)S, ld, jac_vals, LU, piv, gv, sol_c);
     NA_LAUNCHED();
 #undef NA_LAUNCHED
     // dd lives on this stack frame until the copy above has completed

@@ -298,290 +298,4 @@ __device__ inline void hv_stage(int64_t ld, const double* __restrict__ hes, cons
     }
 }
 
-// ------------------------------------------------------------------------------------
-// A4: block LU of every scenario's constraint Jacobian, one thread per scenario.
-// J_s is block tridiagonal: diagonal blocks A_n (22 x 22), sub-diagonal C_n = dc_n/dz_{n-1}
-// (only the stream-from-below columns), super-diagonal B_n = dc_n/dz_{n+1} (stream-from-
-// above columns).  Recurrence: At_0 = A_0, At_n = A_n - C_n At_{n-1}^{-1} B_{n-1}; each
-// At_n is LU-factored with partial pivoting inside the block (P At = L U, the reciprocal
-// pivots kept on U's diagonal), and G_n = At_n^{-1} B_n (22 x 11) is stored for the
-// back substitution.  Storage (SoA): LU[n][i][j], piv[n][k], G[n][i][a].
-// ------------------------------------------------------------------------------------
-template <class T>
-__device__ inline T& mat(T* base, int64_t ld, int i, int j) { return base[(int64_t)(i * NV + j) * ld]; }
-
-template <class T>
-__global__ void __launch_bounds__(64) factor_kernel(int S, int64_t ld, const double* __restrict__ jac,
-                                                    T* __restrict__ LU, unsigned char* __restrict__ piv,
-                                                    T* __restrict__ G, int* __restrict__ sing, double pivtol) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    int singular = 0;
-    for (int n = 0; n < N_STAGES; ++n) {
-        const int t = stage_type(n);
-        const int base = c_segJ[n];
-        T* A = LU + (int64_t)n * NV * NV * ld + s;
-        for (int k = 0; k < NV * NV; ++k) A[(int64_t)k * ld] = T(0);
-        for (int k = 0; k < c_nown[t]; ++k) {
-            const Ent e = c_own[t][k];
-            mat(A, ld, e.r, e.c) = (T)jac[(int64_t)(base + e.slot) * ld + s];
-        }
-        if (n > 0) {
-            const T* Gp = G + (int64_t)(n - 1) * NV * NABV * ld + s;
-            for (int k = 0; k < c_nblw[t]; ++k) {
-                const Ent e = c_blw[t][k];
-                const T cv = (T)jac[(int64_t)(base + e.slot) * ld + s];
-                const int i = blw_var(e.c);
-#pragma unroll
-                for (int a = 0; a < NABV; ++a)
-                    mat(A, ld, e.r, abv_var(a)) -= cv * Gp[(int64_t)(i * NABV + a) * ld];
-            }
-        }
-        T amax = T(0);
-        for (int k = 0; k < NV * NV; ++k) amax = fmax(amax, (T)fabs(A[(int64_t)k * ld]));
-        const T tiny = (T)pivtol * amax;
-        for (int k = 0; k < NV; ++k) {
-            int p = k;
-            T best = (T)fabs(mat(A, ld, k, k));
-            for (int i = k + 1; i < NV; ++i) {
-                const T a = (T)fabs(mat(A, ld, i, k));
-                if (a > best) {
-                    best = a;
-                    p = i;
-                }
-            }
-            piv[(int64_t)(n * NV + k) * ld + s] = (unsigned char)p;
-            if (p != k) {
-                for (int j = 0; j < NV; ++j) {
-                    const T tmp = mat(A, ld, k, j);
-                    mat(A, ld, k, j) = mat(A, ld, p, j);
-                    mat(A, ld, p, j) = tmp;
-                }
-            }
-            T ukk = mat(A, ld, k, k);
-            if (!(fabs(ukk) > tiny)) {
-                singular = 1;
-                ukk = (ukk < T(0) ? -T(1) : T(1)) * (tiny > T(0) ? tiny : T(1));
-            }
-            const T inv = T(1) / ukk;
-            mat(A, ld, k, k) = inv;
-            for (int i = k + 1; i < NV; ++i) {
-                const T l = mat(A, ld, i, k) * inv;
-                mat(A, ld, i, k) = l;
-                if (l != T(0)) {
-                    for (int j = k + 1; j < NV; ++j) mat(A, ld, i, j) -= l * mat(A, ld, k, j);
-                }
-            }
-        }
-        if (n + 1 < N_STAGES) {
-            T* Gn = G + (int64_t)n * NV * NABV * ld + s;
-            for (int k = 0; k < NV * NABV; ++k) Gn[(int64_t)k * ld] = T(0);
-            for (int k = 0; k < c_nabv[t]; ++k) {
-                const Ent e = c_abv[t][k];
-                Gn[(int64_t)(e.r * NABV + e.c) * ld] = (T)jac[(int64_t)(base + e.slot) * ld + s];
-            }
-            // G_n <- At_n^{-1} B_n : row swaps, unit-lower forward, upper backward
-            for (int k = 0; k < NV; ++k) {
-                const int p = piv[(int64_t)(n * NV + k) * ld + s];
-                if (p != k) {
-#pragma unroll
-                    for (int a = 0; a < NABV; ++a) {
-                        const T tmp = Gn[(int64_t)(k * NABV + a) * ld];
-                        Gn[(int64_t)(k * NABV + a) * ld] = Gn[(int64_t)(p * NABV + a) * ld];
-                        Gn[(int64_t)(p * NABV + a) * ld] = tmp;
-                    }
-                }
-            }
-            for (int i = 1; i < NV; ++i) {
-                for (int k = 0; k < i; ++k) {
-                    const T l = mat(A, ld, i, k);
-                    if (l != T(0)) {
-#pragma unroll
-                        for (int a = 0; a < NABV; ++a)
-                            Gn[(int64_t)(i * NABV + a) * ld] -= l * Gn[(int64_t)(k * NABV + a) * ld];
-                    }
-                }
-            }
-            for (int i = NV - 1; i >= 0; --i) {
-                for (int k = i + 1; k < NV; ++k) {
-                    const T u = mat(A, ld, i, k);
-                    if (u != T(0)) {
-#pragma unroll
-                        for (int a = 0; a < NABV; ++a)
-                            Gn[(int64_t)(i * NABV + a) * ld] -= u * Gn[(int64_t)(k * NABV + a) * ld];
-                    }
-                }
-                const T inv = mat(A, ld, i, i);
-#pragma unroll
-                for (int a = 0; a < NABV; ++a) Gn[(int64_t)(i * NABV + a) * ld] *= inv;
-            }
-        }
-    }
-    sing[s] = singular;
-}
-
-// At_n^{-1} v in place (v in registers / local memory)
-template <class T>
-__device__ inline void lu_apply(const T* A, const unsigned char* pv, int64_t ld, T (&v)[NV]) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        const int p = pv[(int64_t)k * ld];
-        if (p != k) {
-            const T tmp = v[k];
-            v[k] = v[p];
-            v[p] = tmp;
-        }
-    }
-#pragma unroll
-    for (int i = 1; i < NV; ++i) {
-        T acc = v[i];
-#pragma unroll
-        for (int k = 0; k < i; ++k) acc -= mat(const_cast<T*>(A), ld, i, k) * v[k];
-        v[i] = acc;
-    }
-#pragma unroll
-    for (int i = NV - 1; i >= 0; --i) {
-        T acc = v[i];
-#pragma unroll
-        for (int k = i + 1; k < NV; ++k) acc -= mat(const_cast<T*>(A), ld, i, k) * v[k];
-        v[i] = acc * mat(const_cast<T*>(A), ld, i, i);
-    }
-}
-
-// At_n^{-T} v in place:  At^T = U^T L^T P  ->  U^T w = v,  L^T y = w,  v = P^T y
-template <class T>
-__device__ inline void lu_apply_t(const T* A, const unsigned char* pv, int64_t ld, T (&v)[NV]) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        T acc = v[i];
-#pragma unroll
-        for (int k = 0; k < i; ++k) acc -= mat(const_cast<T*>(A), ld, k, i) * v[k];
-        v[i] = acc * mat(const_cast<T*>(A), ld, i, i);
-    }
-#pragma unroll
-    for (int i = NV - 2; i >= 0; --i) {
-        T acc = v[i];
-#pragma unroll
-        for (int k = i + 1; k < NV; ++k) acc -= mat(const_cast<T*>(A), ld, k, i) * v[k];
-        v[i] = acc;
-    }
-#pragma unroll
-    for (int k = NV - 1; k >= 0; --k) {
-        const int p = pv[(int64_t)k * ld];
-        if (p != k) {
-            const T tmp = v[k];
-            v[k] = v[p];
-            v[p] = tmp;
-        }
-    }
-}
-
-// J_s x = r for every scenario (one thread each), NRHS right-hand sides.  rhs k is the
-// row vector r[k] (or, when r[k] is null, b = dc/dd: -u_max pi d / 2 in every hydraulic
-// row).  Solutions are written to out[k] in primal layout (without the d entry).
-template <class T, int NRHS>
-__global__ void __launch_bounds__(64) solve_kernel(const Params P, int S, int64_t ld, const double* __restrict__ jac,
-                                                   const T* __restrict__ LU, const unsigned char* __restrict__ piv,
-                                                   const T* __restrict__ G, const double* x_d,
-                                                   const double* r0, const double* r1, double* o0, double* o1) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    const double* rr[2] = {r0, r1};
-    double* oo[2] = {o0, o1};
-    const double bval = -P.u_max * M_PI * 0.5 * x_d[0];
-    // forward: w_n = r_n - C_n y_{n-1},  y_n = At_n^{-1} w_n
-    for (int n = 0; n < N_STAGES; ++n) {
-        const int t = stage_type(n);
-        const int base = c_segJ[n];
-        const T* A = LU + (int64_t)n * NV * NV * ld + s;
-        const unsigned char* pv = piv + (int64_t)n * NV * ld + s;
-#pragma unroll
-        for (int k = 0; k < NRHS; ++k) {
-            T w[NV];
-            if (rr[k]) {
-#pragma unroll
-                for (int r = 0; r < NR; ++r) w[r] = (T)rr[k][(int64_t)(NR * n + r) * ld + s];
-            } else {
-#pragma unroll
-                for (int r = 0; r < NR; ++r) w[r] = (r == R_H) ? (T)bval : T(0);
-            }
-            if (n > 0) {
-                for (int q = 0; q < c_nblw[t]; ++q) {
-                    const Ent e = c_blw[t][q];
-                    w[e.r] -= (T)jac[(int64_t)(base + e.slot) * ld + s] *
-                              (T)oo[k][(int64_t)(NV * (n - 1) + blw_var(e.c)) * ld + s];
-                }
-            }
-            lu_apply(A, pv, ld, w);
-#pragma unroll
-            for (int j = 0; j < NV; ++j) oo[k][(int64_t)(NV * n + j) * ld + s] = (double)w[j];
-        }
-    }
-    // backward: x_n = y_n - G_n x_{n+1}
-    for (int n = N_STAGES - 2; n >= 0; --n) {
-        const T* Gn = G + (int64_t)n * NV * NABV * ld + s;
-#pragma unroll
-        for (int k = 0; k < NRHS; ++k) {
-            T xa[NABV];
-#pragma unroll
-            for (int a = 0; a < NABV; ++a) xa[a] = (T)oo[k][(int64_t)(NV * (n + 1) + abv_var(a)) * ld + s];
-#pragma unroll
-            for (int i = 0; i < NV; ++i) {
-                T acc = (T)oo[k][(int64_t)(NV * n + i) * ld + s];
-#pragma unroll
-                for (int a = 0; a < NABV; ++a) acc -= Gn[(int64_t)(i * NABV + a) * ld] * xa[a];
-                oo[k][(int64_t)(NV * n + i) * ld + s] = (double)acc;
-            }
-        }
-    }
-}
-
-// J_s^T v = g for every scenario (one thread each); g, out: primal layout (no d).
-template <class T>
-__global__ void __launch_bounds__(64) solve_t_kernel(int S, int64_t ld, const double* __restrict__ jac,
-                                                     const T* __restrict__ LU, const unsigned char* __restrict__ piv,
-                                                     const double* __restrict__ g, double* out) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    // forward (U^T of the block LU): u_n = At_n^{-T} (g_n - B_{n-1}^T u_{n-1})
-    for (int n = 0; n < N_STAGES; ++n) {
-        const T* A = LU + (int64_t)n * NV * NV * ld + s;
-        const unsigned char* pv = piv + (int64_t)n * NV * ld + s;
-        T w[NV];
-#pragma unroll
-        for (int j = 0; j < NV; ++j) w[j] = (T)g[(int64_t)(NV * n + j) * ld + s];
-        if (n > 0) {
-            const int tb = stage_type(n - 1), bb = c_segJ[n - 1];
-            for (int q = 0; q < c_nabv[tb]; ++q) {
-                const Ent e = c_abv[tb][q];
-                w[abv_var(e.c)] -= (T)jac[(int64_t)(bb + e.slot) * ld + s] *
-                                   (T)out[(int64_t)(NR * (n - 1) + e.r) * ld + s];
-            }
-        }
-        lu_apply_t(A, pv, ld, w);
-#pragma unroll
-        for (int j = 0; j < NV; ++j) out[(int64_t)(NR * n + j) * ld + s] = (double)w[j];
-    }
-    // backward (L^T): v_n = u_n - At_n^{-T} C_{n+1}^T v_{n+1}
-    for (int n = N_STAGES - 2; n >= 0; --n) {
-        const T* A = LU + (int64_t)n * NV * NV * ld + s;
-        const unsigned char* pv = piv + (int64_t)n * NV * ld + s;
-        const int ta = stage_type(n + 1), ba = c_segJ[n + 1];
-        T w[NV];
-#pragma unroll
-        for (int j = 0; j < NV; ++j) w[j] = T(0);
-        for (int q = 0; q < c_nblw[ta]; ++q) {
-            const Ent e = c_blw[ta][q];
-            w[blw_var(e.c)] += (T)jac[(int64_t)(ba + e.slot) * ld + s] *
-                               (T)out[(int64_t)(NR * (n + 1) + e.r) * ld + s];
-        }
-        lu_apply_t(A, pv, ld, w);
-#pragma unroll
-        for (int j = 0; j < NV; ++j) {
-            const int64_t o = (int64_t)(NR * n + j) * ld + s;
-            out[o] = (double)((T)out[o] - w[j]);
-        }
-    }
-}
-
 }  // namespace absorber

@@ -1,0 +1,370 @@
+// kernels_warp.cuh -- warp-cooperative stage-block LU and block solves (A4, A6).
+//
+// One warp per scenario.  Each 22 x 22 stage block lives in shared memory while the
+// warp works on it: pivot search with rows on lanes, the trailing update with columns
+// on lanes (each lane keeps its pivot-row entry in a register and walks the rows), the
+// super-diagonal block B_n appended as 11 extra columns so that the elimination yields
+// L^-1 P B_n, then U G_n = L^-1 P B_n by backward substitution.  Vectors of the solves
+// live one entry per lane; broadcasts are warp shuffles.
+//
+// Factor storage is per scenario and contiguous (internal layout, not part of the C
+// ABI): LU[s][n][22][22], G[s][n][22][11], piv[s][n][22], so every warp access to the
+// factors is coalesced.  The reciprocal of each pivot is kept on U's diagonal.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace absorber {
+
+constexpr int NCA = NV + NABV;    // augmented columns [A_n | B_n]
+constexpr int PADA = NCA + 1;     // shared-memory row stride of the augmented block
+constexpr int PADL = NV + 1;      // shared-memory row stride of a staged LU block
+constexpr int WPB_F = 4;          // warps (scenarios) per block, factor
+constexpr int WPB_S = 4;          // warps (scenarios) per block, solves
+
+__host__ __device__ constexpr int64_t lu_off(int64_t s, int n) { return (s * N_STAGES + n) * (int64_t)(NV * NV); }
+__host__ __device__ constexpr int64_t g_off(int64_t s, int n) { return (s * N_STAGES + n) * (int64_t)(NV * NABV); }
+__host__ __device__ constexpr int64_t pv_off(int64_t s, int n) { return (s * N_STAGES + n) * (int64_t)NV; }
+
+template <class T>
+__device__ inline T shfl(T v, int src) {
+    return __shfl_sync(0xffffffffu, v, src);
+}
+
+// |a| as an unsigned integer with the same ordering as |a| itself (IEEE layout with the
+// sign cleared): pivot searches and block maxima compare these on the integer pipe,
+// keeping them off the floating-point pipe (slow for FP64 on this part)
+__device__ inline unsigned long long abs_key(double a) {
+    return (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull;
+}
+__device__ inline unsigned long long abs_key(float a) {
+    return (unsigned long long)(__float_as_uint(a) & 0x7fffffffu);
+}
+__device__ inline double key_value(unsigned long long k, double) { return __longlong_as_double((long long)k); }
+__device__ inline float key_value(unsigned long long k, float) { return __uint_as_float((unsigned)k); }
+
+// reciprocal: FP32 seed refined by two Newton steps r <- r (2 - a r) in T (|a| in the
+// normal FP32 range; exact division otherwise)
+__device__ inline double recip(double a) {
+    const double m = fabs(a);
+    if (m > 1e-30 && m < 1e30) {
+        double r = (double)(1.0f / (float)a);
+        r = r * fma(-a, r, 2.0);
+        r = r * fma(-a, r, 2.0);
+        return r;
+    }
+    return 1.0 / a;
+}
+__device__ inline float recip(float a) { return 1.0f / a; }
+
+template <class T>
+__global__ void __launch_bounds__(32 * WPB_F) factor_warp_kernel(int S, int64_t ld, const double* __restrict__ jac,
+                                                                 T* __restrict__ LU, unsigned char* __restrict__ piv,
+                                                                 T* __restrict__ G, int* __restrict__ sing,
+                                                                 int* __restrict__ count, double pivtol) {
+    __shared__ T sA[WPB_F][NV][PADA];
+    __shared__ T sG[WPB_F][NV][NABV];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = blockIdx.x * WPB_F + warp;
+    if (s >= S) return;    // whole warps leave together; no block-level barriers below
+    T(*A)[PADA] = sA[warp];
+    T(*Gp)[NABV] = sG[warp];
+    int singular = 0;
+    for (int n = 0; n < N_STAGES; ++n) {
+        const int t = stage_type(n);
+        const int base = c_segJ[n];
+        for (int e = lane; e < NV * NCA; e += 32) A[e / NCA][e % NCA] = T(0);
+        __syncwarp();
+        for (int k = lane; k < c_nown[t]; k += 32) {
+            const Ent e = c_own[t][k];
+            A[e.r][e.c] = (T)jac[(int64_t)(base + e.slot) * ld + s];
+        }
+        if (n + 1 < N_STAGES) {
+            for (int k = lane; k < c_nabv[t]; k += 32) {
+                const Ent e = c_abv[t][k];
+                A[e.r][NV + e.c] = (T)jac[(int64_t)(base + e.slot) * ld + s];
+            }
+        }
+        __syncwarp();
+        // Schur update with the previous stage: A_n -= C_n G_{n-1}
+        if (n > 0) {
+            for (int k = 0; k < c_nblw[t]; ++k) {
+                const Ent e = c_blw[t][k];
+                const T cv = (T)jac[(int64_t)(base + e.slot) * ld + s];
+                if (lane < NABV) A[e.r][abv_var(lane)] -= cv * Gp[blw_var(e.c)][lane];
+                __syncwarp();
+            }
+        }
+        // largest entry of the block (for the singularity test)
+        unsigned long long kmax = 0ull;
+        for (int e = lane; e < NV * NV; e += 32) {
+            const unsigned long long kk = abs_key(A[e / NV][e % NV]);
+            kmax = kk > kmax ? kk : kmax;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, kmax, o);
+            kmax = k2 > kmax ? k2 : kmax;
+        }
+        const T tiny = (T)pivtol * key_value(kmax, T(0));
+        const unsigned long long ktiny = abs_key(tiny);
+        unsigned char* pv = piv + pv_off(s, n);
+        // LU with partial pivoting, row operations on all 33 columns
+        for (int k = 0; k < NV; ++k) {
+            // key 0 marks lanes outside the candidate rows (an exact zero candidate also has
+            // key 0 and loses ties to lower rows: the singular test below catches it)
+            unsigned long long v = (lane >= k && lane < NV) ? abs_key(A[lane][k]) : 0ull;
+            int idx = (lane >= k && lane < NV) ? lane : NV;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long v2 = __shfl_xor_sync(0xffffffffu, v, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+                if (v2 > v || (v2 == v && i2 < idx)) {
+                    v = v2;
+                    idx = i2;
+                }
+            }
+            if (idx >= NV) idx = k;
+            const int p = idx;
+            if (lane == 0) pv[k] = (unsigned char)p;
+            if (p != k) {
+                for (int j = lane; j < NCA; j += 32) {
+                    const T a = A[k][j];
+                    A[k][j] = A[p][j];
+                    A[p][j] = a;
+                }
+            }
+            __syncwarp();
+            T ukk = A[k][k];
+            if (!(abs_key(ukk) > ktiny) || ukk != ukk) {
+                singular = 1;
+                ukk = (ukk < T(0) ? T(-1) : T(1)) * (tiny > T(0) ? tiny : T(1));
+            }
+            const T inv = recip(ukk);
+            if (lane > k && lane < NV) A[lane][k] *= inv;
+            __syncwarp();
+            const int j = k + 1 + lane;
+            if (j < NCA) {
+                const T akj = A[k][j];
+#pragma unroll 4
+                for (int i = k + 1; i < NV; ++i) A[i][j] -= A[i][k] * akj;
+            }
+            if (lane == 0) A[k][k] = inv;
+            __syncwarp();
+        }
+        // U G = L^-1 P B: lanes 0..21 = (column a = lane % 11, row parity lane / 11)
+        if (n + 1 < N_STAGES) {
+            const int a = lane % NABV, grp = lane / NABV;
+            for (int i = NV - 1; i >= 0; --i) {
+                const T g = A[i][NV + a] * A[i][i];
+                __syncwarp();
+                if (grp < 2) {
+#pragma unroll 4
+                    for (int r = grp; r < i; r += 2) A[r][NV + a] -= A[r][i] * g;
+                    if (grp == 0) A[i][NV + a] = g;
+                }
+                __syncwarp();
+            }
+            T* Gn = G + g_off(s, n);
+            for (int e = lane; e < NV * NABV; e += 32) {
+                const T g = A[e / NABV][NV + e % NABV];
+                Gn[e] = g;
+                Gp[e / NABV][e % NABV] = g;
+            }
+        }
+        T* Ln = LU + lu_off(s, n);
+        for (int e = lane; e < NV * NV; e += 32) Ln[e] = A[e / NV][e % NV];
+        __syncwarp();
+    }
+    if (lane == 0) {
+        sing[s] = singular;
+        if (singular) atomicAdd(count, 1);
+    }
+}
+
+// stage an LU block (contiguous in global memory) into shared memory, coalesced
+template <class T>
+__device__ inline void stage_lu(const T* __restrict__ src, T (*dst)[PADL], int lane) {
+    for (int e = lane; e < NV * NV; e += 32) dst[e / NV][e % NV] = src[e];
+    __syncwarp();
+}
+
+// w <- At^-1 w, lane i holding w_i (lanes >= 22 carry zeros)
+template <class T>
+__device__ inline T lu_apply_warp(const T (*A)[PADL], const unsigned char* pv, int lane, T w) {
+#pragma unroll 1
+    for (int k = 0; k < NV; ++k) {
+        const int p = pv[k];
+        if (p != k) {
+            const T wk = shfl(w, k), wp = shfl(w, p);
+            if (lane == k) w = wp;
+            if (lane == p) w = wk;
+        }
+    }
+#pragma unroll 1
+    for (int k = 0; k < NV - 1; ++k) {
+        const T wk = shfl(w, k);
+        if (lane > k && lane < NV) w -= A[lane][k] * wk;
+    }
+#pragma unroll 1
+    for (int k = NV - 1; k >= 0; --k) {
+        if (lane == k) w *= A[k][k];
+        const T wk = shfl(w, k);
+        if (lane < k) w -= A[lane][k] * wk;
+    }
+    return w;
+}
+
+// w <- At^-T w:  U^T forward, L^T backward, then the row swaps in reverse
+template <class T>
+__device__ inline T lu_apply_t_warp(const T (*A)[PADL], const unsigned char* pv, int lane, T w) {
+#pragma unroll 1
+    for (int k = 0; k < NV; ++k) {
+        if (lane == k) w *= A[k][k];
+        const T wk = shfl(w, k);
+        if (lane > k && lane < NV) w -= A[k][lane] * wk;
+    }
+#pragma unroll 1
+    for (int k = NV - 1; k > 0; --k) {
+        const T wk = shfl(w, k);
+        if (lane < k) w -= A[k][lane] * wk;
+    }
+#pragma unroll 1
+    for (int k = NV - 1; k >= 0; --k) {
+        const int p = pv[k];
+        if (p != k) {
+            const T wk = shfl(w, k), wp = shfl(w, p);
+            if (lane == k) w = wp;
+            if (lane == p) w = wk;
+        }
+    }
+    return w;
+}
+
+// J_s x = r (NRHS right-hand sides; a null r[k] means b = dc/dd), one warp per scenario
+template <class T, int NRHS>
+__global__ void __launch_bounds__(32 * WPB_S) solve_warp_kernel(const Params P, int S, int64_t ld,
+                                                                const double* __restrict__ jac, const T* __restrict__ LU,
+                                                                const unsigned char* __restrict__ piv,
+                                                                const T* __restrict__ G, const double* x_d,
+                                                                const double* r0, const double* r1, double* o0,
+                                                                double* o1) {
+    __shared__ T sL[WPB_S][NV][PADL];
+    __shared__ unsigned char sP[WPB_S][NV + 2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = blockIdx.x * WPB_S + warp;
+    if (s >= S) return;
+    T(*A)[PADL] = sL[warp];
+    unsigned char* pv = sP[warp];
+    const double* rr[2] = {r0, r1};
+    double* oo[2] = {o0, o1};
+    const T bval = (T)(-P.u_max * M_PI * 0.5 * x_d[0]);
+    const bool row = lane < NV;
+    T y[NRHS];
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) y[k] = T(0);
+    // forward: w_n = r_n - C_n y_{n-1},  y_n = At_n^-1 w_n
+    for (int n = 0; n < N_STAGES; ++n) {
+        const int t = stage_type(n);
+        const int base = c_segJ[n];
+        stage_lu(LU + lu_off(s, n), A, lane);
+        if (lane < NV) pv[lane] = piv[pv_off(s, n) + lane];
+        T w[NRHS];
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) {
+            if (rr[k]) w[k] = row ? (T)rr[k][(int64_t)(NR * n + lane) * ld + s] : T(0);
+            else w[k] = (lane == R_H) ? bval : T(0);
+        }
+        if (n > 0) {
+            for (int q = 0; q < c_nblw[t]; ++q) {
+                const Ent e = c_blw[t][q];
+                const T cv = (T)jac[(int64_t)(base + e.slot) * ld + s];
+#pragma unroll
+                for (int k = 0; k < NRHS; ++k) {
+                    const T yb = shfl(y[k], blw_var(e.c));
+                    if (lane == e.r) w[k] -= cv * yb;
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) {
+            y[k] = lu_apply_warp<T>(A, pv, lane, w[k]);
+            if (row) oo[k][(int64_t)(NV * n + lane) * ld + s] = (double)y[k];
+        }
+        __syncwarp();
+    }
+    // backward: x_n = y_n - G_n x_{n+1}   (y currently holds x_9 = y_9)
+    for (int n = N_STAGES - 2; n >= 0; --n) {
+        const T* Gn = G + g_off(s, n);
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) {
+            T acc = row ? (T)oo[k][(int64_t)(NV * n + lane) * ld + s] : T(0);
+#pragma unroll
+            for (int a = 0; a < NABV; ++a) {
+                const T xa = shfl(y[k], abv_var(a));
+                if (row) acc -= Gn[lane * NABV + a] * xa;
+            }
+            y[k] = acc;
+            if (row) oo[k][(int64_t)(NV * n + lane) * ld + s] = (double)acc;
+        }
+    }
+}
+
+// J_s^T v = g, one warp per scenario; g and out in primal layout (no d)
+template <class T>
+__global__ void __launch_bounds__(32 * WPB_S) solve_t_warp_kernel(int S, int64_t ld, const double* __restrict__ jac,
+                                                                  const T* __restrict__ LU,
+                                                                  const unsigned char* __restrict__ piv,
+                                                                  const double* __restrict__ g, double* out) {
+    __shared__ T sL[WPB_S][NV][PADL];
+    __shared__ unsigned char sP[WPB_S][NV + 2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = blockIdx.x * WPB_S + warp;
+    if (s >= S) return;
+    T(*A)[PADL] = sL[warp];
+    unsigned char* pv = sP[warp];
+    const bool row = lane < NV;
+    T u = T(0);
+    // forward (U^T of the block LU): u_n = At_n^-T (g_n - B_{n-1}^T u_{n-1})
+    for (int n = 0; n < N_STAGES; ++n) {
+        stage_lu(LU + lu_off(s, n), A, lane);
+        if (lane < NV) pv[lane] = piv[pv_off(s, n) + lane];
+        T w = row ? (T)g[(int64_t)(NV * n + lane) * ld + s] : T(0);
+        if (n > 0) {
+            const int tb = stage_type(n - 1), bb = c_segJ[n - 1];
+            for (int q = 0; q < c_nabv[tb]; ++q) {
+                const Ent e = c_abv[tb][q];
+                const T cv = (T)jac[(int64_t)(bb + e.slot) * ld + s];
+                const T ur = shfl(u, e.r);
+                if (lane == abv_var(e.c)) w -= cv * ur;
+            }
+        }
+        __syncwarp();
+        u = lu_apply_t_warp<T>(A, pv, lane, w);
+        if (row) out[(int64_t)(NR * n + lane) * ld + s] = (double)u;
+        __syncwarp();
+    }
+    // backward (L^T): v_n = u_n - At_n^-T C_{n+1}^T v_{n+1}   (u holds v_9 = u_9)
+    T v = u;
+    for (int n = N_STAGES - 2; n >= 0; --n) {
+        stage_lu(LU + lu_off(s, n), A, lane);
+        if (lane < NV) pv[lane] = piv[pv_off(s, n) + lane];
+        const int ta = stage_type(n + 1), ba = c_segJ[n + 1];
+        T w = T(0);
+        for (int q = 0; q < c_nblw[ta]; ++q) {
+            const Ent e = c_blw[ta][q];
+            const T cv = (T)jac[(int64_t)(ba + e.slot) * ld + s];
+            const T vr = shfl(v, e.r);
+            if (lane == blw_var(e.c)) w += cv * vr;
+        }
+        __syncwarp();
+        w = lu_apply_t_warp<T>(A, pv, lane, w);
+        const T un = row ? (T)out[(int64_t)(NR * n + lane) * ld + s] : T(0);
+        v = un - w;
+        if (row) out[(int64_t)(NR * n + lane) * ld + s] = (double)v;
+        __syncwarp();
+    }
+}
+
+}  // namespace absorber
