@@ -235,6 +235,17 @@ def batched_sizes(P=64, seed=3, lo=50, hi=2000):
     return np.rint(np.exp(math.log(lo) + (math.log(hi) - math.log(lo)) * u)).astype(np.int64)
 
 
+def batched_feeds(sizes, seed=3, dist="uniform"):
+    """Independent feed draws of a batch of problems: problem p takes the scenario
+    counters after those of problems 0..p-1 on its own stream (2), so no two scenarios
+    of the batch share a draw."""
+    out, first = [], 0
+    for S in sizes:
+        out.append(make_feeds(int(S), seed, dist=dist, stream=2, first=first))
+        first += int(S)
+    return out
+
+
 # Named workloads (sizes, draws and seeds of the five configurations).
 WORKLOADS = {
     "absorber-S10-u10-seed0": dict(S=10, seed=0, dist="uniform"),

@@ -287,6 +287,32 @@ abs_status ipm_solve(abs_problem* h, const abs_options* opt, const double* warm_
                      const double* warm_y, abs_result* res, double* x_out, double* y_out,
                      abs_stream_t stream);
 
+/* Batched interior-point solve of P independent design problems of form (10), each
+ * with its own scenario count, feeds, diameter, barrier parameter, filter and
+ * inertia-correction state (the batching form of the scenario workflow: many design
+ * studies of Section "Case study: absorber diameter minimization" side by side on one GPU).  Every kernel launch
+ * covers the scenarios of all problems still iterating, laid out side by side in one
+ * structure-of-arrays (problem p owns a contiguous run of scenario slots); per-problem
+ * sums, maxima and minima come from segmented reductions; the host takes each
+ * problem's scalar decisions from one fetch of those reductions per phase.  A problem
+ * that has converged or failed stops taking part.  The method and its starting point are
+ * those of ipm_solve with warm_x = warm_y = NULL, applied to each problem: the
+ * expected-value starts of all problems are themselves solved as one batch of P
+ * one-scenario problems.
+ *   probs   host array of P handles from absorber_create (each a single problem; all
+ *           with the same parameter table).  The batch workspace is built on the first
+ *           call and cached on probs[0] for later calls with the same scenario counts; it
+ *           is freed with probs[0].
+ *   opt     host (NULL = defaults); obj_scaling <= 0 scales problem p by its own S_p.
+ *   res     host array of P results, one per problem (timings and launch counts are
+ *           those of the whole batch).
+ *   x_out   host array of P device primal vectors (each in its own problem's layout,
+ *           220*ld_p + 1) or NULL; entries may be NULL.
+ * Returns ABS_OK when the batch ran (each problem's outcome is in res[p].status) or an
+ * error of the batch as a whole (bad argument, CUDA error).  Synchronous. */
+abs_status ipm_solve_batched(abs_problem** probs, int32_t P, const abs_options* opt,
+                             abs_result* res, double** x_out, abs_stream_t stream);
+
 /* Newton direction of one interior-point iteration without any allocation.
  *
  * The paper has no counterpart: this entry exists for callers that cannot allocate

@@ -110,6 +110,8 @@ EXPORTS = {
                                      C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "ipm_solve": (C.c_int, [C.c_void_p, C.POINTER(AbsOptions), C.c_void_p, C.c_void_p, C.POINTER(AbsResult),
                             C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ipm_solve_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(AbsOptions), C.POINTER(AbsResult),
+                                    C.POINTER(C.c_void_p), C.c_void_p]),
 }
 
 _lib = None
@@ -331,3 +333,23 @@ class Problem:
     def values_to_scen(self, vals, nnz):
         """value array [nnz * ld] -> (S, nnz)."""
         return np.asarray(vals)[:nnz * self.ld].reshape(nnz, self.ld)[:, :self.S].T.copy()
+
+
+def ipm_solve_batched(problems, options=None, x_out=None, stream=None):
+    """Solve independent problems as one batch; returns one AbsResult per problem.
+
+    problems: list of Problem; x_out: None or a list of device primal vectors (or None
+    entries), one per problem, each in its own problem's layout."""
+    P = len(problems)
+    if P < 1:
+        raise ValueError("empty batch")
+    hs = (C.c_void_p * P)(*[p.h for p in problems])
+    res = (AbsResult * P)()
+    xo = None
+    if x_out is not None:
+        xo = (C.c_void_p * P)(*[_ptr(v) for v in x_out])
+    st = lib().ipm_solve_batched(hs, P, C.byref(options) if options is not None else None, res, xo,
+                                 _stream(stream))
+    if st != ABS_OK:
+        raise AbsorberError(st, lib().abs_last_error(problems[0].h).decode())
+    return list(res)

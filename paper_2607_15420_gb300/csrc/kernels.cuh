@@ -45,43 +45,61 @@ __host__ __device__ constexpr bool has_lo(int j) { return !(j >= LE && j < LE + 
 __host__ __device__ constexpr bool has_hi(int j) { return j == LT; }
 
 // ------------------------------------------------------------------------------------
-// block reductions (deterministic: fixed shuffle tree, fixed smem order)
+// problems: a launch covers one or many independent problems (a batch).  Scenario slot
+// s belongs to problem pid[s] (-1: padding); per-problem scalars live in device arrays
+// ps[field * NP + p].  pid == nullptr means a single problem owning every slot s < S,
+// ps == nullptr means no per-problem scalars (every problem active).
+// ------------------------------------------------------------------------------------
+enum PsField {
+    PS_MU = 0,     // barrier parameter
+    PS_TAU,        // fraction-to-the-boundary parameter
+    PS_ALPHA,      // primal step / trial step
+    PS_ALPHAZ,     // bound-multiplier step
+    PS_DW,         // primal regularisation delta_w
+    PS_ACT,        // 1: problem takes part in this iteration
+    PS_LSACT,      // 1: problem takes part in this line-search trial
+    PS_SOC,        // 1: the trial follows the second-order-correction direction
+    PS_A0,         // coefficient (first trial step) of the SOC right-hand side
+    PS_COUNT
+};
+
+struct BView {
+    const int* pid;
+    const double* ps;
+    int NP;
+};
+
+__device__ inline int prob_of(const BView& b, int s) { return b.pid ? b.pid[s] : 0; }
+__device__ inline double psv(const BView& b, int field, int p) { return b.ps[(int64_t)field * b.NP + p]; }
+// problem of slot s if it takes part (flag field PS_ACT or PS_LSACT), else -1
+__device__ inline int live_prob(const BView& b, int s, int S, int flag) {
+    if (s >= S) return -1;
+    const int p = prob_of(b, s);
+    if (p < 0) return -1;
+    if (b.ps && psv(b, flag, p) == 0.0) return -1;
+    return p;
+}
+
+// ------------------------------------------------------------------------------------
+// reductions: every (scenario, stage) thread stores its K partial values at
+// part[k * plane + n * ld + s] (plane = N_STAGES * ld); chunk_reduce / problem_reduce
+// (vec_kernels.cuh) combine them per problem in a fixed order (deterministic)
 // ------------------------------------------------------------------------------------
 enum RedOp { RSUM = 0, RMAX = 1, RMIN = 2 };
 
-__device__ inline double warp_red(double v, int op) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        double w = __shfl_xor_sync(0xffffffffu, v, o);
-        if (op == RSUM) v += w;
-        else if (op == RMAX) v = (w > v || w != w) ? w : v;
-        else v = (w < v || w != w) ? w : v;
-    }
-    return v;
+__device__ inline double red_id(int op) { return op == RSUM ? 0.0 : (op == RMAX ? -INFINITY : INFINITY); }
+
+__device__ inline double red_op(int op, double a, double b) {
+    if (op == RSUM) return a + b;
+    if (op == RMAX) return (b > a || b != b) ? b : a;
+    return (b < a || b != b) ? b : a;
 }
 
-// reduce K values per thread across the block; thread 0 writes part[k * nblk + blk]
 template <int K>
-__device__ inline void block_reduce_store(double (&v)[K], const int (&ops)[K], double* part,
-                                          int nblk, int blk) {
-    __shared__ double sm[K][32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = (blockDim.x + 31) >> 5;
+__device__ inline void store_partials(const double (&v)[K], double* part, int64_t ld, int s, int n) {
+    const int64_t plane = (int64_t)N_STAGES * ld;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double w = warp_red(v[k], ops[k]);
-        if (lane == 0) sm[k][wid] = w;
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            double w = (lane < nw) ? sm[k][lane]
-                                   : (ops[k] == RSUM ? 0.0 : (ops[k] == RMAX ? -INFINITY : INFINITY));
-            w = warp_red(w, ops[k]);
-            if (lane == 0) part[(int64_t)k * nblk + blk] = w;
-        }
-    }
+    for (int k = 0; k < K; ++k) part[(int64_t)k * plane + (int64_t)n * ld + s] = v[k];
 }
 
 // ------------------------------------------------------------------------------------
@@ -113,7 +131,7 @@ struct DevEmit {
 
 __device__ inline void load_stage(const Params& P, int S, int64_t ld, const double* __restrict__ x,
                                   const double* __restrict__ dx, double alpha, const double* __restrict__ feed,
-                                  int s, int n, StageIn& in) {
+                                  int s, int n, int p, StageIn& in) {
     const double* xs = x + s;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
@@ -151,21 +169,25 @@ __device__ inline void load_stage(const Params& P, int S, int64_t ld, const doub
         in.qb[4] = feed[(int64_t)F_V0 * ld + s];
         in.qb[5] = feed[(int64_t)F_T0 * ld + s] / P.sT;
     }
-    const int64_t od = (int64_t)NSC * ld;
+    const int64_t od = (int64_t)NSC * ld + p;   // the problem's d slot
     in.d = x[od] + (dx ? alpha * dx[od] : 0.0);
     in.P = feed[(int64_t)F_P * ld + s];
 }
 
-// partials (if non-null): [0] sum |c|, [1] max |c|, [2] sum of barrier logs of the
-// stage unknowns (at x + alpha dx), all per block.
+// partials (if part non-null): [0] |c| summed over the stage's rows, [1] their max,
+// [2] sum of the barrier logs of the stage unknowns.  trial = false: evaluation at x of
+// the problems flagged PS_ACT; trial = true: at x + alpha_p dir of the problems flagged
+// PS_LSACT, dir = dxB where PS_SOC is set, else dxA.
 template <bool WR, bool WJ, bool WH>
-__global__ void __launch_bounds__(128) eval_kernel(const Params P, int S, int64_t ld,
-                                                   const double* __restrict__ x, const double* __restrict__ dx,
-                                                   double alpha, const double* __restrict__ lam,
+__global__ void __launch_bounds__(128) eval_kernel(const Params P, int S, int64_t ld, const BView b, bool trial,
+                                                   const double* __restrict__ x, const double* __restrict__ dxA,
+                                                   const double* __restrict__ dxB, const double* __restrict__ lam,
                                                    const double* __restrict__ feed, double* c, double* jac,
                                                    double* hes, double* part) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
+    const int p = live_prob(b, s, S, trial ? PS_LSACT : PS_ACT);
+    if (p < 0) return;
     DevEmit<WR, WJ, WH> em;
     em.cv = c;
     em.jv = jac;
@@ -177,44 +199,45 @@ __global__ void __launch_bounds__(128) eval_kernel(const Params P, int S, int64_
     em.asum = 0.0;
     em.amax = 0.0;
     double blog = 0.0;
-    if (s < S) {
-        StageIn in;
-        load_stage(P, S, ld, x, dx, alpha, feed, s, n, in);
-        StageLam L;
-        if (WH) {
+    StageIn in;
+    const double* dx = nullptr;
+    double alpha = 0.0;
+    if (trial) {
+        dx = (b.ps && psv(b, PS_SOC, p) != 0.0) ? dxB : dxA;
+        alpha = psv(b, PS_ALPHA, p);
+    }
+    load_stage(P, S, ld, x, dx, alpha, feed, s, n, p, in);
+    StageLam L;
+    if (WH) {
 #pragma unroll
-            for (int r = 0; r < NR; ++r) L.own[r] = lam[(int64_t)(NR * n + r) * ld + s];
-            if (n > 0) {
+        for (int r = 0; r < NR; ++r) L.own[r] = lam[(int64_t)(NR * n + r) * ld + s];
+        if (n > 0) {
 #pragma unroll
-                for (int k = 0; k < 9; ++k) L.below[k] = lam[(int64_t)(NR * (n - 1) + k) * ld + s];
-                L.below[9] = lam[(int64_t)(NR * (n - 1) + R_E) * ld + s];
-            }
-            if (n + 1 < N_STAGES) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) L.above[k] = lam[(int64_t)(NR * (n + 1) + 7 + k) * ld + s];
-                L.above[4] = lam[(int64_t)(NR * (n + 1) + R_E) * ld + s];
-            }
+            for (int k = 0; k < 9; ++k) L.below[k] = lam[(int64_t)(NR * (n - 1) + k) * ld + s];
+            L.below[9] = lam[(int64_t)(NR * (n - 1) + R_E) * ld + s];
         }
-        stage_eval(P, in, WH ? &L : nullptr, em);
-        if (WH && n == 0) {
-            // the scenario's share of d-d: -u_max pi / 2 * sum_n lambda_hydraulic
-            double sl = 0.0;
+        if (n + 1 < N_STAGES) {
 #pragma unroll
-            for (int m = 0; m < N_STAGES; ++m) sl += lam[(int64_t)(NR * m + R_H) * ld + s];
-            hes[(int64_t)(NHS * N_STAGES) * ld + s] = -P.u_max * M_PI * 0.5 * sl;
-        }
-        if (part) {
-#pragma unroll
-            for (int j = 0; j < NV; ++j) {
-                if (has_lo(j)) blog += log(in.q[j] - (j == LT ? P.T_lo / P.sT : 0.0));
-                if (has_hi(j)) blog += log(P.T_hi / P.sT - in.q[j]);
-            }
+            for (int k = 0; k < 4; ++k) L.above[k] = lam[(int64_t)(NR * (n + 1) + 7 + k) * ld + s];
+            L.above[4] = lam[(int64_t)(NR * (n + 1) + R_E) * ld + s];
         }
     }
+    stage_eval(P, in, WH ? &L : nullptr, em);
+    if (WH && n == 0) {
+        // the scenario's share of d-d: -u_max pi / 2 * sum_n lambda_hydraulic
+        double sl = 0.0;
+#pragma unroll
+        for (int m = 0; m < N_STAGES; ++m) sl += lam[(int64_t)(NR * m + R_H) * ld + s];
+        hes[(int64_t)(NHS * N_STAGES) * ld + s] = -P.u_max * M_PI * 0.5 * sl;
+    }
     if (part) {
-        double v[3] = {em.asum, em.amax, blog};
-        const int ops[3] = {RSUM, RMAX, RSUM};
-        block_reduce_store<3>(v, ops, part, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            if (has_lo(j)) blog += log(in.q[j] - (j == LT ? P.T_lo / P.sT : 0.0));
+            if (has_hi(j)) blog += log(P.T_hi / P.sT - in.q[j]);
+        }
+        const double v[3] = {em.asum, em.amax, blog};
+        store_partials<3>(v, part, ld, s, n);
     }
 }
 

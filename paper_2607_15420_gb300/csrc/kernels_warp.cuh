@@ -58,15 +58,16 @@ __device__ inline double recip(double a) {
 __device__ inline float recip(float a) { return 1.0f / a; }
 
 template <class T>
-__global__ void __launch_bounds__(32 * WPB_F) factor_warp_kernel(int S, int64_t ld, const double* __restrict__ jac,
-                                                                 T* __restrict__ LU, unsigned char* __restrict__ piv,
-                                                                 T* __restrict__ G, int* __restrict__ sing,
-                                                                 int* __restrict__ count, double pivtol) {
+__global__ void __launch_bounds__(32 * WPB_F) factor_warp_kernel(int S, int64_t ld, const BView b,
+                                                                 const double* __restrict__ jac, T* __restrict__ LU,
+                                                                 unsigned char* __restrict__ piv, T* __restrict__ G,
+                                                                 int* __restrict__ sing, double pivtol) {
     __shared__ T sA[WPB_F][NV][PADA];
     __shared__ T sG[WPB_F][NV][NABV];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * WPB_F + warp;
-    if (s >= S) return;    // whole warps leave together; no block-level barriers below
+    // whole warps leave together; no block-level barriers below
+    if (live_prob(b, s, S, PS_ACT) < 0) return;
     T(*A)[PADA] = sA[warp];
     T(*Gp)[NABV] = sG[warp];
     int singular = 0;
@@ -176,10 +177,7 @@ __global__ void __launch_bounds__(32 * WPB_F) factor_warp_kernel(int S, int64_t 
         for (int e = lane; e < NV * NV; e += 32) Ln[e] = A[e / NV][e % NV];
         __syncwarp();
     }
-    if (lane == 0) {
-        sing[s] = singular;
-        if (singular) atomicAdd(count, 1);
-    }
+    if (lane == 0) sing[s] = singular;
 }
 
 // stage an LU block (contiguous in global memory) into shared memory, coalesced
@@ -243,22 +241,23 @@ __device__ inline T lu_apply_t_warp(const T (*A)[PADL], const unsigned char* pv,
 
 // J_s x = r (NRHS right-hand sides; a null r[k] means b = dc/dd), one warp per scenario
 template <class T, int NRHS>
-__global__ void __launch_bounds__(32 * WPB_S) solve_warp_kernel(const Params P, int S, int64_t ld,
+__global__ void __launch_bounds__(32 * WPB_S) solve_warp_kernel(const Params P, int S, int64_t ld, const BView b,
                                                                 const double* __restrict__ jac, const T* __restrict__ LU,
                                                                 const unsigned char* __restrict__ piv,
-                                                                const T* __restrict__ G, const double* x_d,
+                                                                const T* __restrict__ G, const double* x,
                                                                 const double* r0, const double* r1, double* o0,
                                                                 double* o1) {
     __shared__ T sL[WPB_S][NV][PADL];
     __shared__ unsigned char sP[WPB_S][NV + 2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * WPB_S + warp;
-    if (s >= S) return;
+    const int pr = live_prob(b, s, S, PS_ACT);
+    if (pr < 0) return;
     T(*A)[PADL] = sL[warp];
     unsigned char* pv = sP[warp];
     const double* rr[2] = {r0, r1};
     double* oo[2] = {o0, o1};
-    const T bval = (T)(-P.u_max * M_PI * 0.5 * x_d[0]);
+    const T bval = (T)(-P.u_max * M_PI * 0.5 * x[(int64_t)NSC * ld + pr]);   // b = dc/dd of the problem
     const bool row = lane < NV;
     T y[NRHS];
 #pragma unroll
@@ -313,7 +312,8 @@ __global__ void __launch_bounds__(32 * WPB_S) solve_warp_kernel(const Params P, 
 
 // J_s^T v = g, one warp per scenario; g and out in primal layout (no d)
 template <class T>
-__global__ void __launch_bounds__(32 * WPB_S) solve_t_warp_kernel(int S, int64_t ld, const double* __restrict__ jac,
+__global__ void __launch_bounds__(32 * WPB_S) solve_t_warp_kernel(int S, int64_t ld, const BView b,
+                                                                  const double* __restrict__ jac,
                                                                   const T* __restrict__ LU,
                                                                   const unsigned char* __restrict__ piv,
                                                                   const double* __restrict__ g, double* out) {
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(32 * WPB_S) solve_t_warp_kernel(int S, int64_t
     __shared__ unsigned char sP[WPB_S][NV + 2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * WPB_S + warp;
-    if (s >= S) return;
+    if (live_prob(b, s, S, PS_ACT) < 0) return;
     T(*A)[PADL] = sL[warp];
     unsigned char* pv = sP[warp];
     const bool row = lane < NV;

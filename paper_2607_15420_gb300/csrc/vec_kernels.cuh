@@ -1,0 +1,456 @@
+// vec_kernels.cuh -- interior-point vector kernels (A5-A7) over one or many problems.
+//
+// One thread per (scenario slot, stage): grid (ceil(S / 128), N_STAGES).  Every scalar of
+// the method (mu, tau, step sizes, delta_w, the diameter d and its step) is per problem:
+// scalars from ps (BView), d and its step from the problem's d slot [NSC * ld + p] of
+// the primal vectors.  Reductions store per-thread partials (store_partials) that
+// chunk_reduce_kernel + problem_reduce_kernel combine per problem in a fixed order.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace absorber {
+
+// Schur: r_d and S_d per problem; PS_BASE: 1 if the problem starts from the base states
+enum PsExtra { PS_RD = PS_COUNT, PS_SD, PS_BASE, PS_NFIELDS };
+
+__device__ inline double lo_of(const Params& P, int j) { return j == LT ? P.T_lo / P.sT : 0.0; }
+__device__ inline double hi_of(const Params& P, int /*j*/) { return P.T_hi / P.sT; }
+
+struct RedOps {
+    int op[12];
+};
+
+// J^T lambda for the stage's unknowns and the optimality-error partials:
+// [0] max |J^T l - zL + zU|, [1] sum |lambda|, [2] sum |zL| + |zU|, [3] max and [4] min
+// complementarity product over bounded unknowns, [5] the stage's hydraulic multiplier
+__global__ void __launch_bounds__(128) dual_kernel(const Params P, int S, int64_t ld, const BView b,
+                                                   const double* __restrict__ jac, const double* __restrict__ lam,
+                                                   const double* __restrict__ x, const double* __restrict__ zL,
+                                                   const double* __restrict__ zU, double* __restrict__ jtl,
+                                                   double* part) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (live_prob(b, s, S, PS_ACT) < 0) return;
+    double v[6] = {0.0, 0.0, 0.0, -INFINITY, INFINITY, 0.0};
+    double g[NV];
+    jt_stage(ld, jac, lam, s, n, g);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        jtl[o] = g[j];
+        const double zl = zL[o], zu = zU[o];
+        const double r = fabs(g[j] - zl + zu);
+        v[0] = (r > v[0] || r != r) ? r : v[0];
+        v[1] += fabs(lam[o]);
+        v[2] += fabs(zl) + fabs(zu);
+        const double xv = x[o];
+        if (has_lo(j)) {
+            const double cp = zl * (xv - lo_of(P, j));
+            v[3] = fmax(v[3], cp);
+            v[4] = fmin(v[4], cp);
+        }
+        if (has_hi(j)) {
+            const double cp = zu * (hi_of(P, j) - xv);
+            v[3] = fmax(v[3], cp);
+            v[4] = fmin(v[4], cp);
+        }
+    }
+    v[5] = lam[(int64_t)(NR * n + R_H) * ld + s];
+    store_partials<6>(v, part, ld, s, n);
+}
+
+// barrier diagonal Sigma and right-hand sides r_z = -(J^T l - mu/sl + mu/su), r_c = -c
+__global__ void __launch_bounds__(128) rhs_kernel(const Params P, int S, int64_t ld, const BView b,
+                                                  const double* __restrict__ x, const double* __restrict__ zL,
+                                                  const double* __restrict__ zU, const double* __restrict__ jtl,
+                                                  const double* __restrict__ c, double* __restrict__ sig,
+                                                  double* __restrict__ rz, double* __restrict__ rc) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    const int p = live_prob(b, s, S, PS_ACT);
+    if (p < 0) return;
+    const double mu = psv(b, PS_MU, p);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        const double xv = x[o];
+        double sg = 0.0, gb = 0.0;
+        if (has_lo(j)) {
+            const double sl = xv - lo_of(P, j);
+            sg += zL[o] / sl;
+            gb -= mu / sl;
+        }
+        if (has_hi(j)) {
+            const double su = hi_of(P, j) - xv;
+            sg += zU[o] / su;
+            gb += mu / su;
+        }
+        sig[o] = sg;
+        rz[o] = -(jtl[o] + gb);
+        rc[o] = -c[o];
+    }
+}
+
+// Schur partial sums with H = W + Sigma (W optional): [0] q^T H q, [1] q^T q,
+// [2] q^T (r - H p), [3] q^T p, [4] the scenario's d-d Hessian entry, [5] singular flag
+__global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BView b, const double* __restrict__ hes,
+                                                    const double* __restrict__ sig, bool use_w,
+                                                    const double* __restrict__ p, const double* __restrict__ q,
+                                                    const double* __restrict__ r, const int* __restrict__ sing,
+                                                    double* part) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (live_prob(b, s, S, PS_ACT) < 0) return;
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double hq[NV];
+    hv_stage(ld, hes, sig, 0.0, use_w, q, s, n, hq);
+    double hp[NV];
+    if (p) hv_stage(ld, hes, sig, 0.0, use_w, p, s, n, hp);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        const double qj = q[o];
+        v[0] += qj * hq[j];
+        v[1] += qj * qj;
+        if (r) v[2] += qj * (r[o] - (p ? hp[j] : 0.0));
+        if (p) v[3] += qj * p[o];
+    }
+    if (n == 0) {
+        if (use_w) v[4] = hes[(int64_t)(NHS * N_STAGES) * ld + s];
+        if (sing) v[5] = (double)sing[s];
+    }
+    store_partials<6>(v, part, ld, s, n);
+}
+
+// dz = p - q dd ;  g = r - (W + Sigma + dw I) dz ;  dd, dw of the slot's problem
+__global__ void __launch_bounds__(128) dz_kernel(int S, int64_t ld, const BView b, const double* __restrict__ hes,
+                                                 const double* __restrict__ sig, bool use_w,
+                                                 const double* __restrict__ p, const double* __restrict__ q,
+                                                 const double* __restrict__ r, double* dz, double* __restrict__ g) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    const int pr = live_prob(b, s, S, PS_ACT);
+    if (pr < 0) return;
+    const double dd = dz[(int64_t)NSC * ld + pr];
+    const double dw = b.ps ? psv(b, PS_DW, pr) : 0.0;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        dz[o] = p[o] - q[o] * dd;
+    }
+    double h[NV];
+    hv_stage(ld, hes, sig, dw, use_w, dz, s, n, h);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        g[o] = r[o] - h[j];
+    }
+}
+
+// residual of the full KKT system: rho_z = r_z - (H dz + J^T dl), rho_c = r_c - (J dz + b dd).
+// partials: [0] max|rho_z|, [1] max|rho_c|, [2] the stage's hydraulic dl, [3] max|r_z|, [4] max|r_c|
+__global__ void __launch_bounds__(128) kkt_residual_kernel(int S, int64_t ld, const BView b,
+                                                           const double* __restrict__ jac,
+                                                           const double* __restrict__ hes,
+                                                           const double* __restrict__ sig, bool use_w,
+                                                           const double* __restrict__ dz, const double* __restrict__ dl,
+                                                           const double* __restrict__ rz, const double* __restrict__ rc,
+                                                           double* __restrict__ rhoz, double* __restrict__ rhoc,
+                                                           double* part) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    const int pr = live_prob(b, s, S, PS_ACT);
+    if (pr < 0) return;
+    const double dd = dz[(int64_t)NSC * ld + pr];
+    const double dw = b.ps ? psv(b, PS_DW, pr) : 0.0;
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double h[NV], jt[NV], jv[NR];
+    hv_stage(ld, hes, sig, dw, use_w, dz, s, n, h);
+    jt_stage(ld, jac, dl, s, n, jt);
+    jv_stage(ld, jac, dz, dd, s, n, jv);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        const double a = rz[o] - (h[j] + jt[j]);
+        const double c = rc[o] - jv[j];
+        rhoz[o] = a;
+        rhoc[o] = c;
+        v[0] = fmax(v[0], fabs(a));
+        v[1] = fmax(v[1], fabs(c));
+        v[3] = fmax(v[3], fabs(rz[o]));
+        v[4] = fmax(v[4], fabs(rc[o]));
+        if (a != a || c != c) v[0] = NAN;
+    }
+    v[2] = dl[(int64_t)(NR * n + R_H) * ld + s];
+    store_partials<5>(v, part, ld, s, n);
+}
+
+// bound-multiplier steps and step-size limits (mu, tau of the problem):
+// [0] min primal ratio (alpha_max), [1] min dual ratio (alpha_z),
+// [2] barrier gradient . dz, [3] max |dz| / (1 + |z|)
+__global__ void __launch_bounds__(128) step_kernel(const Params P, int S, int64_t ld, const BView b,
+                                                   const double* __restrict__ x, const double* __restrict__ dz,
+                                                   const double* __restrict__ zL, const double* __restrict__ zU,
+                                                   double* __restrict__ dzL, double* __restrict__ dzU, double* part) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    const int pr = live_prob(b, s, S, PS_ACT);
+    if (pr < 0) return;
+    const double mu = psv(b, PS_MU, pr), tau = psv(b, PS_TAU, pr);
+    double v[4] = {1.0, 1.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        const double xv = x[o], d = dz[o];
+        v[3] = fmax(v[3], fabs(d) / (1.0 + fabs(xv)));
+        if (d != d) v[3] = NAN;
+        if (has_lo(j)) {
+            const double sl = xv - lo_of(P, j);
+            const double z = zL[o];
+            const double dzl = mu / sl - z - (z / sl) * d;
+            dzL[o] = dzl;
+            if (d < 0.0) v[0] = fmin(v[0], -tau * sl / d);
+            if (dzl < 0.0) v[1] = fmin(v[1], -tau * z / dzl);
+            v[2] += (-mu / sl) * d;
+        } else {
+            dzL[o] = 0.0;
+        }
+        if (has_hi(j)) {
+            const double su = hi_of(P, j) - xv;
+            const double z = zU[o];
+            const double dzu = mu / su - z + (z / su) * d;
+            dzU[o] = dzu;
+            if (d > 0.0) v[0] = fmin(v[0], tau * su / d);
+            if (dzu < 0.0) v[1] = fmin(v[1], -tau * z / dzu);
+            v[2] += (mu / su) * d;
+        } else {
+            dzU[o] = 0.0;
+        }
+    }
+    store_partials<4>(v, part, ld, s, n);
+}
+
+// primal fraction-to-the-boundary limit of a direction (problems flagged PS_LSACT)
+__global__ void __launch_bounds__(128) ftb_kernel(const Params P, int S, int64_t ld, const BView b,
+                                                  const double* __restrict__ x, const double* __restrict__ dz,
+                                                  double* part) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    const int pr = live_prob(b, s, S, PS_LSACT);
+    if (pr < 0) return;
+    const double tau = psv(b, PS_TAU, pr);
+    double v[1] = {1.0};
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        const double xv = x[o], d = dz[o];
+        if (has_lo(j) && d < 0.0) v[0] = fmin(v[0], -tau * (xv - lo_of(P, j)) / d);
+        if (has_hi(j) && d > 0.0) v[0] = fmin(v[0], tau * (hi_of(P, j) - xv) / d);
+        if (d != d) v[0] = NAN;
+    }
+    store_partials<1>(v, part, ld, s, n);
+}
+
+// accept the step of the problems flagged PS_ACT, then the kappa_Sigma safeguard on the
+// bound multipliers
+__global__ void __launch_bounds__(128) accept_kernel(const Params P, int S, int64_t ld, const BView b, double ksig,
+                                                     double* __restrict__ x, const double* __restrict__ dz,
+                                                     double* __restrict__ lam, const double* __restrict__ dl,
+                                                     double* __restrict__ zL, const double* __restrict__ dzL,
+                                                     double* __restrict__ zU, const double* __restrict__ dzU) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    const int pr = live_prob(b, s, S, PS_ACT);
+    if (pr < 0) return;
+    const double alpha = psv(b, PS_ALPHA, pr), alpha_z = psv(b, PS_ALPHAZ, pr), mu = psv(b, PS_MU, pr);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        const double xv = x[o] + alpha * dz[o];
+        x[o] = xv;
+        lam[o] += alpha * dl[o];
+        if (has_lo(j)) {
+            const double sl = xv - lo_of(P, j);
+            const double z = zL[o] + alpha_z * dzL[o];
+            zL[o] = fmin(fmax(z, mu / (ksig * sl)), ksig * mu / sl);
+        }
+        if (has_hi(j)) {
+            const double su = hi_of(P, j) - xv;
+            const double z = zU[o] + alpha_z * dzU[o];
+            zU[o] = fmin(fmax(z, mu / (ksig * su)), ksig * mu / su);
+        }
+    }
+}
+
+// the problems' own step of d: x[d_p] += alpha_p dz[d_p]   (one thread per problem)
+__global__ void dstep_kernel(int64_t ld, const BView b, double* __restrict__ x, const double* __restrict__ dz) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.NP || psv(b, PS_ACT, p) == 0.0) return;
+    const int64_t o = (int64_t)NSC * ld + p;
+    x[o] += psv(b, PS_ALPHA, p) * dz[o];
+}
+
+// starting point: every stage copies the inlet streams (or, with base and the problem's
+// PS_BASE set, the stage states of problem p's expected-value solution at
+// base[v * ldb + p]), the slack from the hydraulic row at the problem's d (already in
+// x's d slot); pushed into the bounds
+__global__ void __launch_bounds__(128) init_kernel(const Params P, int S, int64_t ld, const BView b,
+                                                   const double* __restrict__ feed, const double* __restrict__ base,
+                                                   int64_t ldb, double push, double frac, double* __restrict__ x,
+                                                   double* __restrict__ zL, double* __restrict__ zU,
+                                                   double* __restrict__ lam) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    const int pr = live_prob(b, s, S, PS_ACT);
+    if (pr < 0) return;
+    const double d = x[(int64_t)NSC * ld + pr];
+    double q[NV];
+    if (base && (!b.ps || psv(b, PS_BASE, pr) != 0.0)) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) q[j] = base[(int64_t)(NV * n + j) * ldb + pr];
+    } else {
+#pragma unroll
+        for (int l = 0; l < 9; ++l) q[LX + l] = feed[(int64_t)(F_XIN + l) * ld + s] / P.sx[l];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) q[LY + j] = feed[(int64_t)(F_Y0 + j) * ld + s] / P.sy[j];
+        q[LL] = feed[(int64_t)F_LIN * ld + s];
+        q[LV] = feed[(int64_t)F_V0 * ld + s];
+        q[LT] = 0.5 * (feed[(int64_t)F_T0 * ld + s] + feed[(int64_t)F_TIN * ld + s]) / P.sT;
+#pragma unroll
+        for (int r = 0; r < 5; ++r) q[LE + r] = 0.0;
+    }
+    q[LS] = P.u_max * M_PI * d * d * 0.25 - q[LV] * P.R * (P.sT * q[LT]) / feed[(int64_t)F_P * ld + s];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        double v = q[j];
+        const double lo = lo_of(P, j), hi = hi_of(P, j);
+        if (has_lo(j)) {
+            const double w = has_hi(j) ? frac * (hi - lo) : INFINITY;
+            v = fmax(v, lo + fmin(push * fmax(1.0, fabs(lo)), w));
+        }
+        if (has_hi(j)) {
+            const double w = has_lo(j) ? frac * (hi - lo) : INFINITY;
+            v = fmin(v, hi - fmin(push * fmax(1.0, fabs(hi)), w));
+        }
+        x[o] = v;
+        zL[o] = has_lo(j) ? 1.0 : 0.0;
+        zU[o] = has_hi(j) ? 1.0 : 0.0;
+        lam[o] = 0.0;
+    }
+}
+
+// z-part of the least-squares multiplier right-hand side, zL - zU; `one` = 1 (Sigma = I)
+__global__ void ls_rhs_kernel(int S, int64_t ld, const BView b, const double* __restrict__ zL,
+                              const double* __restrict__ zU, double* __restrict__ rz, double* __restrict__ one) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (live_prob(b, s, S, PS_ACT) < 0) return;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        rz[o] = zL[o] - zU[o];
+        one[o] = 1.0;
+    }
+}
+
+// y = a x + c y over the per-scenario part; a = ps[afield][p] when afield >= 0.
+// flag selects which problems take part (PS_ACT or PS_LSACT).  In place (x == y) is allowed.
+__global__ void axpby_kernel(int S, int64_t ld, const BView b, int flag, int afield, double a, const double* xv,
+                             double c, double* y) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    const int pr = live_prob(b, s, S, flag);
+    if (pr < 0) return;
+    const double aa = afield >= 0 ? psv(b, afield, pr) : a;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        y[o] = c == 0.0 ? aa * xv[o] : aa * xv[o] + c * y[o];   // y is not read when c = 0
+    }
+}
+
+// y += x on the per-scenario part and, with d_slots, on the problems' d slots
+__global__ void axpy_d_kernel(int S, int64_t ld, const BView b, const double* __restrict__ xv,
+                              double* __restrict__ y, bool d_slots) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (d_slots && n == 0 && s < b.NP && (!b.ps || psv(b, PS_ACT, s) != 0.0))
+        y[(int64_t)NSC * ld + s] += xv[(int64_t)NSC * ld + s];
+    if (live_prob(b, s, S, PS_ACT) < 0) return;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        y[o] += xv[o];
+    }
+}
+
+__global__ void max_abs_kernel(int S, int64_t ld, const BView b, const double* __restrict__ v, double* part) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (live_prob(b, s, S, PS_ACT) < 0) return;
+    double m[1] = {0.0};
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const double a = fabs(v[(int64_t)(NV * n + j) * ld + s]);
+        m[0] = (a > m[0] || a != a) ? a : m[0];
+    }
+    store_partials<1>(m, part, ld, s, n);
+}
+
+// ---- reductions per problem ---------------------------------------------------------
+// chunk c covers elements [i0, i1) of problem p (element i: stage i / S_p, slot off_p +
+// i % S_p); one block per chunk, fixed-order tree; out[k * nchunk + c]
+__global__ void __launch_bounds__(256) chunk_reduce_kernel(const double* __restrict__ part, int64_t ld, int K,
+                                                           const RedOps ops, const int* __restrict__ ch,
+                                                           int nchunk, const double* __restrict__ ps, int NP,
+                                                           int flag, double* __restrict__ out) {
+    __shared__ double sm[256];
+    const int c = blockIdx.x;
+    const int p = ch[5 * c + 0], off = ch[5 * c + 1], Sp = ch[5 * c + 2], i0 = ch[5 * c + 3], i1 = ch[5 * c + 4];
+    const bool live = !ps || ps[(int64_t)flag * NP + p] != 0.0;
+    const int64_t plane = (int64_t)N_STAGES * ld;
+    for (int k = 0; k < K; ++k) {
+        const int op = ops.op[k];
+        double a = red_id(op);
+        if (live) {
+            for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x) {
+                const int n = i / Sp, s = off + i % Sp;
+                a = red_op(op, a, part[(int64_t)k * plane + (int64_t)n * ld + s]);
+            }
+        }
+        sm[threadIdx.x] = a;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) sm[threadIdx.x] = red_op(op, sm[threadIdx.x], sm[threadIdx.x + o]);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[(int64_t)k * nchunk + c] = sm[0];
+        __syncthreads();
+    }
+}
+
+// per problem: combine its chunks in order; out[k * NP + p]
+__global__ void problem_reduce_kernel(const double* __restrict__ cout, int nchunk, int K, const RedOps ops,
+                                      const int* __restrict__ pchunk, int NP, double* __restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NP) return;
+    for (int k = 0; k < K; ++k) {
+        double a = red_id(ops.op[k]);
+        for (int c = pchunk[p]; c < pchunk[p + 1]; ++c) a = red_op(ops.op[k], a, cout[(int64_t)k * nchunk + c]);
+        out[(int64_t)k * NP + p] = a;
+    }
+}
+
+// dd_p = (r_d - (beta - dw qp)) / S_d from the Schur sums red[2][p], red[3][p]; into the
+// problem's d slot of dz
+__global__ void finalize_dd_kernel(int64_t ld, const BView b, const double* __restrict__ red, double* __restrict__ dz) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.NP || psv(b, PS_ACT, p) == 0.0) return;
+    const double beta = red[2 * (int64_t)b.NP + p], qp = red[3 * (int64_t)b.NP + p];
+    const double dw = psv(b, PS_DW, p);
+    dz[(int64_t)NSC * ld + p] = (psv(b, PS_RD, p) - (beta - dw * qp)) / psv(b, PS_SD, p);
+}
+
+}  // namespace absorber
