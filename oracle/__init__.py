@@ -17,6 +17,8 @@ Plain, slow, FP64, numpy/scipy:
   checks.py  independent checks: complex-step Jacobians, conservation of elements,
              charge and enthalpy, the square MESH system by Newton, the closed-form
              optimal diameter, E_0 from the definitions
+  mlp.py     the warm-start network (3 -> 256 -> 256 -> 256 -> 440, GELU, bfloat16
+             weights): forward pass, loss, reverse-mode gradient, Adam step
 
 Pins (tests/test_oracle_*.py, -m "not gpu"): the paper's printed problem size at
 |Omega| = 5000; AD against closed forms and against complex step; the Hessian against
@@ -24,6 +26,9 @@ finite differences of complex-step gradients; Schur solve against the monolithic
 LDL^T; inertia against eigenvalue signs; at the returned point E_0 <= 1e-8, d* equal
 to max sqrt(4 V R T / (pi u_max P)), one active hydraulic row, C/H/N/O/charge and
 enthalpy conserved, the square MESH system's Newton root, identical-scenario symmetry,
-a brute-force diameter sweep.  Parity unpinned: agreement with the paper's own numbers
+a brute-force diameter sweep; for mlp.py, bfloat16 rounding against hand-worked
+ties, GELU against Phi(+-1), the gradient against central finite differences, the
+zero-weight and single-path networks and the first Adam steps against closed forms.
+Parity unpinned: agreement with the paper's own numbers
 (its constants and scenario data are not published), and uniqueness of the MESH root.
 """
