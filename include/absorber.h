@@ -134,7 +134,7 @@ abs_status abs_scenario_pattern(int32_t* nnzJ_scen, int32_t* nnzH_scen, int32_t*
 
 /* Host-only: sizeof of the ABI structs, for binding checks.  which: 0 abs_params,
  * 1 abs_sizes, 2 abs_kkt_diag, 3 abs_inertia, 4 abs_solve_info, 5 abs_options,
- * 6 abs_result; -1 for an unknown index. */
+ * 6 abs_result, 7 abs_train_options; -1 for an unknown index. */
 int64_t abs_struct_size(int which);
 
 /* Per-scenario sparsity patterns (host arrays), identical for every scenario.
@@ -231,10 +231,17 @@ typedef struct abs_options {
     int32_t max_ls;        /* maximum line-search trials per iteration */
     int32_t verbose;       /* 1: print one line per iteration to stdout */
     int32_t profile;       /* 1: time the hot kernels with CUDA events (abs_result.kernel_*) */
-    int32_t init;          /* 0: expected-value start (S > 1, see ipm_solve), 1: inlet copy */
+    int32_t init;          /* 0: expected-value start (S > 1, see ipm_solve), 1: inlet copy,
+                              2: one expected-value start shared by every problem of a
+                              batch (the mean over all its scenarios) */
     int32_t soc_max;       /* second-order corrections per iteration (0 disables) */
     double kappa_soc;      /* required theta reduction between corrections */
     double obj_scaling;    /* the solver minimises obj_scaling * d; <= 0 means S */
+    double warm_mu_init;   /* ipm_solve_learned: barrier parameter of the learned start */
+    double warm_bound_push;/* ipm_solve_learned: bound push and fraction at the learned start */
+    int32_t warm_multipliers; /* ipm_solve_learned: 0 least-squares estimate at the learned
+                                 point, 1 the network's multipliers */
+    int32_t reserved_opt;
 } abs_options;
 
 void abs_default_options(abs_options* o);
@@ -260,6 +267,11 @@ typedef struct abs_result {
     int32_t soc_steps;           /* second-order correction steps taken */
     int32_t fp64_fallbacks;      /* FP32 iterations refactored in FP64 (refinement stalled) */
     double base_ms;              /* host time of the expected-value start solve */
+    int32_t warm_status;         /* ipm_solve_learned: 1 learned start used, 0 rejected */
+    int32_t reserved;
+    double warm_ms;              /* ipm_solve_learned: host time of prediction + acceptance test */
+    double warm_E0, cold_E0;     /* E_0 at the learned start and at the inlet-copy start */
+    double warm_theta, cold_theta;  /* constraint violation ||c||_1 at the same two starts */
 } abs_result;
 
 /* Diagnostic: measured throughput of dependent-free fused multiply-adds on the current
@@ -287,6 +299,22 @@ abs_status ipm_solve(abs_problem* h, const abs_options* opt, const double* warm_
                      const double* warm_y, abs_result* res, double* x_out, double* y_out,
                      abs_stream_t stream);
 
+/* A handle holding P independent design problems side by side: problem q has sizes[q]
+ * scenarios, and its feeds are columns [off_q, off_q + sizes[q]) of feeds (off_q = the
+ * sum of the earlier sizes).
+ *   feeds  host or device, [18][sum(sizes)] as in absorber_create.
+ *   sizes  host, P counts >= 1.
+ * Vectors of a batch handle use S = sum(sizes) and ld = S rounded up to 32; the primal
+ * vectors hold the P diameters in their last ld entries (problem q's at 220*ld + q).
+ * eval_grad_jac_hess evaluates every problem at its own diameter; kkt_factor,
+ * kkt_solve and ipm_solve need single-problem handles (ipm_solve_batch solves a batch
+ * handle).  Synchronous.  Errors as absorber_create. */
+abs_status absorber_create_batched(const abs_params* p, const double* feeds, const int64_t* sizes,
+                                   int32_t P, abs_problem** out);
+
+/* Number of problems a handle holds (1 for absorber_create; 0 for NULL). */
+int32_t absorber_num_problems(const abs_problem* h);
+
 /* Batched interior-point solve of P independent design problems of form (10), each
  * with its own scenario count, feeds, diameter, barrier parameter, filter and
  * inertia-correction state (the batching form of the scenario workflow: many design
@@ -312,6 +340,119 @@ abs_status ipm_solve(abs_problem* h, const abs_options* opt, const double* warm_
  * error of the batch as a whole (bad argument, CUDA error).  Synchronous. */
 abs_status ipm_solve_batched(abs_problem** probs, int32_t P, const abs_options* opt,
                              abs_result* res, double** x_out, abs_stream_t stream);
+
+/* The batched solve of the P problems of a handle from absorber_create_batched (or of a
+ * single-problem handle, P = 1), with the method of ipm_solve_batched.
+ *   res    host array of absorber_num_problems(h) results.
+ *   x_out  device primal vector in the batch handle's layout, or NULL.
+ *   y_out  device row vector, or NULL: each problem's multipliers of its unscaled
+ *          problem min d.
+ * Returns ABS_OK when the batch ran (outcomes in res[q].status).  Synchronous. */
+abs_status ipm_solve_batch(abs_problem* h, const abs_options* opt, abs_result* res,
+                           double* x_out, double* y_out, abs_stream_t stream);
+
+/* ---- learned warm start ------------------------------------------------------------
+ * The paper solves every instance from a fixed starting point; this is the learned-
+ * warm-start form of its workflow: a network, trained on the GPU from solutions of
+ * single-scenario instances of problem (10), predicts the starting point of a new
+ * instance, which the interior-point method then accepts or rejects.
+ *
+ * The network (abs_mlp): 3 -> 256 -> 256 -> 256 -> 440 perceptron with GELU
+ * (x Phi(x)) activations, bfloat16 weights and FP32 activations and sums:
+ *   a0 = (X - in_shift) / in_scale;  a_l = gelu(a_{l-1} W_l^T + b_l), l = 1..3;
+ *   yhat = a3 W4^T + b4;  prediction = yhat * out_scale + out_shift.
+ * Inputs per scenario: V0 (flue-gas flow), y_CO2,0 (its CO2 fraction), d.  Outputs: the
+ * scenario's 220 unknowns (this header's per-scenario order, with the 13 species
+ * fractions xt, yt of each stage as natural logarithms) then its 220 row multipliers
+ * (of the unscaled problem).  Training minimises
+ *   loss = sum (yhat - (Y - out_shift) / out_scale)^2 / (2 n 440)
+ * with Adam (Kingma & Ba 2015); W_l enter every product rounded to bfloat16 (nearest,
+ * ties to even) from FP32 master weights.  Parameters, flat (ABS_MLP_PARAMS floats):
+ * W1 [256][3], b1, W2 [256][256], b2, W3 [256][256], b3, W4 [440][256], b4.
+ * Device arrays X are [n][3] and Y [n][440] floats, row-major.  A network is not
+ * thread-safe; its calls use the current device. */
+#define ABS_MLP_IN 3
+#define ABS_MLP_HIDDEN 256
+#define ABS_MLP_OUT 440
+#define ABS_MLP_PARAMS 245688
+typedef struct abs_mlp abs_mlp;
+
+/* New network: Glorot-uniform weights from seed (splitmix64 draws), zero biases,
+ * identity normalisation.  Errors: ABS_ERR_ARG, ABS_ERR_OOM, ABS_ERR_CUDA. */
+abs_status abs_mlp_create(uint64_t seed, abs_mlp** out);
+void abs_mlp_destroy(abs_mlp* net);
+const char* abs_mlp_last_error(const abs_mlp* net);
+
+/* Host copies of the FP32 master parameters (ABS_MLP_PARAMS floats).  set_params
+ * refreshes the bfloat16 copies and resets Adam's moments and step count.  Synchronous. */
+abs_status abs_mlp_set_params(abs_mlp* net, const float* params);
+abs_status abs_mlp_get_params(const abs_mlp* net, float* params);
+
+/* Normalisation constants (host, 3 + 3 + 440 + 440 doubles; scales > 0; stored as
+ * float).  fit_normalization sets them to the per-column mean and standard deviation
+ * of device data X [n][3], Y [n][440] (scale 1 for a column with no spread). */
+abs_status abs_mlp_set_normalization(abs_mlp* net, const double* in_shift, const double* in_scale,
+                                     const double* out_shift, const double* out_scale);
+abs_status abs_mlp_get_normalization(const abs_mlp* net, double* in_shift, double* in_scale,
+                                     double* out_shift, double* out_scale);
+abs_status abs_mlp_fit_normalization(abs_mlp* net, const float* X, const float* Y, int64_t n,
+                                     abs_stream_t stream);
+
+/* Prediction: raw inputs X [n][3] -> raw outputs Y [n][440] (device).  Asynchronous. */
+abs_status abs_mlp_forward(abs_mlp* net, const float* X, int64_t n, float* Y, abs_stream_t stream);
+
+/* Loss of the n pairs (X, Y) (raw, device) and its gradient with respect to the
+ * parameters (device, ABS_MLP_PARAMS floats, or NULL).  *loss: host.  Synchronous. */
+abs_status abs_mlp_loss_grad(abs_mlp* net, const float* X, const float* Y, int64_t n, double* loss,
+                             float* grad, abs_stream_t stream);
+
+typedef struct abs_train_options {
+    int32_t epochs;        /* passes over the data */
+    int32_t batch;         /* rows per Adam step (the last step of an epoch takes the rest) */
+    double lr, lr_final;   /* learning rate, decayed geometrically from lr to lr_final */
+    double beta1, beta2, eps;
+    uint64_t seed;         /* order of the rows in each epoch (Fisher-Yates, splitmix64) */
+} abs_train_options;
+void abs_default_train_options(abs_train_options* o);
+
+/* Train on n pairs (raw, device) with the network's current normalisation: each epoch
+ * visits the rows in a seeded random order in minibatches, one Adam step per batch.
+ * epoch_loss: host, opt->epochs doubles (mean loss of each epoch's batches) or NULL.
+ * Synchronous. */
+abs_status abs_mlp_train(abs_mlp* net, const float* X, const float* Y, int64_t n,
+                         const abs_train_options* opt, double* epoch_loss, abs_stream_t stream);
+
+/* Training pairs from a solved handle (typically a batch of one-scenario problems),
+ * one row per (scenario of a kept problem, diameter copy a = 0..n_aug-1):
+ *   X row = (V0, y_CO2,0 of the scenario, d),  d = d_p (1 + d_spread a / (n_aug - 1))
+ *           with d_p the problem's optimal diameter (x's d slot; copy 0 is d_p itself);
+ *   Y row = (the scenario's 220 entries of x -- species fractions as logarithms,
+ *            hydraulic slacks recomputed at d -- then its 220 entries of y).
+ * The stage states of a scenario do not depend on d (its MESH system is square in
+ * them), so the copies teach the network that; only the slacks follow d.
+ *   x, y   device primal / row vectors of the solved handle (unscaled multipliers, as
+ *          ipm_solve_batch writes them).
+ *   keep   host, one flag per problem (nonzero = use), or NULL for all.
+ *   X, Y   device [rows][3], [rows][440] floats, or NULL to only count.
+ *   rows   host, receives the number of rows.
+ * Synchronous. */
+abs_status abs_mlp_make_dataset(const abs_problem* h, const double* x, const double* y,
+                                const int32_t* keep, int32_t n_aug, double d_spread, float* X,
+                                float* Y, int64_t* rows, abs_stream_t stream);
+
+/* Interior-point solve of a single-problem handle from the network's predicted start
+ * (one network pass at the mean training diameter; its targets do not depend on d):
+ * stage states from the network; d0 solves stationarity in d when every scenario's
+ * largest-volume hydraulic row carries the multiplier warm_mu_init / slack; slacks from
+ * the hydraulic rows at d0; unknowns pushed into their bounds by warm_bound_push and
+ * bound multipliers warm_mu_init / slack; row multipliers from the least-squares
+ * estimate at that point (warm_multipliers = 0) or the network's, scaled onto the same
+ * central path (1).  The start is accepted when its E_0 and ||c||_1 do not exceed those
+ * of the inlet-copy start; the solve then runs from it with mu_init = warm_mu_init,
+ * else from the default start (res.warm_status says which).  Outputs as ipm_solve.
+ * Synchronous. */
+abs_status ipm_solve_learned(abs_problem* h, abs_mlp* net, const abs_options* opt,
+                             abs_result* res, double* x_out, double* y_out, abs_stream_t stream);
 
 /* Newton direction of one interior-point iteration without any allocation.
  *

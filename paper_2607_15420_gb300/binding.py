@@ -69,7 +69,8 @@ class AbsOptions(C.Structure):
                 ("kw_minus", C.c_double), ("kw_plus", C.c_double), ("kw_plus_bar", C.c_double),
                 ("max_ls", C.c_int32), ("verbose", C.c_int32), ("profile", C.c_int32),
                 ("init", C.c_int32), ("soc_max", C.c_int32), ("kappa_soc", C.c_double),
-                ("obj_scaling", C.c_double)]
+                ("obj_scaling", C.c_double), ("warm_mu_init", C.c_double), ("warm_bound_push", C.c_double),
+                ("warm_multipliers", C.c_int32), ("reserved_opt", C.c_int32)]
 
 
 class AbsResult(C.Structure):
@@ -80,7 +81,17 @@ class AbsResult(C.Structure):
                 ("phase_ms", C.c_double * 6), ("kernel_ms", C.c_double * 5),
                 ("kernel_launches", C.c_int32 * 5), ("launches", C.c_int64),
                 ("base_iters", C.c_int32), ("soc_steps", C.c_int32), ("fp64_fallbacks", C.c_int32),
-                ("base_ms", C.c_double)]
+                ("base_ms", C.c_double), ("warm_status", C.c_int32), ("reserved", C.c_int32),
+                ("warm_ms", C.c_double), ("warm_E0", C.c_double), ("cold_E0", C.c_double),
+                ("warm_theta", C.c_double), ("cold_theta", C.c_double)]
+
+
+class AbsTrainOptions(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double), ("lr_final", C.c_double),
+                ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double), ("seed", C.c_uint64)]
+
+
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 3, 256, 440, 245688
 
 KERNELS = ("eval", "eval_trial", "factor", "solve", "solve_t")
 PHASES = ("eval", "factor", "solve", "linesearch", "step", "other")
@@ -112,6 +123,29 @@ EXPORTS = {
                             C.c_void_p, C.c_void_p, C.c_void_p]),
     "ipm_solve_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(AbsOptions), C.POINTER(AbsResult),
                                     C.POINTER(C.c_void_p), C.c_void_p]),
+    "absorber_create_batched": (C.c_int, [C.POINTER(AbsParams), C.c_void_p, C.POINTER(C.c_int64), C.c_int32,
+                                          C.POINTER(C.c_void_p)]),
+    "absorber_num_problems": (C.c_int32, [C.c_void_p]),
+    "ipm_solve_batch": (C.c_int, [C.c_void_p, C.POINTER(AbsOptions), C.POINTER(AbsResult), C.c_void_p, C.c_void_p,
+                                  C.c_void_p]),
+    "abs_mlp_create": (C.c_int, [C.c_uint64, C.POINTER(C.c_void_p)]),
+    "abs_mlp_destroy": (None, [C.c_void_p]),
+    "abs_mlp_last_error": (C.c_char_p, [C.c_void_p]),
+    "abs_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "abs_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "abs_mlp_set_normalization": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "abs_mlp_get_normalization": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "abs_mlp_fit_normalization": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "abs_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "abs_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double),
+                                    C.c_void_p, C.c_void_p]),
+    "abs_default_train_options": (None, [C.POINTER(AbsTrainOptions)]),
+    "abs_mlp_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(AbsTrainOptions),
+                                C.c_void_p, C.c_void_p]),
+    "abs_mlp_make_dataset": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double,
+                                       C.c_void_p, C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
+    "ipm_solve_learned": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(AbsOptions), C.POINTER(AbsResult),
+                                    C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -201,7 +235,7 @@ def kkt_newton_noalloc(params, S, ld, x, jac, hess, sigma, rhs_x, rhs_c, sol_x, 
     return sd.value
 
 
-STRUCTS = [AbsParams, AbsSizes, AbsKKTDiag, AbsInertia, AbsSolveInfo, AbsOptions, AbsResult]
+STRUCTS = [AbsParams, AbsSizes, AbsKKTDiag, AbsInertia, AbsSolveInfo, AbsOptions, AbsResult, AbsTrainOptions]
 
 
 def scenario_pattern():
@@ -335,6 +369,51 @@ class Problem:
         return np.asarray(vals)[:nnz * self.ld].reshape(nnz, self.ld)[:, :self.S].T.copy()
 
 
+class Batch(Problem):
+    """P independent problems in one handle (absorber_create_batched)."""
+
+    def __init__(self, params: dict, feeds_list):
+        sizes = np.array([np.asarray(F).shape[1] for F in feeds_list], dtype=np.int64)
+        feeds = np.ascontiguousarray(np.concatenate([np.asarray(F, dtype=np.float64) for F in feeds_list], axis=1))
+        if feeds.shape[0] != N_FEED:
+            raise ValueError("feeds must be (18, S_q)")
+        self.params = make_params(params)
+        h = C.c_void_p()
+        st = lib().absorber_create_batched(C.byref(self.params), feeds.ctypes.data,
+                                           sizes.ctypes.data_as(C.POINTER(C.c_int64)), len(sizes), C.byref(h))
+        if st != ABS_OK:
+            raise AbsorberError(st, lib().abs_last_error(None).decode())
+        self.h = h
+        self.sizes = AbsSizes()
+        self._check(lib().absorber_sizes(self.h, C.byref(self.sizes)))
+        self.S = self.sizes.S
+        self.ld = self.sizes.ld
+        self.P = int(lib().absorber_num_problems(self.h))
+        self.problem_sizes = sizes
+        self.off = np.concatenate([[0], np.cumsum(sizes)])
+
+    @property
+    def n_primal(self):
+        return NSC * self.ld + self.ld
+
+    def ipm_solve(self, options=None, x_out=None, y_out=None, stream=None):
+        res = (AbsResult * self.P)()
+        self._check(lib().ipm_solve_batch(self.h, C.byref(options) if options is not None else None, res,
+                                          _ptr(x_out), _ptr(y_out), _stream(stream)))
+        return list(res)
+
+    def split(self, v):
+        """flat batch vector -> list of ((S_q, 220), d_q or None) per problem."""
+        v = np.asarray(v)
+        Z = v[:NSC * self.ld].reshape(NSC, self.ld)
+        out = []
+        for q in range(self.P):
+            Zq = Z[:, self.off[q]:self.off[q + 1]].T.copy()
+            dq = float(v[NSC * self.ld + q]) if v.shape[0] > NSC * self.ld else None
+            out.append((Zq, dq))
+        return out
+
+
 def ipm_solve_batched(problems, options=None, x_out=None, stream=None):
     """Solve independent problems as one batch; returns one AbsResult per problem.
 
@@ -353,3 +432,102 @@ def ipm_solve_batched(problems, options=None, x_out=None, stream=None):
     if st != ABS_OK:
         raise AbsorberError(st, lib().abs_last_error(problems[0].h).decode())
     return list(res)
+
+
+def train_options(**kw) -> AbsTrainOptions:
+    o = AbsTrainOptions()
+    lib().abs_default_train_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class MLP:
+    """The warm-start network held by the library (abs_mlp_*)."""
+
+    def __init__(self, seed=1):
+        h = C.c_void_p()
+        st = lib().abs_mlp_create(int(seed), C.byref(h))
+        if st != ABS_OK:
+            raise AbsorberError(st, lib().abs_mlp_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st):
+        if st != ABS_OK:
+            raise AbsorberError(st, lib().abs_mlp_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().abs_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        assert theta.shape == (MLP_PARAMS,)
+        self._check(lib().abs_mlp_set_params(self.h, theta.ctypes.data))
+
+    def get_params(self):
+        out = np.zeros(MLP_PARAMS, dtype=np.float32)
+        self._check(lib().abs_mlp_get_params(self.h, out.ctypes.data))
+        return out
+
+    def set_normalization(self, in_shift, in_scale, out_shift, out_scale):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (in_shift, in_scale, out_shift, out_scale)]
+        self._check(lib().abs_mlp_set_normalization(self.h, *[a.ctypes.data for a in arrs]))
+
+    def get_normalization(self):
+        a = [np.zeros(n) for n in (MLP_IN, MLP_IN, MLP_OUT, MLP_OUT)]
+        self._check(lib().abs_mlp_get_normalization(self.h, *[x.ctypes.data for x in a]))
+        return dict(in_shift=a[0], in_scale=a[1], out_shift=a[2], out_scale=a[3])
+
+    def fit_normalization(self, X, Y, stream=None):
+        self._check(lib().abs_mlp_fit_normalization(self.h, _ptr(X), _ptr(Y), X.shape[0], _stream(stream)))
+
+    def forward(self, X, Y, stream=None):
+        self._check(lib().abs_mlp_forward(self.h, _ptr(X), X.shape[0], _ptr(Y), _stream(stream)))
+
+    def loss_grad(self, X, Y, grad=None, stream=None):
+        loss = C.c_double()
+        self._check(lib().abs_mlp_loss_grad(self.h, _ptr(X), _ptr(Y), X.shape[0], C.byref(loss), _ptr(grad),
+                                            _stream(stream)))
+        return loss.value
+
+    def train(self, X, Y, options=None, stream=None):
+        o = options if options is not None else train_options()
+        hist = np.zeros(o.epochs)
+        self._check(lib().abs_mlp_train(self.h, _ptr(X), _ptr(Y), X.shape[0], C.byref(o), hist.ctypes.data,
+                                        _stream(stream)))
+        return hist
+
+
+def make_dataset(problem, x, y, keep=None, n_aug=1, d_spread=0.0, stream=None):
+    """Training pairs of a solved handle as new device tensors (X [rows][3], Y [rows][440])."""
+    import torch
+    kp = None
+    if keep is not None:
+        keep = np.ascontiguousarray(keep, dtype=np.int32)
+        kp = keep.ctypes.data
+    rows = C.c_int64()
+    problem._check(lib().abs_mlp_make_dataset(problem.h, _ptr(x), _ptr(y), kp, int(n_aug), float(d_spread), None,
+                                              None, C.byref(rows), _stream(stream)))
+    X = torch.zeros((rows.value, MLP_IN), dtype=torch.float32, device="cuda")
+    Y = torch.zeros((rows.value, MLP_OUT), dtype=torch.float32, device="cuda")
+    problem._check(lib().abs_mlp_make_dataset(problem.h, _ptr(x), _ptr(y), kp, int(n_aug), float(d_spread),
+                                              _ptr(X), _ptr(Y), C.byref(rows), _stream(stream)))
+    return X, Y
+
+
+def ipm_solve_learned(problem, net, options=None, x_out=None, y_out=None, stream=None):
+    res = AbsResult()
+    st = lib().ipm_solve_learned(problem.h, net.h, C.byref(options) if options is not None else None, C.byref(res),
+                                 _ptr(x_out), _ptr(y_out), _stream(stream))
+    if st != ABS_OK and res.status == ABS_OK:
+        res.status = st
+    return res

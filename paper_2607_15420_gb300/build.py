@@ -1,4 +1,7 @@
-"""Build the CUDA library in-tree: csrc/absorber_lib.cu -> _lib/libabsorber.so (sm_103a)."""
+"""Build the CUDA library in-tree: csrc/*.cu -> _lib/libabsorber.so (sm_103a).
+
+Each translation unit compiles in its own nvcc process (in parallel); nvcc links the
+objects into the shared library."""
 from __future__ import annotations
 
 import hashlib
@@ -11,10 +14,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libabsorber.so")
-SOURCES = ["absorber_lib.cu"]
+SOURCES = ["absorber_lib.cu", "mlp_lib.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
-         "-Xcompiler", "-O2", "-shared"]
+         "-Xcompiler", "-O2"]
 
 
 def _nvcc():
@@ -42,11 +45,21 @@ def build(force: bool = False, verbose: bool = False) -> str:
     dig = _digest()
     if not force and os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == dig:
         return LIB
-    cmd = [_nvcc(), *ARCH, *FLAGS, "-I", INCLUDE, "-I", CSRC,
-           *[os.path.join(CSRC, s) for s in SOURCES], "-o", LIB + ".tmp"]
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
+        cmd = [_nvcc(), *ARCH, *FLAGS, "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj]
+        if verbose:
+            print(" ".join(cmd))
+        procs.append(subprocess.Popen(cmd))
+        objs.append(obj)
+    failed = [src for src, p in zip(SOURCES, procs) if p.wait() != 0]
+    if failed:
+        raise RuntimeError(f"nvcc failed on {failed}")
+    link = [_nvcc(), *ARCH, "-shared", *objs, "-o", LIB + ".tmp"]
     if verbose:
-        print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
+        print(" ".join(link))
+    subprocess.run(link, check=True)
     os.replace(LIB + ".tmp", LIB)
     with open(stamp, "w") as f:
         f.write(dig)

@@ -294,6 +294,8 @@ struct abs_problem {
     } fac;
     Prof prof;
     int64_t nlaunch = 0;         // kernels launched (every launch is followed by launch_check)
+    float* mlp_x = nullptr;          // learned warm start: network inputs [ld][3] and outputs [ld][440]
+    float* mlp_y = nullptr;
     abs_problem* base = nullptr;     // expected-value sub-problem(s) for the starting point
     abs_problem* batch = nullptr;    // cached batch handle of ipm_solve_batched (on probs[0])
     std::vector<int64_t> batch_key;  // the sizes it was built for
@@ -728,6 +730,8 @@ void abs_default_options(abs_options* o) {
     o->soc_max = 4;
     o->kappa_soc = 0.99;
     o->obj_scaling = 0.0;
+    o->warm_mu_init = 1e-3;
+    o->warm_bound_push = 1e-8;
 }
 
 abs_status absorber_create(const abs_params* p, const double* feeds, const double* prob, int64_t S,
@@ -773,6 +777,8 @@ void absorber_destroy(abs_problem* h) {
     for (auto e : h->prof.pool) cudaEventDestroy(e);
     cudaFree(h->feed);
     cudaFree(h->pid);
+    cudaFree(h->mlp_x);
+    cudaFree(h->mlp_y);
     cudaFree(h->jac);
     cudaFree(h->hes);
     cudaFree(h->vec);
@@ -836,6 +842,7 @@ int64_t abs_struct_size(int which) {
         case 4: return sizeof(abs_solve_info);
         case 5: return sizeof(abs_options);
         case 6: return sizeof(abs_result);
+        case 7: return sizeof(abs_train_options);
         default: return -1;
     }
 }
@@ -850,7 +857,7 @@ abs_status eval_grad_jac_hess(abs_problem* h, const double* x, const double* lam
     if (!h || !x || (hess_vals && !lambda)) return fail(h, ABS_ERR_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;
     const dim3 g = grid2(h);
-    const BView b{nullptr, nullptr, 1};
+    const BView b{h->pid, nullptr, h->NP};   // each scenario reads its own problem's d slot
     if (jac_vals && hess_vals)
         eval_kernel<true, true, true><<<g, kThr, 0, st>>>(h->P, (int)h->S, h->ld, b, false, x, nullptr, nullptr,
                                                           lambda, h->feed, c, jac_vals, hess_vals, nullptr);
@@ -975,6 +982,7 @@ abs_status kkt_solve(abs_problem* h, const double* rhs_x, const double* rhs_c, d
 
 // the interior-point engine lives in its own file (same translation unit)
 #include "engine.inc"
+#include "warm.inc"
 
 namespace {
 template <class T>

@@ -293,11 +293,12 @@ __global__ void dstep_kernel(int64_t ld, const BView b, double* __restrict__ x, 
 
 // starting point: every stage copies the inlet streams (or, with base and the problem's
 // PS_BASE set, the stage states of problem p's expected-value solution at
-// base[v * ldb + p]), the slack from the hydraulic row at the problem's d (already in
+// base[v * ldb + p], or of the one shared solution at base[v * ldb]), the slack from the hydraulic row at the problem's d (already in
 // x's d slot); pushed into the bounds
 __global__ void __launch_bounds__(128) init_kernel(const Params P, int S, int64_t ld, const BView b,
                                                    const double* __restrict__ feed, const double* __restrict__ base,
-                                                   int64_t ldb, double push, double frac, double* __restrict__ x,
+                                                   int64_t ldb, bool base_shared, double push, double frac,
+                                                   double* __restrict__ x,
                                                    double* __restrict__ zL, double* __restrict__ zU,
                                                    double* __restrict__ lam) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -308,7 +309,7 @@ __global__ void __launch_bounds__(128) init_kernel(const Params P, int S, int64_
     double q[NV];
     if (base && (!b.ps || psv(b, PS_BASE, pr) != 0.0)) {
 #pragma unroll
-        for (int j = 0; j < NV; ++j) q[j] = base[(int64_t)(NV * n + j) * ldb + pr];
+        for (int j = 0; j < NV; ++j) q[j] = base[(int64_t)(NV * n + j) * ldb + (base_shared ? 0 : pr)];
     } else {
 #pragma unroll
         for (int l = 0; l < 9; ++l) q[LX + l] = feed[(int64_t)(F_XIN + l) * ld + s] / P.sx[l];
@@ -338,6 +339,35 @@ __global__ void __launch_bounds__(128) init_kernel(const Params P, int S, int64_
         zL[o] = has_lo(j) ? 1.0 : 0.0;
         zU[o] = has_hi(j) ? 1.0 : 0.0;
         lam[o] = 0.0;
+    }
+}
+
+// warm start: push every bounded unknown of x into its bounds as the cold start does and
+// put its bound multipliers on the central path of the problem's mu: z = mu / slack
+__global__ void __launch_bounds__(128) warm_push_kernel(const Params P, int S, int64_t ld, const BView b, double push,
+                                                        double frac, double* __restrict__ x, double* __restrict__ zL,
+                                                        double* __restrict__ zU) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    const int pr = live_prob(b, s, S, PS_ACT);
+    if (pr < 0) return;
+    const double mu = psv(b, PS_MU, pr);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        double v = x[o];
+        const double lo = lo_of(P, j), hi = hi_of(P, j);
+        if (has_lo(j)) {
+            const double w = has_hi(j) ? frac * (hi - lo) : INFINITY;
+            v = fmax(v, lo + fmin(push * fmax(1.0, fabs(lo)), w));
+        }
+        if (has_hi(j)) {
+            const double w = has_lo(j) ? frac * (hi - lo) : INFINITY;
+            v = fmin(v, hi - fmin(push * fmax(1.0, fabs(hi)), w));
+        }
+        x[o] = v;
+        zL[o] = has_lo(j) ? mu / (v - lo) : 0.0;
+        zU[o] = has_hi(j) ? mu / (hi - v) : 0.0;
     }
 }
 

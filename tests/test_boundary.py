@@ -27,7 +27,7 @@ def binding():
 def _declared_functions():
     src = open(os.path.join(ROOT, "include", "absorber.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:abs_status|void|const char\*|int64_t)\s+(\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:abs_status|void|const char\*|int64_t|int32_t)\s+(\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
