@@ -156,6 +156,94 @@ def run_reference(args, S_full):
     print(json.dumps(line), flush=True)
 
 
+def timed(fn, reps):
+    """Device time (CUDA events on the current stream) of reps calls of fn; returns
+    (seconds per call, results)."""
+    import torch
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    out = [fn() for _ in range(reps)]
+    b.record(st)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps, out
+
+
+def learned_forms(B, ai, prob_main, reps, n_train=20000, epochs=100):
+    """The learned warm start: train the network on n_train single-scenario solves (one
+    batched solve), then solve the headline workload and the 20,000-scenario workload
+    from the learned start (FP32 factors + FP64 refinement, and FP64) against the plain
+    FP64 path from the default start."""
+    import torch
+    P = ai.PARAMS
+    t0 = time.perf_counter()
+    Ftr = ai.make_feeds(n_train, 7, stream=3)
+    batch = B.Batch(P, [Ftr[:, i:i + 1] for i in range(n_train)])
+    x = torch.zeros(batch.n_primal, dtype=torch.float64, device="cuda")
+    y = torch.zeros(220 * batch.ld, dtype=torch.float64, device="cuda")
+    res = batch.ipm_solve(B.default_options(init=2, obj_scaling=100.0), x_out=x, y_out=y)
+    keep = [r.status == 0 for r in res]
+    t_data = time.perf_counter() - t0
+    X, Y = B.make_dataset(batch, x, y, keep=keep, n_aug=4, d_spread=0.15)
+    net = B.MLP(seed=11)
+    net.fit_normalization(X, Y)
+    t1 = time.perf_counter()
+    hist = net.train(X, Y, B.train_options(epochs=epochs, batch=256, lr=2e-3, lr_final=2e-5, seed=5))
+    t_train = time.perf_counter() - t1
+    del batch, x, y
+    out = {"training": {"single_scenario_solves": n_train, "converged": int(sum(keep)), "rows": int(X.shape[0]),
+                        "solve_s": t_data, "epochs": epochs, "train_s": t_train,
+                        "loss_first_last": [float(hist[0]), float(hist[-1])]}}
+
+    def o(prec):
+        return B.default_options(precision=prec, max_refine=(8 if prec == B.PREC_FP32 else 0))
+
+    cases = [("headline", prob_main), ("absorber-S20000-u10-seed4", None)]
+    for name, pr in cases:
+        if pr is None:
+            pr = B.Problem(P, ai.workload_feeds(name))
+        entry = {"scenarios": pr.S}
+        for label, prec, learned in (("fp64_cold", B.PREC_FP64, False), ("fp32_cold", B.PREC_FP32, False),
+                                     ("fp64_learned", B.PREC_FP64, True), ("fp32_learned", B.PREC_FP32, True)):
+            fn = (lambda: B.ipm_solve_learned(pr, net, o(prec))) if learned else (lambda: pr.ipm_solve(o(prec)))
+            fn()
+            sec, rs = timed(fn, reps)
+            r = rs[0]
+            entry[label] = {"solve_time_s": sec, "iters": r.iters, "base_iters": r.base_iters,
+                            "status": r.status, "E0": r.E0, "d": r.d,
+                            "learned_start_used": bool(r.warm_status) if learned else None,
+                            "fp64_fallbacks": r.fp64_fallbacks}
+        base = entry["fp64_cold"]["solve_time_s"]
+        for k in ("fp32_cold", "fp64_learned", "fp32_learned"):
+            entry[k]["speedup_vs_fp64_cold"] = base / entry[k]["solve_time_s"]
+        out[name] = entry
+    return out
+
+
+def batched_form(B, ai, reps):
+    """64 independent design problems, scenario counts log-uniform in [50, 2000], solved
+    as one batch (FP32 factors + FP64 refinement) against one-by-one solves."""
+    P = ai.PARAMS
+    sizes = ai.batched_sizes()
+    feeds = ai.batched_feeds(sizes, seed=3)
+    batch = B.Batch(P, feeds)
+    o = B.default_options(precision=B.PREC_FP32, max_refine=8)
+    batch.ipm_solve(o)
+    sec, rs = timed(lambda: batch.ipm_solve(o), reps)
+    res = rs[0]
+    probs = [B.Problem(P, F) for F in feeds[:8]]
+    for p in probs:
+        p.ipm_solve(o)
+    sec1, rs1 = timed(lambda: [p.ipm_solve(o) for p in probs], 1)
+    per_scen_1 = sec1 / float(sum(sizes[:8]))
+    return {"problems": len(sizes), "scenarios": int(sizes.sum()), "solve_time_s": sec,
+            "newton_steps_per_s": sum(r.iters for r in res) / sec,
+            "status": sorted(set(r.status for r in res)), "iters_max": max(r.iters for r in res),
+            "one_by_one_first8_s": sec1, "one_by_one_estimate_all_s": per_scen_1 * float(sizes.sum()),
+            "speedup_vs_one_by_one": per_scen_1 * float(sizes.sum()) / sec}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -166,6 +254,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the learned / batched form comparisons")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -198,8 +287,7 @@ def main():
     st = torch.cuda.current_stream()
 
     def opts(profile=0, p=prec):
-        return B.default_options(precision=p, max_refine=(8 if p == B.PREC_FP32 else 0),
-                                 refine_tol=1e-12, profile=profile)
+        return B.default_options(precision=p, max_refine=(8 if p == B.PREC_FP32 else 0), profile=profile)
 
     for _ in range(args.warmup):
         r = prob.ipm_solve(opts())
@@ -310,6 +398,10 @@ def main():
              "value": sum(r.iters for r in ro) / (oms / 1e3), "solve_time_s": oms / 2e3,
              "iters": [r.iters for r in ro], "d": ro[0].d, "status": [r.status for r in ro]}
 
+    forms = None
+    if rank == 0 and not args.no_forms:
+        forms = {"learned_warm_start": learned_forms(B, ai, prob, reps=3), "batched": batched_form(B, ai, reps=2)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample, its = 50, 6
@@ -337,7 +429,7 @@ def main():
                                    for i, n in enumerate(B.PHASES)},
             "kernels": kern, "roofline": roof,
             "fma_peaks_gflops": {"fp64": fma64, "fp32": fma32},
-            "other_precision": other,
+            "other_precision": other, "forms": forms,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": int(sum(r.launches for r in results)),
         }
