@@ -255,6 +255,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the learned / batched form comparisons")
+    ap.add_argument("--capture-iters", type=int, default=0,
+                    help="profiling case: only N interior-point iterations of the workload from the inlet "
+                         "start (no expected-value solve), then exit without a JSON line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -285,6 +288,13 @@ def main():
     prec = B.PREC_FP32 if args.precision == "fp32" else B.PREC_FP64
     prob = B.Problem(P, F)
     st = torch.cuda.current_stream()
+
+    if args.capture_iters > 0:
+        r = prob.ipm_solve(B.default_options(precision=prec, max_refine=(8 if prec == B.PREC_FP32 else 0),
+                                             max_iter=args.capture_iters, init=1))
+        torch.cuda.synchronize()
+        print(f"capture case: {r.iters} iterations, status {B.STATUS.get(r.status)}", flush=True)
+        return
 
     def opts(profile=0, p=prec):
         return B.default_options(precision=p, max_refine=(8 if p == B.PREC_FP32 else 0), profile=profile)
