@@ -241,7 +241,10 @@ typedef struct abs_options {
     double warm_bound_push;/* ipm_solve_learned: bound push and fraction at the learned start */
     int32_t warm_multipliers; /* ipm_solve_learned: 0 least-squares estimate at the learned
                                  point, 1 the network's multipliers */
-    int32_t reserved_opt;
+    int32_t autotune;      /* 1: the first factor / solve launch of each kernel, precision and
+                              size bucket (S rounded down to a power of two, S >= 256) times
+                              every warps-per-block candidate and keeps the fastest
+                              (results are identical); 0: 4 warps per block */
 } abs_options;
 
 void abs_default_options(abs_options* o);
@@ -272,6 +275,8 @@ typedef struct abs_result {
     double warm_ms;              /* ipm_solve_learned: host time of prediction + acceptance test */
     double warm_E0, cold_E0;     /* E_0 at the learned start and at the inlet-copy start */
     double warm_theta, cold_theta;  /* constraint violation ||c||_1 at the same two starts */
+    int32_t tiles[4];            /* warps per block last used: factor, solve (1 and 2 right-hand
+                                    sides), transposed solve */
 } abs_result;
 
 /* Diagnostic: measured throughput of dependent-free fused multiply-adds on the current
@@ -286,9 +291,11 @@ abs_status abs_measure_fma_peak(int kind, double* gflops);
  * the host only sequences launches and reads a few scalars per iteration.
  * Starting point (unless warm_x is given): for S > 1 and init = 0 the stage states of
  * the expected-value problem -- one scenario whose feed is the mean of the S feeds,
- * solved first by this same method from the inlet-copy start -- copied to every
- * scenario, d = (d_lo + d_hi)/2 and each hydraulic slack from its row; otherwise every
- * stage copies the inlet streams.  The returned multipliers (y_out) are those of the
+ * solved first by this same method from the inlet-copy start, always with FP64 factors
+ * -- copied to every scenario, d = (d_lo + d_hi)/2 and each hydraulic slack from its
+ * row; otherwise every stage copies the inlet streams.  A warm start (warm_x) is pushed
+ * into the bounds by bound_push / bound_frac and its bound multipliers set to
+ * mu_init / slack; without warm_y the row multipliers are the least-squares estimate.  The returned multipliers (y_out) are those of the
  * unscaled problem min d.
  *   opt     host (NULL = defaults).
  *   warm_x  device primal vector or NULL; warm_y device row vector or NULL.

@@ -10,6 +10,9 @@
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -293,6 +296,8 @@ struct abs_problem {
         double d = 0.0, dw = 0.0, Kdd = 0.0, A0 = 0.0, Q2 = 0.0, Sd = 0.0;
     } fac;
     Prof prof;
+    int autotune = 1;                // tile autotuner on (options.autotune)
+    int tile[4] = {4, 4, 4, 4};      // warps per block last used: factor, solve, solve x2, solve^T
     int64_t nlaunch = 0;         // kernels launched (every launch is followed by launch_check)
     float* mlp_x = nullptr;          // learned warm start: network inputs [ld][3] and outputs [ld][440]
     float* mlp_y = nullptr;
@@ -338,6 +343,7 @@ abs_status launch_check(abs_problem* h) {
 }
 
 enum { K_EVAL = 0, K_EVAL_TRIAL = 1, K_FACTOR = 2, K_SOLVE = 3, K_SOLVE_T = 4 };
+enum { TK_FACTOR = 0, TK_SOLVE1 = 1, TK_SOLVE2 = 2, TK_SOLVE_T = 3 };
 
 cudaEvent_t prof_event(abs_problem* h) {
     auto& p = h->prof;
@@ -482,24 +488,121 @@ struct KKTSys {
     std::vector<int> nsing;
 };
 
+// ---- block-tile autotuner ----------------------------------------------------------------
+// The warp kernels run one scenario per warp; how many warps share a block (and with it
+// the block's static shared memory) sets the resident blocks per SM and the tail of the
+// last wave.  The first launch of a kernel kind, precision and size bucket (powers of
+// two of S) on a device times every candidate on that launch's own data -- each
+// candidate computes the same values bit for bit, one warp per scenario -- and keeps the
+// fastest for every later launch with that key.  Launches below TUNE_MIN_S scenarios are
+// latency-bound and use the default shape.
+constexpr int TUNE_MIN_S = 256;
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tuned;   // (device, kind, element size, bucket)
+
+int size_bucket(int64_t S) {
+    int b = 0;
+    while (((int64_t)1 << (b + 1)) <= S) ++b;
+    return b;
+}
+
+template <class Launch>
+abs_status tuned_launch(abs_problem* h, int kind, int es, std::initializer_list<int> cands, int dflt,
+                        Launch&& launch, cudaStream_t st) {
+    int w = dflt;
+    if (h->autotune && h->S >= TUNE_MIN_S) {
+        const auto key = std::make_tuple(h->dev, kind, es, size_bucket(h->S));
+        bool found = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tuned.find(key);
+            if (it != g_tuned.end()) {
+                w = it->second;
+                found = true;
+            }
+        }
+        if (!found) {
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            float best = INFINITY;
+            for (int c : cands) {
+                cudaEventRecord(e0, st);
+                abs_status r = launch(c);
+                cudaEventRecord(e1, st);
+                if (r != ABS_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return r;
+                }
+                float ms = 0.f;
+                if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+                    ms < best) {
+                    best = ms;
+                    w = c;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned[key] = w;
+            h->tile[kind] = w;
+            return ABS_OK;   // the candidates' outputs are identical: the last one stands
+        }
+    }
+    h->tile[kind] = w;
+    return launch(w);
+}
+
+template <class T, int W>
+void factor_w(abs_problem* h, const double* jac, double pivtol, cudaStream_t st) {
+    if constexpr (factor_fits<T, W>())
+        factor_warp_kernel<T, W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (T*)h->LU, h->piv,
+                                                                (T*)h->G, h->sing, pivtol);
+}
+
 template <class T>
 abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaStream_t st) {
     prof_begin(h, K_FACTOR, st);
-    factor_warp_kernel<T><<<gridw(h, WPB_F), 32 * WPB_F, 0, st>>>((int)h->S, h->ld, view(h), jac, (T*)h->LU, h->piv,
-                                                                (T*)h->G, h->sing, pivtol);
+    auto go = [&](int w) {
+        switch (w) {
+            case 1: factor_w<T, 1>(h, jac, pivtol, st); break;
+            case 2: factor_w<T, 2>(h, jac, pivtol, st); break;
+            case 8: factor_w<T, 8>(h, jac, pivtol, st); break;
+            default: factor_w<T, 4>(h, jac, pivtol, st); break;
+        }
+        return launch_check(h);
+    };
+    abs_status r = factor_fits<T, 8>() ? tuned_launch(h, TK_FACTOR, sizeof(T), {1, 2, 4, 8}, WPB_F, go, st)
+                                       : tuned_launch(h, TK_FACTOR, sizeof(T), {1, 2, 4}, WPB_F, go, st);
     prof_end(h, st);
-    return launch_check(h);
+    return r;
+}
+
+template <class T, int NR_, int W>
+void solve_w(abs_problem* h, const double* jac, const double* x, const double* r0, const double* r1, double* o0,
+             double* o1, cudaStream_t st) {
+    solve_warp_kernel<T, NR_, W><<<gridw(h, W), 32 * W, 0, st>>>(h->P, (int)h->S, h->ld, view(h), jac,
+                                                                  (const T*)h->LU, h->piv, (const T*)h->G, x, r0, r1,
+                                                                  o0, o1);
 }
 
 template <class T, int NR_>
 abs_status solve_launch(abs_problem* h, const double* jac, const double* x, const double* r0, const double* r1,
                         double* o0, double* o1, cudaStream_t st) {
     prof_begin(h, K_SOLVE, st);
-    solve_warp_kernel<T, NR_><<<gridw(h, WPB_S), 32 * WPB_S, 0, st>>>(h->P, (int)h->S, h->ld, view(h), jac,
-                                                                       (const T*)h->LU, h->piv, (const T*)h->G, x, r0,
-                                                                       r1, o0, o1);
+    auto go = [&](int w) {
+        switch (w) {
+            case 1: solve_w<T, NR_, 1>(h, jac, x, r0, r1, o0, o1, st); break;
+            case 2: solve_w<T, NR_, 2>(h, jac, x, r0, r1, o0, o1, st); break;
+            case 8: solve_w<T, NR_, 8>(h, jac, x, r0, r1, o0, o1, st); break;
+            default: solve_w<T, NR_, 4>(h, jac, x, r0, r1, o0, o1, st); break;
+        }
+        return launch_check(h);
+    };
+    abs_status r = tuned_launch(h, NR_ == 1 ? TK_SOLVE1 : TK_SOLVE2, sizeof(T), {1, 2, 4, 8}, WPB_S, go, st);
     prof_end(h, st);
-    return launch_check(h);
+    return r;
 }
 
 abs_status solve_j(abs_problem* h, int prec, const double* jac, const double* x, const double* r0, double* o0,
@@ -508,16 +611,31 @@ abs_status solve_j(abs_problem* h, int prec, const double* jac, const double* x,
     return solve_launch<double, 1>(h, jac, x, r0, nullptr, o0, nullptr, st);
 }
 
+template <class T, int W>
+void solve_t_w(abs_problem* h, const double* jac, const double* g, double* out, cudaStream_t st) {
+    solve_t_warp_kernel<T, W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (const T*)h->LU, h->piv,
+                                                               g, out);
+}
+
+template <class T>
+abs_status solve_jt_t(abs_problem* h, const double* jac, const double* g, double* out, cudaStream_t st) {
+    auto go = [&](int w) {
+        switch (w) {
+            case 1: solve_t_w<T, 1>(h, jac, g, out, st); break;
+            case 2: solve_t_w<T, 2>(h, jac, g, out, st); break;
+            case 8: solve_t_w<T, 8>(h, jac, g, out, st); break;
+            default: solve_t_w<T, 4>(h, jac, g, out, st); break;
+        }
+        return launch_check(h);
+    };
+    return tuned_launch(h, TK_SOLVE_T, sizeof(T), {1, 2, 4, 8}, WPB_S, go, st);
+}
+
 abs_status solve_jt(abs_problem* h, int prec, const double* jac, const double* g, double* out, cudaStream_t st) {
     prof_begin(h, K_SOLVE_T, st);
-    if (prec == ABS_PREC_FP32)
-        solve_t_warp_kernel<float><<<gridw(h, WPB_S), 32 * WPB_S, 0, st>>>((int)h->S, h->ld, view(h), jac,
-                                                                            (const float*)h->LU, h->piv, g, out);
-    else
-        solve_t_warp_kernel<double><<<gridw(h, WPB_S), 32 * WPB_S, 0, st>>>((int)h->S, h->ld, view(h), jac,
-                                                                             (const double*)h->LU, h->piv, g, out);
+    abs_status r = prec == ABS_PREC_FP32 ? solve_jt_t<float>(h, jac, g, out, st) : solve_jt_t<double>(h, jac, g, out, st);
     prof_end(h, st);
-    return launch_check(h);
+    return r;
 }
 
 // factor every active problem's J_s, q = J^-1 b and the Schur sums: per problem A0 =
@@ -732,6 +850,7 @@ void abs_default_options(abs_options* o) {
     o->obj_scaling = 0.0;
     o->warm_mu_init = 1e-3;
     o->warm_bound_push = 1e-8;
+    o->autotune = 1;
 }
 
 abs_status absorber_create(const abs_params* p, const double* feeds, const double* prob, int64_t S,

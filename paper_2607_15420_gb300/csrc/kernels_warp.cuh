@@ -19,8 +19,14 @@ namespace absorber {
 constexpr int NCA = NV + NABV;    // augmented columns [A_n | B_n]
 constexpr int PADA = NCA + 1;     // shared-memory row stride of the augmented block
 constexpr int PADL = NV + 1;      // shared-memory row stride of a staged LU block
-constexpr int WPB_F = 4;          // warps (scenarios) per block, factor
-constexpr int WPB_S = 4;          // warps (scenarios) per block, solves
+constexpr int WPB_F = 4;          // default warps (scenarios) per block, factor
+constexpr int WPB_S = 4;          // default warps (scenarios) per block, solves
+
+// static shared memory of the factor kernel with W warps per block (must stay <= 48 KB)
+template <class T, int W>
+constexpr bool factor_fits() {
+    return (size_t)W * (NV * PADA + NV * NABV) * sizeof(T) <= 48 * 1024;
+}
 
 __host__ __device__ constexpr int64_t lu_off(int64_t s, int n) { return (s * N_STAGES + n) * (int64_t)(NV * NV); }
 __host__ __device__ constexpr int64_t g_off(int64_t s, int n) { return (s * N_STAGES + n) * (int64_t)(NV * NABV); }
@@ -57,15 +63,51 @@ __device__ inline double recip(double a) {
 }
 __device__ inline float recip(float a) { return 1.0f / a; }
 
+// the coefficients of a stage-coupling table (<= 32 entries) for scenario s, entry q on
+// lane q: one parallel load instead of a dependent load per entry inside the
+// sequential coupling loops
 template <class T>
-__global__ void __launch_bounds__(32 * WPB_F) factor_warp_kernel(int S, int64_t ld, const BView b,
+__device__ inline T load_coupling(const Ent* tab, int cnt, int base, const double* __restrict__ jac, int64_t ld,
+                                  int s, int lane) {
+    return lane < cnt ? (T)jac[(int64_t)(base + tab[lane].slot) * ld + s] : T(0);
+}
+
+// a stage's LU block and pivots fetched into registers ahead of use (the next stage's
+// loads overlap the current stage's work), then committed to shared memory
+constexpr int LU_PER_LANE = (NV * NV + 31) / 32;
+template <class T>
+struct LUPrefetch {
+    T v[LU_PER_LANE];
+    unsigned char p;
+    __device__ inline void fetch(const T* __restrict__ LU, const unsigned char* __restrict__ piv, int64_t s, int n,
+                                 int lane) {
+        const T* src = LU + lu_off(s, n);
+#pragma unroll
+        for (int i = 0; i < LU_PER_LANE; ++i) {
+            const int e = lane + 32 * i;
+            v[i] = e < NV * NV ? src[e] : T(0);
+        }
+        p = lane < NV ? piv[pv_off(s, n) + lane] : (unsigned char)0;
+    }
+    __device__ inline void commit(T (*A)[PADL], unsigned char* pv, int lane) const {
+#pragma unroll
+        for (int i = 0; i < LU_PER_LANE; ++i) {
+            const int e = lane + 32 * i;
+            if (e < NV * NV) A[e / NV][e % NV] = v[i];
+        }
+        if (lane < NV) pv[lane] = p;
+    }
+};
+
+template <class T, int WPB = WPB_F>
+__global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld, const BView b,
                                                                  const double* __restrict__ jac, T* __restrict__ LU,
                                                                  unsigned char* __restrict__ piv, T* __restrict__ G,
                                                                  int* __restrict__ sing, double pivtol) {
-    __shared__ T sA[WPB_F][NV][PADA];
-    __shared__ T sG[WPB_F][NV][NABV];
+    __shared__ T sA[WPB][NV][PADA];
+    __shared__ T sG[WPB][NV][NABV];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s = blockIdx.x * WPB_F + warp;
+    const int s = blockIdx.x * WPB + warp;
     // whole warps leave together; no block-level barriers below
     if (live_prob(b, s, S, PS_ACT) < 0) return;
     T(*A)[PADA] = sA[warp];
@@ -89,9 +131,11 @@ __global__ void __launch_bounds__(32 * WPB_F) factor_warp_kernel(int S, int64_t 
         __syncwarp();
         // Schur update with the previous stage: A_n -= C_n G_{n-1}
         if (n > 0) {
-            for (int k = 0; k < c_nblw[t]; ++k) {
+            const int nq = c_nblw[t];
+            const T cvq = load_coupling<T>(c_blw[t], nq, base, jac, ld, s, lane);
+            for (int k = 0; k < nq; ++k) {
                 const Ent e = c_blw[t][k];
-                const T cv = (T)jac[(int64_t)(base + e.slot) * ld + s];
+                const T cv = shfl(cvq, k);
                 if (lane < NABV) A[e.r][abv_var(lane)] -= cv * Gp[blw_var(e.c)][lane];
                 __syncwarp();
             }
@@ -240,17 +284,17 @@ __device__ inline T lu_apply_t_warp(const T (*A)[PADL], const unsigned char* pv,
 }
 
 // J_s x = r (NRHS right-hand sides; a null r[k] means b = dc/dd), one warp per scenario
-template <class T, int NRHS>
-__global__ void __launch_bounds__(32 * WPB_S) solve_warp_kernel(const Params P, int S, int64_t ld, const BView b,
+template <class T, int NRHS, int WPB = WPB_S>
+__global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, int S, int64_t ld, const BView b,
                                                                 const double* __restrict__ jac, const T* __restrict__ LU,
                                                                 const unsigned char* __restrict__ piv,
                                                                 const T* __restrict__ G, const double* x,
                                                                 const double* r0, const double* r1, double* o0,
                                                                 double* o1) {
-    __shared__ T sL[WPB_S][NV][PADL];
-    __shared__ unsigned char sP[WPB_S][NV + 2];
+    __shared__ T sL[WPB][NV][PADL];
+    __shared__ unsigned char sP[WPB][NV + 2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s = blockIdx.x * WPB_S + warp;
+    const int s = blockIdx.x * WPB + warp;
     const int pr = live_prob(b, s, S, PS_ACT);
     if (pr < 0) return;
     T(*A)[PADL] = sL[warp];
@@ -262,26 +306,37 @@ __global__ void __launch_bounds__(32 * WPB_S) solve_warp_kernel(const Params P, 
     T y[NRHS];
 #pragma unroll
     for (int k = 0; k < NRHS; ++k) y[k] = T(0);
+    LUPrefetch<T> pre;
+    pre.fetch(LU, piv, s, 0, lane);
+    T rnext[NRHS];
+#pragma unroll
+    for (int k = 0; k < NRHS; ++k) rnext[k] = (rr[k] && row) ? (T)rr[k][(int64_t)lane * ld + s] : T(0);
     // forward: w_n = r_n - C_n y_{n-1},  y_n = At_n^-1 w_n
     for (int n = 0; n < N_STAGES; ++n) {
         const int t = stage_type(n);
         const int base = c_segJ[n];
-        stage_lu(LU + lu_off(s, n), A, lane);
-        if (lane < NV) pv[lane] = piv[pv_off(s, n) + lane];
+        pre.commit(A, pv, lane);
         T w[NRHS];
 #pragma unroll
-        for (int k = 0; k < NRHS; ++k) {
-            if (rr[k]) w[k] = row ? (T)rr[k][(int64_t)(NR * n + lane) * ld + s] : T(0);
-            else w[k] = (lane == R_H) ? bval : T(0);
+        for (int k = 0; k < NRHS; ++k) w[k] = rr[k] ? rnext[k] : ((lane == R_H) ? bval : T(0));
+        if (n + 1 < N_STAGES) {
+            pre.fetch(LU, piv, s, n + 1, lane);
+#pragma unroll
+            for (int k = 0; k < NRHS; ++k)
+                rnext[k] = (rr[k] && row) ? (T)rr[k][(int64_t)(NR * (n + 1) + lane) * ld + s] : T(0);
         }
         if (n > 0) {
-            for (int q = 0; q < c_nblw[t]; ++q) {
-                const Ent e = c_blw[t][q];
-                const T cv = (T)jac[(int64_t)(base + e.slot) * ld + s];
+            // products of C_n's entries (entry q on lane q) with y_{n-1}, then added to
+            // their rows in entry order
+            const int nq = c_nblw[t];
+            const T cvq = load_coupling<T>(c_blw[t], nq, base, jac, ld, s, lane);
+            const int src = lane < nq ? blw_var(c_blw[t][lane].c) : 0;
 #pragma unroll
-                for (int k = 0; k < NRHS; ++k) {
-                    const T yb = shfl(y[k], blw_var(e.c));
-                    if (lane == e.r) w[k] -= cv * yb;
+            for (int k = 0; k < NRHS; ++k) {
+                const T pq = cvq * shfl(y[k], src);
+                for (int q = 0; q < nq; ++q) {
+                    const T pp = shfl(pq, q);
+                    if (lane == c_blw[t][q].r) w[k] -= pp;
                 }
             }
         }
@@ -293,16 +348,32 @@ __global__ void __launch_bounds__(32 * WPB_S) solve_warp_kernel(const Params P, 
         }
         __syncwarp();
     }
-    // backward: x_n = y_n - G_n x_{n+1}   (y currently holds x_9 = y_9)
-    for (int n = N_STAGES - 2; n >= 0; --n) {
+    // backward: x_n = y_n - G_n x_{n+1}   (y currently holds x_9 = y_9); the forward
+    // values y_n and G_n of the next stage down are fetched one stage ahead
+    T gnext[NABV];
+    T ynext[NRHS];
+    auto fetch_back = [&](int n) {
         const T* Gn = G + g_off(s, n);
 #pragma unroll
+        for (int a = 0; a < NABV; ++a) gnext[a] = row ? Gn[lane * NABV + a] : T(0);
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) ynext[k] = row ? (T)oo[k][(int64_t)(NV * n + lane) * ld + s] : T(0);
+    };
+    fetch_back(N_STAGES - 2);
+    for (int n = N_STAGES - 2; n >= 0; --n) {
+        T gc[NABV], yc[NRHS];
+#pragma unroll
+        for (int a = 0; a < NABV; ++a) gc[a] = gnext[a];
+#pragma unroll
+        for (int k = 0; k < NRHS; ++k) yc[k] = ynext[k];
+        if (n > 0) fetch_back(n - 1);
+#pragma unroll
         for (int k = 0; k < NRHS; ++k) {
-            T acc = row ? (T)oo[k][(int64_t)(NV * n + lane) * ld + s] : T(0);
+            T acc = yc[k];
 #pragma unroll
             for (int a = 0; a < NABV; ++a) {
                 const T xa = shfl(y[k], abv_var(a));
-                if (row) acc -= Gn[lane * NABV + a] * xa;
+                if (row) acc -= gc[a] * xa;
             }
             y[k] = acc;
             if (row) oo[k][(int64_t)(NV * n + lane) * ld + s] = (double)acc;
@@ -311,33 +382,42 @@ __global__ void __launch_bounds__(32 * WPB_S) solve_warp_kernel(const Params P, 
 }
 
 // J_s^T v = g, one warp per scenario; g and out in primal layout (no d)
-template <class T>
-__global__ void __launch_bounds__(32 * WPB_S) solve_t_warp_kernel(int S, int64_t ld, const BView b,
+template <class T, int WPB = WPB_S>
+__global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t ld, const BView b,
                                                                   const double* __restrict__ jac,
                                                                   const T* __restrict__ LU,
                                                                   const unsigned char* __restrict__ piv,
                                                                   const double* __restrict__ g, double* out) {
-    __shared__ T sL[WPB_S][NV][PADL];
-    __shared__ unsigned char sP[WPB_S][NV + 2];
+    __shared__ T sL[WPB][NV][PADL];
+    __shared__ unsigned char sP[WPB][NV + 2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s = blockIdx.x * WPB_S + warp;
+    const int s = blockIdx.x * WPB + warp;
     if (live_prob(b, s, S, PS_ACT) < 0) return;
     T(*A)[PADL] = sL[warp];
     unsigned char* pv = sP[warp];
     const bool row = lane < NV;
     T u = T(0);
+    LUPrefetch<T> pre;
+    pre.fetch(LU, piv, s, 0, lane);
+    T gnext = row ? (T)g[(int64_t)lane * ld + s] : T(0);
     // forward (U^T of the block LU): u_n = At_n^-T (g_n - B_{n-1}^T u_{n-1})
     for (int n = 0; n < N_STAGES; ++n) {
-        stage_lu(LU + lu_off(s, n), A, lane);
-        if (lane < NV) pv[lane] = piv[pv_off(s, n) + lane];
-        T w = row ? (T)g[(int64_t)(NV * n + lane) * ld + s] : T(0);
+        pre.commit(A, pv, lane);
+        T w = gnext;
+        if (n + 1 < N_STAGES) {
+            pre.fetch(LU, piv, s, n + 1, lane);
+            gnext = row ? (T)g[(int64_t)(NV * (n + 1) + lane) * ld + s] : T(0);
+        } else {
+            pre.fetch(LU, piv, s, N_STAGES - 2, lane);   // first stage of the backward pass
+        }
         if (n > 0) {
             const int tb = stage_type(n - 1), bb = c_segJ[n - 1];
-            for (int q = 0; q < c_nabv[tb]; ++q) {
-                const Ent e = c_abv[tb][q];
-                const T cv = (T)jac[(int64_t)(bb + e.slot) * ld + s];
-                const T ur = shfl(u, e.r);
-                if (lane == abv_var(e.c)) w -= cv * ur;
+            const int nq = c_nabv[tb];
+            const T cvq = load_coupling<T>(c_abv[tb], nq, bb, jac, ld, s, lane);
+            const T pq = cvq * shfl(u, lane < nq ? (int)c_abv[tb][lane].r : 0);
+            for (int q = 0; q < nq; ++q) {
+                const T pp = shfl(pq, q);
+                if (lane == abv_var(c_abv[tb][q].c)) w -= pp;
             }
         }
         __syncwarp();
@@ -348,19 +428,20 @@ __global__ void __launch_bounds__(32 * WPB_S) solve_t_warp_kernel(int S, int64_t
     // backward (L^T): v_n = u_n - At_n^-T C_{n+1}^T v_{n+1}   (u holds v_9 = u_9)
     T v = u;
     for (int n = N_STAGES - 2; n >= 0; --n) {
-        stage_lu(LU + lu_off(s, n), A, lane);
-        if (lane < NV) pv[lane] = piv[pv_off(s, n) + lane];
+        pre.commit(A, pv, lane);
+        const T un = row ? (T)out[(int64_t)(NR * n + lane) * ld + s] : T(0);
+        if (n > 0) pre.fetch(LU, piv, s, n - 1, lane);
         const int ta = stage_type(n + 1), ba = c_segJ[n + 1];
+        const int nq = c_nblw[ta];
+        const T cvq = load_coupling<T>(c_blw[ta], nq, ba, jac, ld, s, lane);
+        const T pq = cvq * shfl(v, lane < nq ? (int)c_blw[ta][lane].r : 0);
         T w = T(0);
-        for (int q = 0; q < c_nblw[ta]; ++q) {
-            const Ent e = c_blw[ta][q];
-            const T cv = (T)jac[(int64_t)(ba + e.slot) * ld + s];
-            const T vr = shfl(v, e.r);
-            if (lane == blw_var(e.c)) w += cv * vr;
+        for (int q = 0; q < nq; ++q) {
+            const T pp = shfl(pq, q);
+            if (lane == blw_var(c_blw[ta][q].c)) w += pp;
         }
         __syncwarp();
         w = lu_apply_t_warp<T>(A, pv, lane, w);
-        const T un = row ? (T)out[(int64_t)(NR * n + lane) * ld + s] : T(0);
         v = un - w;
         if (row) out[(int64_t)(NR * n + lane) * ld + s] = (double)v;
         __syncwarp();

@@ -119,3 +119,23 @@ def test_batched_64_uneven_problems(B):
         Zn, hist = checks.mesh_newton(P, F[:, pick], Z[pick], d, iters=5)
         assert hist[-1] <= 1e-12
         assert np.max(np.abs(Zn[:, keep] - Z[pick][:, keep]) / np.maximum(1, np.abs(Zn[:, keep]))) <= 1e-6
+
+
+def test_autotuned_tiles_give_identical_results(B):
+    # the tile autotuner only regroups warps (one scenario per warp): the solve is the
+    # same bit for bit with the tuned shapes and with the default shape
+    import torch
+    F = ai.make_feeds(600, 1)
+    prob = B.Problem(P, F)
+    outs = []
+    for tune in (0, 1, 1):
+        x = torch.zeros(prob.n_primal, dtype=torch.float64, device="cuda")
+        o = B.default_options(precision=1, max_refine=8, autotune=tune)
+        r = prob.ipm_solve(o, x_out=x)
+        assert r.status == 0
+        outs.append((r.iters, r.d, _host(x), list(r.tiles)))
+    assert outs[0][0] == outs[1][0] == outs[2][0]
+    assert outs[0][1] == outs[1][1] == outs[2][1]
+    assert np.array_equal(outs[0][2], outs[1][2]) and np.array_equal(outs[1][2], outs[2][2])
+    assert outs[0][3] == [4, 4, 4, 4]
+    assert all(w in (1, 2, 4, 8) for w in outs[2][3])
