@@ -245,6 +245,10 @@ typedef struct abs_options {
                               size bucket (S rounded down to a power of two, S >= 256) times
                               every warps-per-block candidate and keeps the fastest
                               (results are identical); 0: 4 warps per block */
+    int32_t graphs;        /* 1: the Schur-reduced KKT solve (7 launches) is captured into a
+                              CUDA graph on the engine's stream at its second use with a
+                              given set of vectors and replayed from then on */
+    int32_t reserved_opt;
 } abs_options;
 
 void abs_default_options(abs_options* o);
@@ -277,6 +281,8 @@ typedef struct abs_result {
     double warm_theta, cold_theta;  /* constraint violation ||c||_1 at the same two starts */
     int32_t tiles[4];            /* warps per block last used: factor, solve (1 and 2 right-hand
                                     sides), transposed solve */
+    int32_t graph_replays;       /* KKT solves replayed from captured graphs */
+    int32_t reserved_res;
 } abs_result;
 
 /* Diagnostic: measured throughput of dependent-free fused multiply-adds on the current

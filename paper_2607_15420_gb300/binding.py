@@ -70,7 +70,8 @@ class AbsOptions(C.Structure):
                 ("max_ls", C.c_int32), ("verbose", C.c_int32), ("profile", C.c_int32),
                 ("init", C.c_int32), ("soc_max", C.c_int32), ("kappa_soc", C.c_double),
                 ("obj_scaling", C.c_double), ("warm_mu_init", C.c_double), ("warm_bound_push", C.c_double),
-                ("warm_multipliers", C.c_int32), ("autotune", C.c_int32)]
+                ("warm_multipliers", C.c_int32), ("autotune", C.c_int32), ("graphs", C.c_int32),
+                ("reserved_opt", C.c_int32)]
 
 
 class AbsResult(C.Structure):
@@ -83,7 +84,8 @@ class AbsResult(C.Structure):
                 ("base_iters", C.c_int32), ("soc_steps", C.c_int32), ("fp64_fallbacks", C.c_int32),
                 ("base_ms", C.c_double), ("warm_status", C.c_int32), ("reserved", C.c_int32),
                 ("warm_ms", C.c_double), ("warm_E0", C.c_double), ("cold_E0", C.c_double),
-                ("warm_theta", C.c_double), ("cold_theta", C.c_double), ("tiles", C.c_int32 * 4)]
+                ("warm_theta", C.c_double), ("cold_theta", C.c_double), ("tiles", C.c_int32 * 4),
+                ("graph_replays", C.c_int32), ("reserved_res", C.c_int32)]
 
 
 class AbsTrainOptions(C.Structure):

@@ -297,6 +297,20 @@ struct abs_problem {
     } fac;
     Prof prof;
     int autotune = 1;                // tile autotuner on (options.autotune)
+    // the engine's own stream (stream capture needs a non-default stream) and the event
+    // that orders it after the caller's stream
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr;
+    int graphs = 1;                  // replay captured launch sequences (options.graphs)
+    struct GraphEntry {
+        const void* ptr[9];
+        int prec, use_w, tiles[4];
+        int runs;                    // eager runs so far (capture happens on the second)
+        cudaGraphExec_t exec;
+        int64_t nkern;
+    };
+    std::vector<GraphEntry> gcache;
+    int64_t graph_replays = 0;
     int tile[4] = {4, 4, 4, 4};      // warps per block last used: factor, solve, solve x2, solve^T
     int64_t nlaunch = 0;         // kernels launched (every launch is followed by launch_check)
     float* mlp_x = nullptr;          // learned warm start: network inputs [ld][3] and outputs [ld][440]
@@ -408,6 +422,13 @@ abs_status ensure_buffers(abs_problem* h) {
         PSV(h, PS_LSACT, p) = 1.0;
         PSV(h, PS_SD, p) = 1.0;
     }
+    return ABS_OK;
+}
+
+abs_status ensure_stream(abs_problem* h) {
+    if (h->stream) return ABS_OK;
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
     return ABS_OK;
 }
 
@@ -674,8 +695,8 @@ double schur_value(const KKTSys& K, int p, double dw) { return K.Kdd[p] + dw + K
 
 // one Schur-reduced solve for every active problem: rz (z part), rc -> dz (d slots set),
 // dl.  PS_RD, PS_SD, PS_DW must be on the device.  No host round trip.
-abs_status kkt_solve_once(abs_problem* h, const KKTSys& K, const double* x, const double* rz, const double* rc,
-                          double* dz, double* dl, cudaStream_t st) {
+abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, const double* rz, const double* rc,
+                              double* dz, double* dl, cudaStream_t st) {
     abs_status r;
     if ((r = solve_j(h, K.prec, K.jac, x, rc, V(h, V_P), st)) != ABS_OK) return r;
     schur_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q),
@@ -688,6 +709,63 @@ abs_status kkt_solve_once(abs_problem* h, const KKTSys& K, const double* x, cons
                                           dz, V(h, V_G));
     if ((r = launch_check(h)) != ABS_OK) return r;
     return solve_jt(h, K.prec, K.jac, V(h, V_G), dl, st);
+}
+
+// the same, replayed from a CUDA graph on the engine's stream: the launch sequence
+// (7 kernels, with the tile shapes the autotuner chose) is captured on its second use
+// with a given set of vectors and replayed from then on; the per-problem scalars it
+// depends on are read from device memory at replay time
+abs_status kkt_solve_once(abs_problem* h, const KKTSys& K, const double* x, const double* rz, const double* rc,
+                          double* dz, double* dl, cudaStream_t st) {
+    if (!h->graphs || h->prof.on || !h->stream || st != h->stream)
+        return kkt_solve_launches(h, K, x, rz, rc, dz, dl, st);
+    const void* key[9] = {K.jac, K.hes, K.sig, x, rz, rc, dz, dl, h->LU};
+    abs_problem::GraphEntry* ge = nullptr;
+    for (auto& g : h->gcache)
+        if (std::memcmp(g.ptr, key, sizeof(key)) == 0 && g.prec == K.prec && g.use_w == (int)K.use_w &&
+            std::memcmp(g.tiles, h->tile, sizeof(g.tiles)) == 0) {
+            ge = &g;
+            break;
+        }
+    if (!ge) {
+        abs_problem::GraphEntry g{};
+        std::memcpy(g.ptr, key, sizeof(key));
+        g.prec = K.prec;
+        g.use_w = (int)K.use_w;
+        std::memcpy(g.tiles, h->tile, sizeof(g.tiles));
+        h->gcache.push_back(g);
+        ge = &h->gcache.back();
+    }
+    if (!ge->exec && ge->runs < 1) {   // first use: eager (tunes the tile shapes if needed)
+        ge->runs++;
+        abs_status r = kkt_solve_launches(h, K, x, rz, rc, dz, dl, st);
+        std::memcpy(ge->tiles, h->tile, sizeof(ge->tiles));
+        return r;
+    }
+    if (!ge->exec) {
+        const int64_t n0 = h->nlaunch;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        abs_status r = kkt_solve_launches(h, K, x, rz, rc, dz, dl, st);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(st, &graph);
+        if (r != ABS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (e != cudaSuccess) return fail(h, ABS_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&ge->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            ge->exec = nullptr;
+            return fail(h, ABS_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+        }
+        ge->nkern = h->nlaunch - n0;
+        h->nlaunch = n0;
+    }
+    CK(cudaGraphLaunch(ge->exec, st));
+    h->nlaunch += ge->nkern;
+    h->graph_replays++;
+    return ABS_OK;
 }
 
 // solve with FP64 iterative refinement on the full KKT residual of every active problem.
@@ -851,6 +929,7 @@ void abs_default_options(abs_options* o) {
     o->warm_mu_init = 1e-3;
     o->warm_bound_push = 1e-8;
     o->autotune = 1;
+    o->graphs = 1;
 }
 
 abs_status absorber_create(const abs_params* p, const double* feeds, const double* prob, int64_t S,
@@ -894,6 +973,10 @@ void absorber_destroy(abs_problem* h) {
     absorber_destroy(h->base);
     absorber_destroy(h->batch);
     for (auto e : h->prof.pool) cudaEventDestroy(e);
+    for (auto& g : h->gcache)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->stream) cudaStreamDestroy(h->stream);
     cudaFree(h->feed);
     cudaFree(h->pid);
     cudaFree(h->mlp_x);

@@ -139,3 +139,21 @@ def test_autotuned_tiles_give_identical_results(B):
     assert np.array_equal(outs[0][2], outs[1][2]) and np.array_equal(outs[1][2], outs[2][2])
     assert outs[0][3] == [4, 4, 4, 4]
     assert all(w in (1, 2, 4, 8) for w in outs[2][3])
+
+
+def test_graph_replay_gives_identical_results(B):
+    # the Schur-reduced KKT solve replayed from a captured CUDA graph runs the same
+    # kernels with the same arguments: the solve is the same bit for bit
+    import torch
+    F = ai.make_feeds(300, 1)
+    prob = B.Problem(P, F)
+    outs = []
+    for graphs in (0, 1):
+        x = torch.zeros(prob.n_primal, dtype=torch.float64, device="cuda")
+        o = B.default_options(precision=1, max_refine=8, graphs=graphs)
+        r = prob.ipm_solve(o, x_out=x)
+        assert r.status == 0
+        outs.append((r.iters, r.d, _host(x), r.graph_replays))
+    assert outs[0][3] == 0 and outs[1][3] > outs[1][0]
+    assert outs[0][0] == outs[1][0] and outs[0][1] == outs[1][1]
+    assert np.array_equal(outs[0][2], outs[1][2])
