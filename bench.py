@@ -1,15 +1,20 @@
 #!/usr/bin/env python
 """Benchmark: Newton steps/s and solve time of the interior-point solve of the
 5000-scenario absorber design problem (seeded truncated-normal feeds, sigma 5 %, cut at
-+-15 %, seed 2), on the GB300 path, at KKT tolerance E_0 <= 1e-8.
++-15 %, seed 2) on the GB300 path at KKT tolerance E_0 <= 1e-8, against the FP64 GPU
+path.
 
-One "step" is one full interior-point solve from the default start to E_0 <= 1e-8: every
-Newton iteration runs the whole hot path (fused evaluation, block-LU factorization,
-Schur complement on d, block solves, refinement, line search).  value = Newton
-iterations of the K timed solves / their device time.  Prints one JSON line.
+One "step" is one full interior-point solve to E_0 <= 1e-8: every Newton iteration runs
+the whole hot path (fused evaluation, block-LU factorization, Schur complement on d,
+block solves, refinement, line search).  The timed form (--form) defaults to FP32 block
+factors with FP64 refinement from the learned warm start (the network is trained once
+in the run, untimed, on 20,000 single-scenario solves); the other forms -- the plain FP64
+path from the default start among them -- are timed alongside under "forms".
+value = Newton iterations of the K timed solves / their device time.  Prints one JSON
+line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision fp32|fp64] [--workload NAME]
+                  [--form learned-fp32|learned-fp64|fp32|fp64] [--workload NAME]
 """
 from __future__ import annotations
 
@@ -170,11 +175,12 @@ def timed(fn, reps):
     return a.elapsed_time(b) / 1e3 / reps, out
 
 
-def learned_forms(B, ai, prob_main, reps, n_train=20000, epochs=100):
-    """The learned warm start: train the network on n_train single-scenario solves (one
-    batched solve), then solve the headline workload and the 20,000-scenario workload
-    from the learned start (FP32 factors + FP64 refinement, and FP64) against the plain
-    FP64 path from the default start."""
+FORMS = {"fp64": (0, False), "fp32": (1, False), "learned-fp64": (0, True), "learned-fp32": (1, True)}
+
+
+def train_network(B, ai, n_train=20000, epochs=100):
+    """The warm-start network, trained on n_train single-scenario solves (one batched
+    solve from a shared expected-value start) by the library's own kernels."""
     import torch
     P = ai.PARAMS
     t0 = time.perf_counter()
@@ -191,33 +197,39 @@ def learned_forms(B, ai, prob_main, reps, n_train=20000, epochs=100):
     t1 = time.perf_counter()
     hist = net.train(X, Y, B.train_options(epochs=epochs, batch=256, lr=2e-3, lr_final=2e-5, seed=5))
     t_train = time.perf_counter() - t1
-    del batch, x, y
-    out = {"training": {"single_scenario_solves": n_train, "converged": int(sum(keep)), "rows": int(X.shape[0]),
-                        "solve_s": t_data, "epochs": epochs, "train_s": t_train,
-                        "loss_first_last": [float(hist[0]), float(hist[-1])]}}
+    info = {"single_scenario_solves": n_train, "converged": int(sum(keep)), "rows": int(X.shape[0]),
+            "solve_s": t_data, "epochs": epochs, "train_s": t_train,
+            "loss_first_last": [float(hist[0]), float(hist[-1])]}
+    return net, info
 
-    def o(prec):
-        return B.default_options(precision=prec, max_refine=(8 if prec == B.PREC_FP32 else 0))
 
-    cases = [("headline", prob_main), ("absorber-S20000-u10-seed4", None)]
-    for name, pr in cases:
-        if pr is None:
-            pr = B.Problem(P, ai.workload_feeds(name))
-        entry = {"scenarios": pr.S}
-        for label, prec, learned in (("fp64_cold", B.PREC_FP64, False), ("fp32_cold", B.PREC_FP32, False),
-                                     ("fp64_learned", B.PREC_FP64, True), ("fp32_learned", B.PREC_FP32, True)):
-            fn = (lambda: B.ipm_solve_learned(pr, net, o(prec))) if learned else (lambda: pr.ipm_solve(o(prec)))
-            fn()
-            sec, rs = timed(fn, reps)
-            r = rs[0]
-            entry[label] = {"solve_time_s": sec, "iters": r.iters, "base_iters": r.base_iters,
-                            "status": r.status, "E0": r.E0, "d": r.d,
-                            "learned_start_used": bool(r.warm_status) if learned else None,
-                            "fp64_fallbacks": r.fp64_fallbacks}
-        base = entry["fp64_cold"]["solve_time_s"]
-        for k in ("fp32_cold", "fp64_learned", "fp32_learned"):
-            entry[k]["speedup_vs_fp64_cold"] = base / entry[k]["solve_time_s"]
-        out[name] = entry
+def options(B, prec, profile=0, graphs=1):
+    return B.default_options(precision=prec, max_refine=(8 if prec == B.PREC_FP32 else 0), profile=profile,
+                             graphs=graphs)
+
+
+def solve_form(B, prob, net, form, profile=0, graphs=1, x_out=None):
+    prec, learned = FORMS[form]
+    o = options(B, prec, profile, graphs)
+    if learned:
+        return B.ipm_solve_learned(prob, net, o, x_out=x_out)
+    return prob.ipm_solve(o, x_out=x_out)
+
+
+def compare_forms(B, prob, net, reps):
+    """Every form on one problem, each after one untimed solve; solve time from CUDA
+    events around reps solves."""
+    out = {"scenarios": prob.S}
+    for form in ("fp64", "fp32", "learned-fp64", "learned-fp32"):
+        solve_form(B, prob, net, form)
+        sec, rs = timed(lambda: solve_form(B, prob, net, form), reps)
+        r = rs[0]
+        out[form] = {"solve_time_s": sec, "iters": r.iters, "base_iters": r.base_iters, "status": r.status,
+                     "E0": r.E0, "d": r.d, "fp64_fallbacks": r.fp64_fallbacks,
+                     "learned_start_used": bool(r.warm_status) if FORMS[form][1] else None}
+    base = out["fp64"]["solve_time_s"]
+    for form in ("fp32", "learned-fp64", "learned-fp32"):
+        out[form]["speedup_vs_fp64"] = base / out[form]["solve_time_s"]
     return out
 
 
@@ -250,7 +262,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp32", "fp64"])
+    ap.add_argument("--form", default="learned-fp32", choices=list(FORMS))
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -285,9 +297,9 @@ def main():
     P = ai.PARAMS
     # replicas: every rank solves its own instance of the workload (independent problems)
     F = ai.workload_feeds(args.workload)
-    prec = B.PREC_FP32 if args.precision == "fp32" else B.PREC_FP64
     prob = B.Problem(P, F)
     st = torch.cuda.current_stream()
+    prec, learned = FORMS[args.form]
 
     if args.capture_iters > 0:
         r = prob.ipm_solve(B.default_options(precision=prec, max_refine=(8 if prec == B.PREC_FP32 else 0),
@@ -296,11 +308,15 @@ def main():
         print(f"capture case: {r.iters} iterations, status {B.STATUS.get(r.status)}", flush=True)
         return
 
-    def opts(profile=0, p=prec):
-        return B.default_options(precision=p, max_refine=(8 if p == B.PREC_FP32 else 0), profile=profile)
+    net, train_info = (None, None)
+    if learned or not args.no_forms:
+        net, train_info = train_network(B, ai)
+
+    def step(profile=0, graphs=1, x_out=None):
+        return solve_form(B, prob, net, args.form, profile, graphs, x_out)
 
     for _ in range(args.warmup):
-        r = prob.ipm_solve(opts())
+        r = step()
         assert r.status == 0, f"warm-up solve failed: {B.STATUS.get(r.status)}"
 
     # ---- timed region: K full solves --------------------------------------------------
@@ -310,9 +326,11 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")      # lets a profiler select the timed solves
     e0.record(st)
-    results = [prob.ipm_solve(opts(profile=1)) for _ in range(args.steps)]
+    results = [step() for _ in range(args.steps)]
     e1.record(st)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -333,11 +351,14 @@ def main():
         t_job, it_job = t_local, float(iters)
     value = it_job / t_job
 
-    # ---- per-kernel roofline (CUDA events around each hot launch, inside the timed solves)
+    # ---- per-kernel roofline: CUDA events around each hot launch in profiled solves of
+    # the same form (profiling disables graph replay; these solves are not the timed ones)
+    prof = [step(profile=1) for _ in range(2)]
     es = 4 if prec == B.PREC_FP32 else 8
     hbm, hbm_src = load_peaks()
-    kms = [sum(r.kernel_ms[k] for r in results) for k in range(5)]
-    kn = [sum(r.kernel_launches[k] for r in results) for k in range(5)]
+    kms = [sum(r.kernel_ms[k] for r in prof) for k in range(5)]
+    kn = [sum(r.kernel_launches[k] for r in prof) for k in range(5)]
+    prof_ms = sum(r.solve_ms for r in prof)
     Sx = prob.S
     work = {  # (flops, bytes) per launch
         "eval": (None, EVAL_BYTES_PER_SCEN * Sx),
@@ -355,7 +376,7 @@ def main():
             continue
         avg_s = kms[k] / kn[k] / 1e3
         fl, by = work[name]
-        kern[name] = {"launches": kn[k], "avg_us": 1e6 * avg_s, "share_of_solve": kms[k] / ms,
+        kern[name] = {"launches": kn[k], "avg_us": 1e6 * avg_s, "share_of_solve": kms[k] / prof_ms,
                       "GB_s": by / avg_s / 1e9, "GFLOP_s": (fl / avg_s / 1e9) if fl else None}
     dom = max(kern, key=lambda n: kms[B.KERNELS.index(n)])
     dk = kern[dom]
@@ -369,7 +390,7 @@ def main():
                                 "nominal FP64 1.25 TFLOP/s of the GB300 table")}
     else:
         roof = {"bound": "hbm", "achieved": dk["GB_s"], "peak": hbm, "unit": "GB/s", "frac": dk["GB_s"] / hbm,
-                "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json)"}
+                "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json), of measured"}
     roof.update({"kernel": dom, "traffic": None, "algorithmic_bytes_per_launch": by,
                  "algorithmic_flops_per_launch": fl})
 
@@ -386,7 +407,7 @@ def main():
         for _ in range(args.steps):
             dfe.copy_(hf, non_blocking=True)          # H2D of the step's inputs
             prob.set_feeds(dfe)
-            r = prob.ipm_solve(opts(), x_out=xo)
+            r = step(x_out=xo)
             xh.copy_(xo, non_blocking=True)           # D2H of the step's result
             torch.cuda.synchronize()
             assert r.status == 0
@@ -395,22 +416,17 @@ def main():
         e2e = {"value": eit / te, "unit": UNIT, "h2d_bytes_per_step": int(F.nbytes),
                "d2h_bytes_per_step": int(prob.n_primal * 8), "solve_time_s": te / args.steps}
 
-    # ---- the other precision path, for the comparison the metric names ------------------
-    other_p = B.PREC_FP64 if prec == B.PREC_FP32 else B.PREC_FP32
-    torch.cuda.synchronize()
-    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2.record(st)
-    ro = [prob.ipm_solve(opts(p=other_p)) for _ in range(2)]
-    e3.record(st)
-    torch.cuda.synchronize()
-    oms = e2.elapsed_time(e3)
-    other = {"precision": "fp64" if other_p == B.PREC_FP64 else "fp32+fp64-refinement",
-             "value": sum(r.iters for r in ro) / (oms / 1e3), "solve_time_s": oms / 2e3,
-             "iters": [r.iters for r in ro], "d": ro[0].d, "status": [r.status for r in ro]}
-
     forms = None
     if rank == 0 and not args.no_forms:
-        forms = {"learned_warm_start": learned_forms(B, ai, prob, reps=3), "batched": batched_form(B, ai, reps=2)}
+        forms = {"training": train_info, "headline_workload": compare_forms(B, prob, net, reps=3)}
+        # graph replay on / off for the timed form
+        sec_off, _ = timed(lambda: step(graphs=0), 3)
+        forms["graphs"] = {"form": args.form, "solve_time_s_graphs_on": t_job / args.steps,
+                           "solve_time_s_graphs_off": sec_off}
+        p20 = B.Problem(P, ai.workload_feeds("absorber-S20000-u10-seed4"))
+        forms["absorber-S20000-u10-seed4"] = compare_forms(B, p20, net, reps=2)
+        del p20
+        forms["batched"] = batched_form(B, ai, reps=2)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -421,6 +437,7 @@ def main():
                          f"scenarios ({rb['seconds']:.1f} s), per-iteration cost scaled linearly to {Sx}"}
 
     if rank == 0:
+        r0 = results[0]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -428,18 +445,22 @@ def main():
             "dtype": "f32+f64" if prec == B.PREC_FP32 else "f64",
             "data": "synthetic (seeded feeds; the paper's measured cases are not published)",
             "config": {"workload": args.workload, "scenarios": Sx, "variables": int(prob.sizes.n_var_paper),
-                       "tol": 1e-8, "precision": args.precision,
-                       "step": "one full interior-point solve from the default start to E_0 <= 1e-8",
+                       "tol": 1e-8, "form": args.form,
+                       "step": ("one full interior-point solve to E_0 <= 1e-8 from the "
+                                + ("learned warm start (network trained in the run, untimed)" if learned
+                                   else "default start")),
                        "parallelism": f"replicas x{world}",
                        "l2": "working set > L2 (factors + Jacobian values ~ 0.3-0.6 GB per iteration)"},
             "solve_time_s": ms / 1e3 / args.steps,
             "iters_per_solve": [r.iters for r in results],
-            "d_opt": results[0].d, "E0": max(r.E0 for r in results),
-            "phase_ms_per_solve": {n: sum(r.phase_ms[i] for r in results) / args.steps
+            "learned_start_used": [bool(r.warm_status) for r in results] if learned else None,
+            "d_opt": r0.d, "E0": max(r.E0 for r in results),
+            "tiles": list(r0.tiles), "graph_replays_per_solve": r0.graph_replays,
+            "phase_ms_per_solve": {n: sum(r.phase_ms[i] for r in prof) / len(prof)
                                    for i, n in enumerate(B.PHASES)},
             "kernels": kern, "roofline": roof,
             "fma_peaks_gflops": {"fp64": fma64, "fp32": fma32},
-            "other_precision": other, "forms": forms,
+            "forms": forms,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": int(sum(r.launches for r in results)),
         }

@@ -247,7 +247,7 @@ struct Prof {
 
 constexpr int KMAX = 9;          // partial values per (scenario, stage) thread, at most
 constexpr int PS_RING = 16;      // pinned staging buffers for per-problem scalar uploads
-constexpr int CHUNK = 2048;      // reduction elements per chunk
+constexpr int CHUNK = RED_CHUNK;  // reduction elements per chunk
 
 struct abs_problem {
     int dev = 0;
@@ -480,12 +480,11 @@ RedOps make_ops(std::initializer_list<int> l) {
 // h->hred + KMAX * NP, in one round trip
 abs_status reduce(abs_problem* h, cudaStream_t st, int K, const RedOps& ops, int flag, bool fetch,
                   const double* dslots = nullptr) {
-    chunk_reduce_kernel<<<(unsigned)h->nchunk, 256, 0, st>>>(h->part, h->ld, K, ops, h->chunks, h->nchunk, h->ps,
-                                                             h->NP, flag, h->cred);
+    chunk_reduce_kernel<<<(unsigned)h->nchunk, RED_T, 0, st>>>(h->part, h->ld, K, ops, h->chunks, h->nchunk, h->ps,
+                                                               h->NP, flag, h->cred);
     abs_status r = launch_check(h);
     if (r != ABS_OK) return r;
-    problem_reduce_kernel<<<(unsigned)((h->NP + 127) / 128), 128, 0, st>>>(h->cred, h->nchunk, K, ops, h->pchunk,
-                                                                            h->NP, h->red);
+    problem_reduce_kernel<<<(unsigned)h->NP, 32, 0, st>>>(h->cred, h->nchunk, K, ops, h->pchunk, h->NP, h->red);
     if ((r = launch_check(h)) != ABS_OK) return r;
     if (!fetch) return ABS_OK;
     CK(cudaMemcpyAsync(h->hred, h->red, sizeof(double) * (size_t)K * h->NP, cudaMemcpyDeviceToHost, st));

@@ -432,44 +432,71 @@ __global__ void max_abs_kernel(int S, int64_t ld, const BView b, const double* _
 // ---- reductions per problem ---------------------------------------------------------
 // chunk c covers elements [i0, i1) of problem p (element i: stage i / S_p, slot off_p +
 // i % S_p); one block per chunk, fixed-order tree; out[k * nchunk + c]
-__global__ void __launch_bounds__(256) chunk_reduce_kernel(const double* __restrict__ part, int64_t ld, int K,
-                                                           const RedOps ops, const int* __restrict__ ch,
-                                                           int nchunk, const double* __restrict__ ps, int NP,
-                                                           int flag, double* __restrict__ out) {
-    __shared__ double sm[256];
+constexpr int RED_T = 128;                  // threads per chunk block
+constexpr int RED_PER = 4;                  // elements per thread and plane
+constexpr int RED_CHUNK = RED_T * RED_PER;  // elements per chunk
+constexpr int RED_KMAX = 12;
+
+__device__ inline double warp_red(int op, double a) {
+    // xor tree: every lane ends with the same value (each pair is combined in both orders
+    // by commutative operations), in a fixed order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = red_op(op, a, __shfl_xor_sync(0xffffffffu, a, o));
+    return a;
+}
+
+// one block per chunk of a problem's (stage, slot) elements: every plane k < K reduced in
+// a fixed order (4 elements per thread, xor trees within warps, warps in order)
+__global__ void __launch_bounds__(RED_T) chunk_reduce_kernel(const double* __restrict__ part, int64_t ld, int K,
+                                                             const RedOps ops, const int* __restrict__ ch,
+                                                             int nchunk, const double* __restrict__ ps, int NP,
+                                                             int flag, double* __restrict__ out) {
+    __shared__ double sm[RED_T / 32][RED_KMAX];
     const int c = blockIdx.x;
     const int p = ch[5 * c + 0], off = ch[5 * c + 1], Sp = ch[5 * c + 2], i0 = ch[5 * c + 3], i1 = ch[5 * c + 4];
     const bool live = !ps || ps[(int64_t)flag * NP + p] != 0.0;
     const int64_t plane = (int64_t)N_STAGES * ld;
+    int64_t idx[RED_PER];
+    bool ok[RED_PER];
+#pragma unroll
+    for (int t = 0; t < RED_PER; ++t) {
+        const int i = i0 + (int)threadIdx.x + RED_T * t;
+        ok[t] = live && i < i1;
+        idx[t] = ok[t] ? (int64_t)(i / Sp) * ld + off + i % Sp : 0;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int k = 0; k < K; ++k) {
         const int op = ops.op[k];
         double a = red_id(op);
-        if (live) {
-            for (int i = i0 + (int)threadIdx.x; i < i1; i += blockDim.x) {
-                const int n = i / Sp, s = off + i % Sp;
-                a = red_op(op, a, part[(int64_t)k * plane + (int64_t)n * ld + s]);
-            }
-        }
-        sm[threadIdx.x] = a;
-        __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) sm[threadIdx.x] = red_op(op, sm[threadIdx.x], sm[threadIdx.x + o]);
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[(int64_t)k * nchunk + c] = sm[0];
-        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < RED_PER; ++t)
+            if (ok[t]) a = red_op(op, a, part[(int64_t)k * plane + idx[t]]);
+        a = warp_red(op, a);
+        if (lane == 0) sm[warp][k] = a;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < K) {
+        const int k = threadIdx.x, op = ops.op[k];
+        double a = red_id(op);
+#pragma unroll
+        for (int w = 0; w < RED_T / 32; ++w) a = red_op(op, a, sm[w][k]);
+        out[(int64_t)k * nchunk + c] = a;
     }
 }
 
-// per problem: combine its chunks in order; out[k * NP + p]
-__global__ void problem_reduce_kernel(const double* __restrict__ cout, int nchunk, int K, const RedOps ops,
-                                      const int* __restrict__ pchunk, int NP, double* __restrict__ out) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+// one warp per problem: combine its chunks in a fixed order; out[k * NP + p]
+__global__ void __launch_bounds__(32) problem_reduce_kernel(const double* __restrict__ cout, int nchunk, int K,
+                                                            const RedOps ops, const int* __restrict__ pchunk, int NP,
+                                                            double* __restrict__ out) {
+    const int p = blockIdx.x, lane = threadIdx.x;
     if (p >= NP) return;
+    const int c0 = pchunk[p], c1 = pchunk[p + 1];
     for (int k = 0; k < K; ++k) {
-        double a = red_id(ops.op[k]);
-        for (int c = pchunk[p]; c < pchunk[p + 1]; ++c) a = red_op(ops.op[k], a, cout[(int64_t)k * nchunk + c]);
-        out[(int64_t)k * NP + p] = a;
+        const int op = ops.op[k];
+        double a = red_id(op);
+        for (int c = c0 + lane; c < c1; c += 32) a = red_op(op, a, cout[(int64_t)k * nchunk + c]);
+        a = warp_red(op, a);
+        if (lane == 0) out[(int64_t)k * NP + p] = a;
     }
 }
 
