@@ -161,6 +161,21 @@ def run_reference(args, S_full):
     print(json.dumps(line), flush=True)
 
 
+def job_totals(t_local, iters_local, world, device):
+    """Whole-job time and work of N replicas: the slowest rank's time, every rank's
+    iterations (one all-reduce each; no collective on the data path)."""
+    import torch
+    if world <= 1:
+        return t_local, iters_local
+    import torch.distributed as dist
+    t = torch.tensor([t_local, iters_local], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    isum = t.clone()
+    dist.all_reduce(isum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(isum[1])
+
+
 def timed(fn, reps):
     """Device time (CUDA events on the current stream) of reps calls of fn; returns
     (seconds per call, results)."""
@@ -340,15 +355,7 @@ def main():
         assert r.status == 0 and r.E0 <= 1e-8, (r.status, r.E0)
     iters = sum(r.iters for r in results)
     t_local = ms / 1e3
-    t = torch.tensor([t_local, float(iters)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        isum = t.clone()
-        dist.all_reduce(isum, op=dist.ReduceOp.SUM)
-        t_job, it_job = float(tmax[0]), float(isum[1])
-    else:
-        t_job, it_job = t_local, float(iters)
+    t_job, it_job = job_totals(t_local, float(iters), world, "cuda")
     value = it_job / t_job
 
     # ---- per-kernel roofline: CUDA events around each hot launch in profiled solves of

@@ -200,3 +200,20 @@ def test_learned_warm_start_rejects_a_bad_network(B):
     warm = B.ipm_solve_learned(prob, net, o)
     assert warm.warm_status == 0 and warm.status == 0
     assert warm.iters == cold.iters and abs(warm.d - cold.d) <= 1e-12 * cold.d
+
+
+def test_learned_warm_start_full_size_s20000(B):
+    # the 20,000-scenario workload from the learned start with FP32 factors: the same
+    # optimum as the FP64 path from the default start, in fewer iterations
+    X, Y, _ = _training_set(B, 4000, 7)
+    net = B.MLP(seed=11)
+    net.fit_normalization(X, Y)
+    net.train(X, Y, B.train_options(epochs=60, batch=256, lr=2e-3, lr_final=2e-5, seed=5))
+    F = ai.workload_feeds("absorber-S20000-u10-seed4")
+    prob = B.Problem(P, F)
+    cold = prob.ipm_solve(B.default_options())
+    warm = B.ipm_solve_learned(prob, net, B.default_options(precision=1, max_refine=8))
+    assert cold.status == 0 and warm.status == 0 and warm.E0 <= 1e-8
+    assert warm.warm_status == 1
+    assert abs(warm.d - cold.d) <= 1e-6 * cold.d
+    assert warm.iters < cold.iters + cold.base_iters

@@ -246,3 +246,26 @@ def test_error_paths(B):
     assert res.status == -6 and res.iters == 3               # iteration limit is reported
     o = B.default_options(tol=-1.0)
     assert prob.ipm_solve(o).status == -1
+
+
+def test_full_size_s5000_mixed_precision_properties(B):
+    # the bench workload (5000 scenarios, truncated-normal feeds) with FP32 factors and
+    # FP64 refinement: properties that fix the optimum at any size
+    F = ai.workload_feeds("absorber-S5000-tn5-seed2")
+    prob, res, Z, d, lam = _gpu_solve(B, F, prec=1)
+    assert res.status == 0 and res.E0 <= 1e-8
+    dmin, vol = checks.minimum_diameter(P, F, Z)
+    assert abs(d - dmin) <= 1e-8 * dmin
+    arg = int(np.unravel_index(np.argmax(vol), vol.shape)[0])
+    rng = np.random.default_rng(17)
+    sample = np.unique(np.concatenate([[arg, 0, 4999], rng.choice(5000, 5, replace=False)]))
+    Zn, hist = checks.mesh_newton(P, F[:, sample], Z[sample], d, iters=5)
+    assert hist[-1] <= 1e-12
+    keep = np.ones(model.NS, dtype=bool)
+    keep[model.NV - 1::model.NV] = False
+    assert np.max(np.abs(Zn[:, keep] - Z[sample][:, keep]) / np.maximum(1, np.abs(Zn[:, keep]))) <= 1e-6
+    el_in, el_out, h_in, h_out = checks.column_balances(P, F, Z)
+    np.testing.assert_allclose(el_out, el_in, rtol=0, atol=1e-8 * np.abs(el_in).max())
+    # one active hydraulic row: the binding scenario's multiplier carries the objective
+    lh = lam.reshape(5000, model.N, model.NV)[:, :, model.NV - 1]
+    assert abs(lh.sum() * P["u_max"] * math.pi * d / 2.0 - 1.0) <= 1e-6
