@@ -13,6 +13,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <string>
 #include <vector>
 
@@ -574,9 +575,16 @@ abs_status tuned_launch(abs_problem* h, int kind, int es, std::initializer_list<
     return launch(w);
 }
 
-template <class T, int W>
+// factor launch shape: W warps per block; for FP32, W + FACTOR_REG selects the
+// register-resident variant (same arithmetic in the same order)
+constexpr int FACTOR_REG = 16;
+
+template <class T, int W, bool REG>
 void factor_w(abs_problem* h, const double* jac, double pivtol, cudaStream_t st) {
-    if constexpr (factor_fits<T, W>())
+    if constexpr (REG && std::is_same<T, float>::value)
+        factor_reg_kernel<W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (float*)h->LU, h->piv,
+                                                             (float*)h->G, h->sing, pivtol);
+    else if constexpr (!REG && factor_fits<T, W>())
         factor_warp_kernel<T, W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (T*)h->LU, h->piv,
                                                                 (T*)h->G, h->sing, pivtol);
 }
@@ -586,15 +594,24 @@ abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaS
     prof_begin(h, K_FACTOR, st);
     auto go = [&](int w) {
         switch (w) {
-            case 1: factor_w<T, 1>(h, jac, pivtol, st); break;
-            case 2: factor_w<T, 2>(h, jac, pivtol, st); break;
-            case 8: factor_w<T, 8>(h, jac, pivtol, st); break;
-            default: factor_w<T, 4>(h, jac, pivtol, st); break;
+            case 1: factor_w<T, 1, false>(h, jac, pivtol, st); break;
+            case 2: factor_w<T, 2, false>(h, jac, pivtol, st); break;
+            case 8: factor_w<T, 8, false>(h, jac, pivtol, st); break;
+            case FACTOR_REG + 1: factor_w<T, 1, true>(h, jac, pivtol, st); break;
+            case FACTOR_REG + 2: factor_w<T, 2, true>(h, jac, pivtol, st); break;
+            case FACTOR_REG + 4: factor_w<T, 4, true>(h, jac, pivtol, st); break;
+            case FACTOR_REG + 8: factor_w<T, 8, true>(h, jac, pivtol, st); break;
+            default: factor_w<T, 4, false>(h, jac, pivtol, st); break;
         }
         return launch_check(h);
     };
-    abs_status r = factor_fits<T, 8>() ? tuned_launch(h, TK_FACTOR, sizeof(T), {1, 2, 4, 8}, WPB_F, go, st)
-                                       : tuned_launch(h, TK_FACTOR, sizeof(T), {1, 2, 4}, WPB_F, go, st);
+    abs_status r;
+    if (std::is_same<T, float>::value)
+        r = tuned_launch(h, TK_FACTOR, sizeof(T),
+                         {1, 2, 4, 8, FACTOR_REG + 1, FACTOR_REG + 2, FACTOR_REG + 4, FACTOR_REG + 8}, WPB_F, go, st);
+    else
+        r = factor_fits<T, 8>() ? tuned_launch(h, TK_FACTOR, sizeof(T), {1, 2, 4, 8}, WPB_F, go, st)
+                                : tuned_launch(h, TK_FACTOR, sizeof(T), {1, 2, 4}, WPB_F, go, st);
     prof_end(h, st);
     return r;
 }

@@ -49,6 +49,23 @@ __device__ inline unsigned long long abs_key(float a) {
 __device__ inline double key_value(unsigned long long k, double) { return __longlong_as_double((long long)k); }
 __device__ inline float key_value(unsigned long long k, float) { return __uint_as_float((unsigned)k); }
 
+// warp maximum of 64-bit keys with the hardware 32-bit warp reduction: the high words
+// first, then the low words among the lanes holding the highest high word
+__device__ inline unsigned long long warp_max_key(unsigned long long key) {
+    const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+    const unsigned mh = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_max_sync(0xffffffffu, hi == mh ? lo : 0u);
+    return ((unsigned long long)mh << 32) | ml;
+}
+
+// pivot row: the lowest candidate lane whose key is the largest among the candidates
+// (every lane takes part; candidates have cand = true)
+__device__ inline int warp_argmax_key(unsigned long long key, bool cand) {
+    const unsigned long long m = warp_max_key(cand ? key : 0ull);
+    const unsigned won = __ballot_sync(0xffffffffu, cand && key == m);
+    return __ffs((int)won) - 1;
+}
+
 // reciprocal: FP32 seed refined by two Newton steps r <- r (2 - a r) in T (|a| in the
 // normal FP32 range; exact division otherwise)
 __device__ inline double recip(double a) {
@@ -99,6 +116,48 @@ struct LUPrefetch {
     }
 };
 
+// assemble stage n's augmented block [A_n | B_n] of scenario s in shared memory (own
+// entries, the super-diagonal coupling B_n, the Schur update A_n -= C_n G_{n-1}) and
+// return the threshold below which a pivot marks the block singular
+template <class T>
+__device__ inline T assemble_stage(int n, int64_t ld, int s, int lane, const double* __restrict__ jac, double pivtol,
+                                   T (*A)[PADA], const T (*Gp)[NABV]) {
+    const int t = stage_type(n);
+    const int base = c_segJ[n];
+    for (int e = lane; e < NV * NCA; e += 32) A[e / NCA][e % NCA] = T(0);
+    __syncwarp();
+    for (int k = lane; k < c_nown[t]; k += 32) {
+        const Ent e = c_own[t][k];
+        A[e.r][e.c] = (T)jac[(int64_t)(base + e.slot) * ld + s];
+    }
+    if (n + 1 < N_STAGES) {
+        for (int k = lane; k < c_nabv[t]; k += 32) {
+            const Ent e = c_abv[t][k];
+            A[e.r][NV + e.c] = (T)jac[(int64_t)(base + e.slot) * ld + s];
+        }
+    }
+    __syncwarp();
+    // Schur update with the previous stage: A_n -= C_n G_{n-1}
+    if (n > 0) {
+        const int nq = c_nblw[t];
+        const T cvq = load_coupling<T>(c_blw[t], nq, base, jac, ld, s, lane);
+        for (int k = 0; k < nq; ++k) {
+            const Ent e = c_blw[t][k];
+            const T cv = shfl(cvq, k);
+            if (lane < NABV) A[e.r][abv_var(lane)] -= cv * Gp[blw_var(e.c)][lane];
+            __syncwarp();
+        }
+    }
+    // largest entry of the block (for the singularity test)
+    unsigned long long kmax = 0ull;
+    for (int e = lane; e < NV * NV; e += 32) {
+        const unsigned long long kk = abs_key(A[e / NV][e % NV]);
+        kmax = kk > kmax ? kk : kmax;
+    }
+    kmax = warp_max_key(kmax);
+    return (T)pivtol * key_value(kmax, T(0));
+}
+
 template <class T, int WPB = WPB_F>
 __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld, const BView b,
                                                                  const double* __restrict__ jac, T* __restrict__ LU,
@@ -114,63 +173,16 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
     T(*Gp)[NABV] = sG[warp];
     int singular = 0;
     for (int n = 0; n < N_STAGES; ++n) {
-        const int t = stage_type(n);
-        const int base = c_segJ[n];
-        for (int e = lane; e < NV * NCA; e += 32) A[e / NCA][e % NCA] = T(0);
-        __syncwarp();
-        for (int k = lane; k < c_nown[t]; k += 32) {
-            const Ent e = c_own[t][k];
-            A[e.r][e.c] = (T)jac[(int64_t)(base + e.slot) * ld + s];
-        }
-        if (n + 1 < N_STAGES) {
-            for (int k = lane; k < c_nabv[t]; k += 32) {
-                const Ent e = c_abv[t][k];
-                A[e.r][NV + e.c] = (T)jac[(int64_t)(base + e.slot) * ld + s];
-            }
-        }
-        __syncwarp();
-        // Schur update with the previous stage: A_n -= C_n G_{n-1}
-        if (n > 0) {
-            const int nq = c_nblw[t];
-            const T cvq = load_coupling<T>(c_blw[t], nq, base, jac, ld, s, lane);
-            for (int k = 0; k < nq; ++k) {
-                const Ent e = c_blw[t][k];
-                const T cv = shfl(cvq, k);
-                if (lane < NABV) A[e.r][abv_var(lane)] -= cv * Gp[blw_var(e.c)][lane];
-                __syncwarp();
-            }
-        }
-        // largest entry of the block (for the singularity test)
-        unsigned long long kmax = 0ull;
-        for (int e = lane; e < NV * NV; e += 32) {
-            const unsigned long long kk = abs_key(A[e / NV][e % NV]);
-            kmax = kk > kmax ? kk : kmax;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, kmax, o);
-            kmax = k2 > kmax ? k2 : kmax;
-        }
-        const T tiny = (T)pivtol * key_value(kmax, T(0));
+        const T tiny = assemble_stage<T>(n, ld, s, lane, jac, pivtol, A, Gp);
         const unsigned long long ktiny = abs_key(tiny);
         unsigned char* pv = piv + pv_off(s, n);
         // LU with partial pivoting, row operations on all 33 columns
         for (int k = 0; k < NV; ++k) {
             // key 0 marks lanes outside the candidate rows (an exact zero candidate also has
             // key 0 and loses ties to lower rows: the singular test below catches it)
-            unsigned long long v = (lane >= k && lane < NV) ? abs_key(A[lane][k]) : 0ull;
-            int idx = (lane >= k && lane < NV) ? lane : NV;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long v2 = __shfl_xor_sync(0xffffffffu, v, o);
-                const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-                if (v2 > v || (v2 == v && i2 < idx)) {
-                    v = v2;
-                    idx = i2;
-                }
-            }
-            if (idx >= NV) idx = k;
-            const int p = idx;
+            const bool cand = lane >= k && lane < NV;
+            int p = warp_argmax_key(cand ? abs_key(A[lane][k]) : 0ull, cand);
+            if (p < 0 || p >= NV) p = k;
             if (lane == 0) pv[k] = (unsigned char)p;
             if (p != k) {
                 for (int j = lane; j < NCA; j += 32) {
@@ -218,6 +230,97 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
             }
         }
         T* Ln = LU + lu_off(s, n);
+        for (int e = lane; e < NV * NV; e += 32) Ln[e] = A[e / NV][e % NV];
+        __syncwarp();
+    }
+    if (lane == 0) sing[s] = singular;
+}
+
+// FP32 variant with the block in registers: lane i < 22 holds row i of [A_n | B_n] (33
+// values); the pivot search is a warp max over the rows' keys, the row swap and the pivot
+// row's broadcast are shuffles, the rank-1 update runs on registers, and G_n comes from a
+// shuffle-driven back substitution.  Same operations in the same order as
+// factor_warp_kernel (identical results), without its shared-memory traffic: the FP32
+// kernel is issue-bound, the FP64 one is bound by the FP64 pipe and keeps the
+// columns-on-lanes form, which fills more lanes per FP64 instruction.
+template <int WPB = WPB_F>
+__global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld, const BView b,
+                                                              const double* __restrict__ jac, float* __restrict__ LU,
+                                                              unsigned char* __restrict__ piv, float* __restrict__ G,
+                                                              int* __restrict__ sing, double pivtol) {
+    __shared__ float sA[WPB][NV][PADA];
+    __shared__ float sG[WPB][NV][NABV];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = blockIdx.x * WPB + warp;
+    if (live_prob(b, s, S, PS_ACT) < 0) return;   // whole warps leave together
+    float(*A)[PADA] = sA[warp];
+    float(*Gp)[NABV] = sG[warp];
+    const bool rowlane = lane < NV;
+    int singular = 0;
+    for (int n = 0; n < N_STAGES; ++n) {
+        const float tiny = assemble_stage<float>(n, ld, s, lane, jac, pivtol, A, Gp);
+        const unsigned long long ktiny = abs_key(tiny);
+        unsigned char* pv = piv + pv_off(s, n);
+        float row[NCA];
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < NCA; ++j) row[j] = rowlane ? A[lane][j] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const bool cand = lane >= k && rowlane;
+            int p = warp_argmax_key(cand ? abs_key(row[k]) : 0ull, cand);
+            if (p < 0 || p >= NV) p = k;
+            if (lane == 0) pv[k] = (unsigned char)p;
+            if (p != k) {
+                const int src = lane == k ? p : (lane == p ? k : lane);
+#pragma unroll
+                for (int j = 0; j < NCA; ++j) row[j] = __shfl_sync(0xffffffffu, row[j], src);
+            }
+            float ukk = __shfl_sync(0xffffffffu, row[k], k);
+            if (!(abs_key(ukk) > ktiny) || ukk != ukk) {
+                singular = 1;
+                ukk = (ukk < 0.0f ? -1.0f : 1.0f) * (tiny > 0.0f ? tiny : 1.0f);
+            }
+            const float inv = recip(ukk);
+            const bool below = lane > k && rowlane;
+            if (below) row[k] *= inv;
+            const float l = row[k];
+#pragma unroll
+            for (int j = k + 1; j < NCA; ++j) {
+                const float u = __shfl_sync(0xffffffffu, row[j], k);
+                if (below) row[j] -= l * u;
+            }
+            if (lane == k) row[k] = inv;
+        }
+        // U G = L^-1 P B (the B columns of the rows), i from the bottom up
+        if (n + 1 < N_STAGES) {
+#pragma unroll
+            for (int i = NV - 1; i >= 0; --i) {
+                const float dinv = __shfl_sync(0xffffffffu, row[i], i);   // 1 / U_ii
+#pragma unroll
+                for (int a = 0; a < NABV; ++a) {
+                    const float g = __shfl_sync(0xffffffffu, row[NV + a], i) * dinv;
+                    if (lane < i) row[NV + a] -= row[i] * g;
+                    if (lane == i) row[NV + a] = g;
+                }
+            }
+        }
+        __syncwarp();
+        // rows to shared memory, then coalesced stores of LU and G
+        if (rowlane) {
+#pragma unroll
+            for (int j = 0; j < NCA; ++j) A[lane][j] = row[j];
+        }
+        __syncwarp();
+        if (n + 1 < N_STAGES) {
+            float* Gn = G + g_off(s, n);
+            for (int e = lane; e < NV * NABV; e += 32) {
+                const float g = A[e / NABV][NV + e % NABV];
+                Gn[e] = g;
+                Gp[e / NABV][e % NABV] = g;
+            }
+        }
+        float* Ln = LU + lu_off(s, n);
         for (int e = lane; e < NV * NV; e += 32) Ln[e] = A[e / NV][e % NV];
         __syncwarp();
     }
