@@ -137,6 +137,19 @@ abs_status abs_scenario_pattern(int32_t* nnzJ_scen, int32_t* nnzH_scen, int32_t*
  * 6 abs_result, 7 abs_train_options; -1 for an unknown index. */
 int64_t abs_struct_size(int which);
 
+/* Per-scenario status of the last factorization (kkt_factor or the last one of a solve):
+ * status[s] = ABS_ERR_NUMERIC when a stage block of scenario s was singular or not
+ * finite, else ABS_OK.  status: host, S entries.  Synchronous. */
+abs_status absorber_scenario_status(const abs_problem* h, int32_t* status);
+
+/* A primal vector in the paper's layout (Section "Numerical results"): out = [d, z_1 ..
+ * z_S] with 300 entries per scenario -- per stage x over the 11 species, y over the 11
+ * species, L, V, T, the 5 reaction extents, in physical units -- and the 90 fixed
+ * entries per scenario (y of the 7 non-volatile species, x of N2 and O2) exactly 0.
+ *   x    device primal vector of a single-problem handle.
+ *   out  device, 1 + 300 S doubles.  Asynchronous. */
+abs_status absorber_paper_layout(abs_problem* h, const double* x, double* out, abs_stream_t stream);
+
 /* Per-scenario sparsity patterns (host arrays), identical for every scenario.
  *   jrow, jcol: nnzJ_scen entries of dc_s/d(z_s, d) in CSR order (row ascending, then
  *               column ascending); columns 0..219 are z_s, column 220 is d.

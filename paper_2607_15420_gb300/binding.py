@@ -130,6 +130,8 @@ EXPORTS = {
     "absorber_num_problems": (C.c_int32, [C.c_void_p]),
     "ipm_solve_batch": (C.c_int, [C.c_void_p, C.POINTER(AbsOptions), C.POINTER(AbsResult), C.c_void_p, C.c_void_p,
                                   C.c_void_p]),
+    "absorber_scenario_status": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "absorber_paper_layout": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "abs_mlp_create": (C.c_int, [C.c_uint64, C.POINTER(C.c_void_p)]),
     "abs_mlp_destroy": (None, [C.c_void_p]),
     "abs_mlp_last_error": (C.c_char_p, [C.c_void_p]),
@@ -339,6 +341,15 @@ class Problem:
         if check:
             self._check(st)
         return res
+
+    def scenario_status(self):
+        out = np.zeros(self.S, dtype=np.int32)
+        self._check(lib().absorber_scenario_status(self.h, out.ctypes.data))
+        return out
+
+    def paper_layout(self, x, out, stream=None):
+        """Device primal vector -> device [d, z_1..z_S] (300 per scenario, paper's layout)."""
+        self._check(lib().absorber_paper_layout(self.h, _ptr(x), _ptr(out), _stream(stream)))
 
     def set_feeds(self, feeds, stream=None):
         """Replace the scenario feeds (host numpy array or device tensor, (18, S))."""

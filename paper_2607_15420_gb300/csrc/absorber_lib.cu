@@ -39,6 +39,12 @@ struct PatternTables {
     short slotH[NV][NV];
     Ent own[3][MAXOWN], abv[3][MAXABV], blw[3][MAXBLW], hes[NHS];
     int nown[3], nabv[3], nblw[3], dslot[3];
+    // the same entries grouped by destination (see kernels.cuh)
+    short ownRp[3][NV + 1], abvRp[3][NV + 1], blwRp[3][NV + 1];
+    Ent ownC[3][MAXOWN], abvC[3][MAXABV], blwC[3][MAXBLW];
+    short ownCp[3][NV + 1], abvCp[3][NV + 1], blwCp[3][NV + 1];
+    Ent hesF[2 * NHS];
+    short hesFp[NV + 1];
     std::vector<int> jrow, jcol, hrow, hcol;
     bool ok = false;
 };
@@ -195,6 +201,56 @@ bool build_pattern(PatternTables& T, std::string& err) {
         }
     T.hrow.push_back(NSC);
     T.hcol.push_back(NSC);
+    // destination-grouped copies: row pointers of the (row-ordered) tables, and copies
+    // ordered by the unknown they feed in J^T y (own column, abv_var, blw_var)
+    auto rowptr = [](const Ent* tab, int cnt, short* ptr) {
+        for (int r = 0; r <= NV; ++r) {
+            int k = 0;
+            while (k < cnt && tab[k].r < r) ++k;
+            ptr[r] = (short)k;
+        }
+    };
+    auto bydest = [](const Ent* tab, int cnt, int kind, Ent* out, short* ptr) {
+        auto dest = [kind](const Ent& e) { return kind == 0 ? (int)e.c : (kind == 1 ? abv_var(e.c) : blw_var(e.c)); };
+        int m = 0;
+        for (int j = 0; j < NV; ++j) {
+            ptr[j] = (short)m;
+            for (int k = 0; k < cnt; ++k)
+                if (dest(tab[k]) == j) out[m++] = tab[k];
+        }
+        ptr[NV] = (short)m;
+    };
+    for (int t = 0; t < 3; ++t) {
+        for (int k = 1; k < T.nown[t]; ++k)
+            if (T.own[t][k].r < T.own[t][k - 1].r) {
+                err = "own table not in row order";
+                return false;
+            }
+        rowptr(T.own[t], T.nown[t], T.ownRp[t]);
+        rowptr(T.abv[t], T.nabv[t], T.abvRp[t]);
+        rowptr(T.blw[t], T.nblw[t], T.blwRp[t]);
+        bydest(T.own[t], T.nown[t], 0, T.ownC[t], T.ownCp[t]);
+        bydest(T.abv[t], T.nabv[t], 1, T.abvC[t], T.abvCp[t]);
+        bydest(T.blw[t], T.nblw[t], 2, T.blwC[t], T.blwCp[t]);
+    }
+    // the symmetric Hessian block expanded to both triangles, grouped by row
+    {
+        int m = 0;
+        for (int r = 0; r < NV; ++r) {
+            T.hesFp[r] = (short)m;
+            for (int k = 0; k < NHS; ++k) {
+                const Ent& e = T.hes[k];
+                if (e.r == r) T.hesF[m++] = e;
+                else if (e.c == r) {
+                    Ent f = e;
+                    f.r = e.c;
+                    f.c = e.r;
+                    T.hesF[m++] = f;
+                }
+            }
+        }
+        T.hesFp[NV] = (short)m;
+    }
     T.ok = true;
     return true;
 }
@@ -231,6 +287,17 @@ cudaError_t upload_tables(int dev) {
     UP(c_nabv, T.nabv);
     UP(c_nblw, T.nblw);
     UP(c_dslot, T.dslot);
+    UP(c_ownRp, T.ownRp);
+    UP(c_abvRp, T.abvRp);
+    UP(c_blwRp, T.blwRp);
+    UP(c_ownC, T.ownC);
+    UP(c_abvC, T.abvC);
+    UP(c_blwC, T.blwC);
+    UP(c_ownCp, T.ownCp);
+    UP(c_abvCp, T.abvCp);
+    UP(c_blwCp, T.blwCp);
+    UP(c_hesF, T.hesF);
+    UP(c_hesFp, T.hesFp);
 #undef UP
     g_uploaded[dev] = true;
     return cudaSuccess;
@@ -346,6 +413,8 @@ abs_status fail(abs_problem* h, abs_status st, const std::string& msg) {
 int64_t vsize(const abs_problem* h) { return (int64_t)NSC * h->ld + h->ld; }
 double* V(abs_problem* h, int k) { return h->vec + (int64_t)k * vsize(h); }
 dim3 grid2(const abs_problem* h) { return dim3((unsigned)((h->S + kThr - 1) / kThr), N_STAGES); }
+// kernels with QS threads per (scenario, stage)
+dim3 gridq(const abs_problem* h) { return dim3((unsigned)((h->S + QS_SCEN - 1) / QS_SCEN), N_STAGES); }
 dim3 gridw(const abs_problem* h, int wpb) { return dim3((unsigned)((h->S + wpb - 1) / wpb)); }
 BView view(const abs_problem* h) { return BView{h->pid, h->ps, h->NP}; }
 double& PSV(abs_problem* h, int field, int p) { return h->hps[(size_t)field * h->NP + p]; }
@@ -689,7 +758,7 @@ abs_status kkt_factor_core(abs_problem* h, KKTSys& K, const double* x, cudaStrea
     else r = factor_launch<double>(h, K.jac, pivtol, st);
     if (r != ABS_OK) return r;
     if ((r = solve_j(h, K.prec, K.jac, x, nullptr, V(h, V_Q), st)) != ABS_OK) return r;
-    schur_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, nullptr, V(h, V_Q),
+    schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, nullptr, V(h, V_Q),
                                              nullptr, h->sing, h->part);
     if ((r = launch_check(h)) != ABS_OK) return r;
     if ((r = reduce(h, st, 6, make_ops({RSUM, RSUM, RSUM, RSUM, RSUM, RSUM}), PS_ACT, true)) != ABS_OK) return r;
@@ -715,13 +784,13 @@ abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, 
                               double* dz, double* dl, cudaStream_t st) {
     abs_status r;
     if ((r = solve_j(h, K.prec, K.jac, x, rc, V(h, V_P), st)) != ABS_OK) return r;
-    schur_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q),
+    schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q),
                                              rz, nullptr, h->part);
     if ((r = launch_check(h)) != ABS_OK) return r;
     if ((r = reduce(h, st, 4, make_ops({RSUM, RSUM, RSUM, RSUM}), PS_ACT, false)) != ABS_OK) return r;
     finalize_dd_kernel<<<(unsigned)((h->NP + 127) / 128), 128, 0, st>>>(h->ld, view(h), h->red, dz);
     if ((r = launch_check(h)) != ABS_OK) return r;
-    dz_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q), rz,
+    dz_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q), rz,
                                           dz, V(h, V_G));
     if ((r = launch_check(h)) != ABS_OK) return r;
     return solve_jt(h, K.prec, K.jac, V(h, V_G), dl, st);
@@ -800,7 +869,7 @@ abs_status kkt_solve_refined(abs_problem* h, KKTSys& K, const double* x, const d
     }
     std::vector<double> rhod(NP, 0.0);
     for (;;) {
-        kkt_residual_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.jac, K.hes, K.sig, K.use_w, dz,
+        kkt_residual_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.jac, K.hes, K.sig, K.use_w, dz,
                                                         dl, rz, rc, V(h, V_RHOZ), V(h, V_RHOC), h->part);
         if ((r = launch_check(h)) != ABS_OK) return r;
         if ((r = reduce(h, st, 5, make_ops({RMAX, RMAX, RSUM, RMAX, RMAX}), PS_ACT, true, dz + (int64_t)NSC * h->ld)) !=
@@ -834,6 +903,31 @@ abs_status kkt_solve_refined(abs_problem* h, KKTSys& K, const double* x, const d
     if ((r = upload_ps(h, st)) != ABS_OK) return r;   // PS_RD restored
     if (steps) *steps = k;
     return ABS_OK;
+}
+
+// the paper's layout (Section "Numerical results"): [d, z_1 .. z_S], z_s = per stage x
+// over the 11 species, y over the 11 species, L, V, T, the 5 extents (physical units);
+// the fixed entries (y of the 7 non-volatile species, x of N2 and O2) exactly 0
+__global__ void __launch_bounds__(128) paper_layout_kernel(const Params P, int S, int64_t ld,
+                                                           const double* __restrict__ x, double* __restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (s >= S) return;
+    constexpr int PER = 30;
+    double* z = out + 1 + (int64_t)s * (N_STAGES * PER) + PER * n;
+    auto xv = [&](int j) { return x[(int64_t)(NV * n + j) * ld + s]; };
+#pragma unroll
+    for (int k = 0; k < PER; ++k) z[k] = 0.0;
+#pragma unroll
+    for (int l = 0; l < 9; ++l) z[l] = xv(LX + l) * P.sx[l];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) z[11 + 7 + j] = xv(LY + j) * P.sy[j];   // CO2, H2O, N2, O2 are species 7..10
+    z[22] = xv(LL);
+    z[23] = xv(LV);
+    z[24] = xv(LT) * P.sT;
+#pragma unroll
+    for (int r = 0; r < 5; ++r) z[25 + r] = xv(LE + r);
+    if (s == 0 && n == 0) out[0] = x[(int64_t)NSC * ld];
 }
 
 // feeds: host or device, [18][S] -> device [18][ld]; padding columns copy the last
@@ -1105,6 +1199,23 @@ abs_status eval_grad_jac_hess(abs_problem* h, const double* x, const double* lam
     return ABS_OK;
 }
 
+abs_status absorber_scenario_status(const abs_problem* ch, int32_t* status) {
+    abs_problem* h = const_cast<abs_problem*>(ch);
+    if (!h || !status) return fail(h, ABS_ERR_ARG, "bad argument");
+    std::vector<int> sg((size_t)h->S, 0);
+    if (h->sing) CK(cudaMemcpy(sg.data(), h->sing, sizeof(int) * (size_t)h->S, cudaMemcpyDeviceToHost));
+    for (int64_t s = 0; s < h->S; ++s) status[s] = sg[(size_t)s] ? ABS_ERR_NUMERIC : ABS_OK;
+    return ABS_OK;
+}
+
+abs_status absorber_paper_layout(abs_problem* h, const double* x, double* out, abs_stream_t stream) {
+    if (!h || !x || !out) return fail(h, ABS_ERR_ARG, "bad argument");
+    if (h->NP != 1) return fail(h, ABS_ERR_ARG, "absorber_paper_layout needs a single-problem handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    paper_layout_kernel<<<grid2(h), kThr, 0, st>>>(h->P, (int)h->S, h->ld, x, out);
+    return launch_check(h);
+}
+
 abs_status kkt_factor(abs_problem* h, const double* x, const double* jac_vals, const double* hess_vals,
                       const abs_kkt_diag* diag, int precision, abs_inertia* inertia, abs_stream_t stream) {
     if (!h || !x || !jac_vals || !hess_vals || !diag || !diag->sigma || !inertia)
@@ -1329,6 +1440,7 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
     }
     for (int j = 0; j < 4; ++j) P.hV0[j] = p->hV_ref[j] + p->hV_dh[j];
     const dim3 g2((unsigned)((S + kThr - 1) / kThr), N_STAGES);
+    const dim3 gq((unsigned)((S + QS_SCEN - 1) / QS_SCEN), N_STAGES);
     const int64_t od = (int64_t)NSC * ld;
     cudaError_t e;
 #define NA_LAUNCHED()                                                                                  \
@@ -1348,7 +1460,7 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
     solve_warp_kernel<double, 2><<<gs, 32 * WPB_S, 0, st>>>(P, (int)S, ld, bv, jac_vals, LU, piv, G, x, rhs_c, nullptr,
                                                             pv, qv);
     NA_LAUNCHED();
-    schur_kernel<<<g2, kThr, 0, st>>>((int)S, ld, bv, hess_vals, sigma, true, pv, qv, rhs_x, sing, part);
+    schur_kernel<<<gq, kThr, 0, st>>>((int)S, ld, bv, hess_vals, sigma, true, pv, qv, rhs_x, sing, part);
     NA_LAUNCHED();
     double hx[3] = {0.0, 0.0, 0.0};
     const int64_t plane = (int64_t)N_STAGES * ld;
@@ -1373,7 +1485,7 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
     const double beta = red[2] - delta_w * red[3];
     const double dd = (hx[2] - beta) / Sd;
     CK(cudaMemcpyAsync(sol_x + od, &dd, sizeof(double), cudaMemcpyHostToDevice, st));
-    dz_kernel<<<g2, kThr, 0, st>>>((int)S, ld, bv, hess_vals, sigma, true, pv, qv, rhs_x, sol_x, gv);
+    dz_kernel<<<gq, kThr, 0, st>>>((int)S, ld, bv, hess_vals, sigma, true, pv, qv, rhs_x, sol_x, gv);
     NA_LAUNCHED();
     solve_t_warp_kernel<double><<<gs, 32 * WPB_S, 0, st>>>((int)S, ld, bv, jac_vals, LU, piv, gv, sol_c);
     NA_LAUNCHED();

@@ -38,6 +38,15 @@ __constant__ Ent c_blw[3][MAXBLW];
 __constant__ Ent c_hes[NHS];
 __constant__ int c_nown[3], c_nabv[3], c_nblw[3];
 __constant__ int c_dslot[3];           // the d entry of the stage's hydraulic row
+// The same entries grouped by destination, so that the sparse products below accumulate
+// into statically indexed registers (table-indexed register arrays would live in local
+// memory): row pointers of the row-ordered tables (J v), copies ordered by the unknown
+// they feed (J^T y), and the Hessian block expanded to both triangles by row (H v).
+__constant__ short c_ownRp[3][NV + 1], c_abvRp[3][NV + 1], c_blwRp[3][NV + 1];
+__constant__ Ent c_ownC[3][MAXOWN], c_abvC[3][MAXABV], c_blwC[3][MAXBLW];
+__constant__ short c_ownCp[3][NV + 1], c_abvCp[3][NV + 1], c_blwCp[3][NV + 1];
+__constant__ Ent c_hesF[2 * NHS];
+__constant__ short c_hesFp[NV + 1];
 
 // bounds of the stage unknowns (10d): lower 0 for fractions, flows and the slack,
 // both for T, none for the extents
@@ -231,11 +240,31 @@ __global__ void __launch_bounds__(128) eval_kernel(const Params P, int S, int64_
         hes[(int64_t)(NHS * N_STAGES) * ld + s] = -P.u_max * M_PI * 0.5 * sl;
     }
     if (part) {
+        // sum of ln(slack) over the stage's 18 bounds as the logarithm of their product: the
+        // product is carried as a mantissa in [1, 2) times a power of two (exponent read from
+        // the bit pattern), so it neither overflows nor underflows; a slack that is not
+        // positive and finite makes the sum NaN (the trial is rejected as before)
+        double m = 1.0;
+        long long e2 = 0;
+        bool bad = false;
+        auto take = [&](double sl) {
+            bad = bad || !(sl > 0.0) || !(sl < INFINITY);
+            m *= sl;
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+            const int ex = (int)((bits >> 52) & 0x7ffull);
+            if (ex == 0 || ex == 0x7ff) {
+                bad = true;
+                return;
+            }
+            e2 += ex - 1023;
+            m = __longlong_as_double((long long)((bits & ~(0x7ffull << 52)) | (1023ull << 52)));
+        };
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
-            if (has_lo(j)) blog += log(in.q[j] - (j == LT ? P.T_lo / P.sT : 0.0));
-            if (has_hi(j)) blog += log(P.T_hi / P.sT - in.q[j]);
+            if (has_lo(j)) take(in.q[j] - (j == LT ? P.T_lo / P.sT : 0.0));
+            if (has_hi(j)) take(P.T_hi / P.sT - in.q[j]);
         }
+        blog = bad ? NAN : log(m) + (double)e2 * 0.69314718055994530942;   // ln 2
         const double v[3] = {em.asum, em.amax, blog};
         store_partials<3>(v, part, ld, s, n);
     }
@@ -244,81 +273,71 @@ __global__ void __launch_bounds__(128) eval_kernel(const Params P, int S, int64_
 // ------------------------------------------------------------------------------------
 // sparse products with the stage-structured Jacobian / Hessian
 // ------------------------------------------------------------------------------------
-// (J^T y) for the unknowns of stage n of scenario s: rows of stage n (own entries), of
-// stage n-1 (their stream-from-above entries) and of stage n+1 (stream-from-below).
-__device__ inline void jt_stage(int64_t ld, const double* __restrict__ jac, const double* __restrict__ y,
-                                int s, int n, double (&out)[NV]) {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) out[j] = 0.0;
+// (J^T y)_j for unknown j of stage n: rows of stage n (own entries), of stage n-1 (their
+// stream-from-above entries) and of stage n+1 (stream-from-below), in a fixed order
+__device__ __forceinline__ double jt_one(int64_t ld, const double* __restrict__ jac, const double* __restrict__ y, int s,
+                                int n, int j) {
     const int t = stage_type(n);
     const int base = c_segJ[n];
-    for (int k = 0; k < c_nown[t]; ++k) {
-        const Ent e = c_own[t][k];
-        out[e.c] += jac[(int64_t)(base + e.slot) * ld + s] * y[(int64_t)(NR * n + e.r) * ld + s];
+    double a = 0.0;
+    for (int k = c_ownCp[t][j]; k < c_ownCp[t][j + 1]; ++k) {
+        const Ent e = c_ownC[t][k];
+        a += jac[(int64_t)(base + e.slot) * ld + s] * y[(int64_t)(NR * n + e.r) * ld + s];
     }
     if (n > 0) {
         const int tb = stage_type(n - 1), bb = c_segJ[n - 1];
-        for (int k = 0; k < c_nabv[tb]; ++k) {
-            const Ent e = c_abv[tb][k];
-            out[abv_var(e.c)] += jac[(int64_t)(bb + e.slot) * ld + s] * y[(int64_t)(NR * (n - 1) + e.r) * ld + s];
+        for (int k = c_abvCp[tb][j]; k < c_abvCp[tb][j + 1]; ++k) {
+            const Ent e = c_abvC[tb][k];
+            a += jac[(int64_t)(bb + e.slot) * ld + s] * y[(int64_t)(NR * (n - 1) + e.r) * ld + s];
         }
     }
     if (n + 1 < N_STAGES) {
         const int ta = stage_type(n + 1), ba = c_segJ[n + 1];
-        for (int k = 0; k < c_nblw[ta]; ++k) {
-            const Ent e = c_blw[ta][k];
-            out[blw_var(e.c)] += jac[(int64_t)(ba + e.slot) * ld + s] * y[(int64_t)(NR * (n + 1) + e.r) * ld + s];
+        for (int k = c_blwCp[ta][j]; k < c_blwCp[ta][j + 1]; ++k) {
+            const Ent e = c_blwC[ta][k];
+            a += jac[(int64_t)(ba + e.slot) * ld + s] * y[(int64_t)(NR * (n + 1) + e.r) * ld + s];
         }
     }
+    return a;
 }
 
-// (J v) for the rows of stage n; v is a primal vector (d at [NSC*ld]) -- dd multiplies
-// the d column (set has_d false to leave it out).
-__device__ inline void jv_stage(int64_t ld, const double* __restrict__ jac, const double* __restrict__ v,
-                                double vd, int s, int n, double (&out)[NR]) {
-#pragma unroll
-    for (int r = 0; r < NR; ++r) out[r] = 0.0;
+// (J v)_r for row r of stage n; v a primal vector, vd the d step (the hydraulic row's d
+// column)
+__device__ __forceinline__ double jv_one(int64_t ld, const double* __restrict__ jac, const double* __restrict__ v, double vd,
+                                int s, int n, int r) {
     const int t = stage_type(n);
     const int base = c_segJ[n];
-    for (int k = 0; k < c_nown[t]; ++k) {
+    double a = 0.0;
+    for (int k = c_ownRp[t][r]; k < c_ownRp[t][r + 1]; ++k) {
         const Ent e = c_own[t][k];
-        out[e.r] += jac[(int64_t)(base + e.slot) * ld + s] * v[(int64_t)(NV * n + e.c) * ld + s];
+        a += jac[(int64_t)(base + e.slot) * ld + s] * v[(int64_t)(NV * n + e.c) * ld + s];
     }
-    if (n + 1 < N_STAGES) {
-        for (int k = 0; k < c_nabv[t]; ++k) {
+    if (n + 1 < N_STAGES)
+        for (int k = c_abvRp[t][r]; k < c_abvRp[t][r + 1]; ++k) {
             const Ent e = c_abv[t][k];
-            out[e.r] += jac[(int64_t)(base + e.slot) * ld + s] * v[(int64_t)(NV * (n + 1) + abv_var(e.c)) * ld + s];
+            a += jac[(int64_t)(base + e.slot) * ld + s] * v[(int64_t)(NV * (n + 1) + abv_var(e.c)) * ld + s];
         }
-    }
-    if (n > 0) {
-        for (int k = 0; k < c_nblw[t]; ++k) {
+    if (n > 0)
+        for (int k = c_blwRp[t][r]; k < c_blwRp[t][r + 1]; ++k) {
             const Ent e = c_blw[t][k];
-            out[e.r] += jac[(int64_t)(base + e.slot) * ld + s] * v[(int64_t)(NV * (n - 1) + blw_var(e.c)) * ld + s];
+            a += jac[(int64_t)(base + e.slot) * ld + s] * v[(int64_t)(NV * (n - 1) + blw_var(e.c)) * ld + s];
         }
-    }
-    out[R_H] += jac[(int64_t)(base + c_dslot[t]) * ld + s] * vd;
+    if (r == R_H) a += jac[(int64_t)(base + c_dslot[t]) * ld + s] * vd;
+    return a;
 }
 
-// ((W + Sigma + dw I) v) for the unknowns of stage n (W block diagonal by stage);
-// use_w = false gives (Sigma + dw I) v.
-__device__ inline void hv_stage(int64_t ld, const double* __restrict__ hes, const double* __restrict__ sig,
-                                double dw, bool use_w, const double* __restrict__ v, int s, int n,
-                                double (&out)[NV]) {
-    double vv[NV];
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        vv[j] = v[(int64_t)(NV * n + j) * ld + s];
-        out[j] = (sig[(int64_t)(NV * n + j) * ld + s] + dw) * vv[j];
-    }
-    if (use_w) {
-#pragma unroll
-        for (int k = 0; k < NHS; ++k) {
-            const Ent e = c_hes[k];
-            const double h = hes[(int64_t)(NHS * n + e.slot) * ld + s];
-            out[e.r] += h * vv[e.c];
-            if (e.r != e.c) out[e.c] += h * vv[e.r];
+// ((W + Sigma + dw I) v)_j for unknown j of stage n (W block diagonal by stage);
+// use_w = false gives (Sigma + dw I) v
+__device__ __forceinline__ double hv_one(int64_t ld, const double* __restrict__ hes, const double* __restrict__ sig,
+                                double dw, bool use_w, const double* __restrict__ v, int s, int n, int j) {
+    const int64_t o = (int64_t)(NV * n + j) * ld + s;
+    double a = (sig[o] + dw) * v[o];
+    if (use_w)
+        for (int k = c_hesFp[j]; k < c_hesFp[j + 1]; ++k) {
+            const Ent e = c_hesF[k];
+            a += hes[(int64_t)(NHS * n + e.slot) * ld + s] * v[(int64_t)(NV * n + e.c) * ld + s];
         }
-    }
+    return a;
 }
 
 }  // namespace absorber

@@ -202,12 +202,17 @@ __host__ __device__ inline void stage_eval(const Params& P, const StageIn& in, c
         }
         e.res(R_VH, Pr * y[1] - x[8] * ps);
         e.res(R_VC, Pr * y[0] - rhoH * x7);
+        // ln of each liquid fraction once (every species enters several reactions)
+        double lx[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) lx[c] = log(in.q[LX + c]) + P.lnsx[c];
+        const double lT = log(T);
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            double r = -(P.KE_A[k] + P.KE_B[k] * invT + P.KE_C[k] * log(T) + P.KE_D[k] * T);
+            double r = -(P.KE_A[k] + P.KE_B[k] * invT + P.KE_C[k] * lT + P.KE_D[k] * T);
 #pragma unroll
             for (int c = 0; c < 9; ++c)
-                if (nu(c, k) != 0) r += nu(c, k) * (log(in.q[LX + c]) + P.lnsx[c]);
+                if (nu(c, k) != 0) r += nu(c, k) * lx[c];
             e.res(R_RX + k, r);
         }
         double sx_ = -1.0, sy_ = -1.0;

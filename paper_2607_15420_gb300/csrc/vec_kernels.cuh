@@ -21,41 +21,78 @@ struct RedOps {
     int op[12];
 };
 
+// Kernels below with QS threads per (scenario, stage): thread q of a group handles the
+// stage's unknowns j = q, q + QS, ...; the QS threads are adjacent lanes, so their
+// partial values combine with xor shuffles (every lane of the group ends with the same
+// value, in a fixed order).  Four times the warps of one thread per (scenario, stage):
+// these kernels wait on global loads, and 5000 scenarios x 10 stages alone fill only a
+// quarter of the GPU's warp slots.
+constexpr int QS = 4;
+constexpr int QS_SCEN = 128 / QS;   // scenarios per 128-thread block
+
+__device__ inline double group_max(double a) {
+#pragma unroll
+    for (int o = 1; o < QS; o <<= 1) {
+        const double b = __shfl_xor_sync(0xffffffffu, a, o);
+        a = (b > a || b != b) ? b : a;
+    }
+    return a;
+}
+__device__ inline double group_min(double a) {
+#pragma unroll
+    for (int o = 1; o < QS; o <<= 1) a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+    return a;
+}
+__device__ inline double group_sum(double a) {
+#pragma unroll
+    for (int o = 1; o < QS; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
+
 // J^T lambda for the stage's unknowns and the optimality-error partials:
 // [0] max |J^T l - zL + zU|, [1] sum |lambda|, [2] sum |zL| + |zU|, [3] max and [4] min
-// complementarity product over bounded unknowns, [5] the stage's hydraulic multiplier
+// complementarity product over bounded unknowns, [5] the stage's hydraulic multiplier.
+// QS threads per (scenario, stage); grid (ceil(S / QS_SCEN), N_STAGES), 128 threads.
 __global__ void __launch_bounds__(128) dual_kernel(const Params P, int S, int64_t ld, const BView b,
                                                    const double* __restrict__ jac, const double* __restrict__ lam,
                                                    const double* __restrict__ x, const double* __restrict__ zL,
                                                    const double* __restrict__ zU, double* __restrict__ jtl,
                                                    double* part) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = threadIdx.x % QS;
+    const int s = blockIdx.x * QS_SCEN + threadIdx.x / QS;
     const int n = blockIdx.y;
-    if (live_prob(b, s, S, PS_ACT) < 0) return;
+    const bool live = live_prob(b, s, S, PS_ACT) >= 0;   // the same for the whole group
     double v[6] = {0.0, 0.0, 0.0, -INFINITY, INFINITY, 0.0};
-    double g[NV];
-    jt_stage(ld, jac, lam, s, n, g);
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        const int64_t o = (int64_t)(NV * n + j) * ld + s;
-        jtl[o] = g[j];
-        const double zl = zL[o], zu = zU[o];
-        const double r = fabs(g[j] - zl + zu);
-        v[0] = (r > v[0] || r != r) ? r : v[0];
-        v[1] += fabs(lam[o]);
-        v[2] += fabs(zl) + fabs(zu);
-        const double xv = x[o];
-        if (has_lo(j)) {
-            const double cp = zl * (xv - lo_of(P, j));
-            v[3] = fmax(v[3], cp);
-            v[4] = fmin(v[4], cp);
-        }
-        if (has_hi(j)) {
-            const double cp = zu * (hi_of(P, j) - xv);
-            v[3] = fmax(v[3], cp);
-            v[4] = fmin(v[4], cp);
+    if (live) {
+#pragma unroll 1
+        for (int j = q; j < NV; j += QS) {
+            const int64_t o = (int64_t)(NV * n + j) * ld + s;
+            const double gj = jt_one(ld, jac, lam, s, n, j);
+            jtl[o] = gj;
+            const double zl = zL[o], zu = zU[o];
+            const double r = fabs(gj - zl + zu);
+            v[0] = (r > v[0] || r != r) ? r : v[0];
+            v[1] += fabs(lam[o]);
+            v[2] += fabs(zl) + fabs(zu);
+            const double xv = x[o];
+            if (has_lo(j)) {
+                const double cp = zl * (xv - lo_of(P, j));
+                v[3] = fmax(v[3], cp);
+                v[4] = fmin(v[4], cp);
+            }
+            if (has_hi(j)) {
+                const double cp = zu * (hi_of(P, j) - xv);
+                v[3] = fmax(v[3], cp);
+                v[4] = fmin(v[4], cp);
+            }
         }
     }
+    v[0] = group_max(v[0]);
+    v[1] = group_sum(v[1]);
+    v[2] = group_sum(v[2]);
+    v[3] = group_max(v[3]);
+    v[4] = group_min(v[4]);
+    if (!live || q != 0) return;
     v[5] = lam[(int64_t)(NR * n + R_H) * ld + s];
     store_partials<6>(v, part, ld, s, n);
 }
@@ -93,29 +130,35 @@ __global__ void __launch_bounds__(128) rhs_kernel(const Params P, int S, int64_t
 }
 
 // Schur partial sums with H = W + Sigma (W optional): [0] q^T H q, [1] q^T q,
-// [2] q^T (r - H p), [3] q^T p, [4] the scenario's d-d Hessian entry, [5] singular flag
+// [2] q^T (r - H p), [3] q^T p, [4] the scenario's d-d Hessian entry, [5] singular flag.
+// QS threads per (scenario, stage).
 __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BView b, const double* __restrict__ hes,
                                                     const double* __restrict__ sig, bool use_w,
                                                     const double* __restrict__ p, const double* __restrict__ q,
                                                     const double* __restrict__ r, const int* __restrict__ sing,
                                                     double* part) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = threadIdx.x % QS;
+    const int s = blockIdx.x * QS_SCEN + threadIdx.x / QS;
     const int n = blockIdx.y;
-    if (live_prob(b, s, S, PS_ACT) < 0) return;
+    const bool live = live_prob(b, s, S, PS_ACT) >= 0;
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    double hq[NV];
-    hv_stage(ld, hes, sig, 0.0, use_w, q, s, n, hq);
-    double hp[NV];
-    if (p) hv_stage(ld, hes, sig, 0.0, use_w, p, s, n, hp);
+    if (live) {
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        const int64_t o = (int64_t)(NV * n + j) * ld + s;
-        const double qj = q[o];
-        v[0] += qj * hq[j];
-        v[1] += qj * qj;
-        if (r) v[2] += qj * (r[o] - (p ? hp[j] : 0.0));
-        if (p) v[3] += qj * p[o];
+        for (int j0 = 0; j0 < NV; j0 += QS) {
+            const int j = j0 + g;
+            if (j < NV) {
+                const int64_t o = (int64_t)(NV * n + j) * ld + s;
+                const double qj = q[o];
+                v[0] += qj * hv_one(ld, hes, sig, 0.0, use_w, q, s, n, j);
+                v[1] += qj * qj;
+                if (r) v[2] += qj * (r[o] - (p ? hv_one(ld, hes, sig, 0.0, use_w, p, s, n, j) : 0.0));
+                if (p) v[3] += qj * p[o];
+            }
+        }
     }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = group_sum(v[k]);
+    if (!live || g != 0) return;
     if (n == 0) {
         if (use_w) v[4] = hes[(int64_t)(NHS * N_STAGES) * ld + s];
         if (sing) v[5] = (double)sing[s];
@@ -123,33 +166,37 @@ __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BVi
     store_partials<6>(v, part, ld, s, n);
 }
 
-// dz = p - q dd ;  g = r - (W + Sigma + dw I) dz ;  dd, dw of the slot's problem
+// dz = p - q dd ;  g = r - (W + Sigma + dw I) dz ;  dd, dw of the slot's problem.
+// QS threads per (scenario, stage); each writes its unknowns of dz, then (after the
+// group's writes) its entries of g, which read the whole stage's dz.
 __global__ void __launch_bounds__(128) dz_kernel(int S, int64_t ld, const BView b, const double* __restrict__ hes,
                                                  const double* __restrict__ sig, bool use_w,
                                                  const double* __restrict__ p, const double* __restrict__ q,
                                                  const double* __restrict__ r, double* dz, double* __restrict__ g) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gq = threadIdx.x % QS;
+    const int s = blockIdx.x * QS_SCEN + threadIdx.x / QS;
     const int n = blockIdx.y;
     const int pr = live_prob(b, s, S, PS_ACT);
-    if (pr < 0) return;
-    const double dd = dz[(int64_t)NSC * ld + pr];
-    const double dw = b.ps ? psv(b, PS_DW, pr) : 0.0;
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        const int64_t o = (int64_t)(NV * n + j) * ld + s;
-        dz[o] = p[o] - q[o] * dd;
+    const bool live = pr >= 0;
+    if (live) {
+        const double dd = dz[(int64_t)NSC * ld + pr];
+        for (int j = gq; j < NV; j += QS) {
+            const int64_t o = (int64_t)(NV * n + j) * ld + s;
+            dz[o] = p[o] - q[o] * dd;
+        }
     }
-    double h[NV];
-    hv_stage(ld, hes, sig, dw, use_w, dz, s, n, h);
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
+    __syncwarp();   // the group's dz entries are visible to its lanes below
+    if (!live) return;
+    const double dw = b.ps ? psv(b, PS_DW, pr) : 0.0;
+    for (int j = gq; j < NV; j += QS) {
         const int64_t o = (int64_t)(NV * n + j) * ld + s;
-        g[o] = r[o] - h[j];
+        g[o] = r[o] - hv_one(ld, hes, sig, dw, use_w, dz, s, n, j);
     }
 }
 
 // residual of the full KKT system: rho_z = r_z - (H dz + J^T dl), rho_c = r_c - (J dz + b dd).
-// partials: [0] max|rho_z|, [1] max|rho_c|, [2] the stage's hydraulic dl, [3] max|r_z|, [4] max|r_c|
+// partials: [0] max|rho_z|, [1] max|rho_c|, [2] the stage's hydraulic dl, [3] max|r_z|,
+// [4] max|r_c|.  QS threads per (scenario, stage).
 __global__ void __launch_bounds__(128) kkt_residual_kernel(int S, int64_t ld, const BView b,
                                                            const double* __restrict__ jac,
                                                            const double* __restrict__ hes,
@@ -158,30 +205,33 @@ __global__ void __launch_bounds__(128) kkt_residual_kernel(int S, int64_t ld, co
                                                            const double* __restrict__ rz, const double* __restrict__ rc,
                                                            double* __restrict__ rhoz, double* __restrict__ rhoc,
                                                            double* part) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gq = threadIdx.x % QS;
+    const int s = blockIdx.x * QS_SCEN + threadIdx.x / QS;
     const int n = blockIdx.y;
     const int pr = live_prob(b, s, S, PS_ACT);
-    if (pr < 0) return;
-    const double dd = dz[(int64_t)NSC * ld + pr];
-    const double dw = b.ps ? psv(b, PS_DW, pr) : 0.0;
+    const bool live = pr >= 0;
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    double h[NV], jt[NV], jv[NR];
-    hv_stage(ld, hes, sig, dw, use_w, dz, s, n, h);
-    jt_stage(ld, jac, dl, s, n, jt);
-    jv_stage(ld, jac, dz, dd, s, n, jv);
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        const int64_t o = (int64_t)(NV * n + j) * ld + s;
-        const double a = rz[o] - (h[j] + jt[j]);
-        const double c = rc[o] - jv[j];
-        rhoz[o] = a;
-        rhoc[o] = c;
-        v[0] = fmax(v[0], fabs(a));
-        v[1] = fmax(v[1], fabs(c));
-        v[3] = fmax(v[3], fabs(rz[o]));
-        v[4] = fmax(v[4], fabs(rc[o]));
-        if (a != a || c != c) v[0] = NAN;
+    if (live) {
+        const double dd = dz[(int64_t)NSC * ld + pr];
+        const double dw = b.ps ? psv(b, PS_DW, pr) : 0.0;
+        for (int j = gq; j < NV; j += QS) {
+            const int64_t o = (int64_t)(NV * n + j) * ld + s;
+            const double a = rz[o] - (hv_one(ld, hes, sig, dw, use_w, dz, s, n, j) + jt_one(ld, jac, dl, s, n, j));
+            const double c = rc[o] - jv_one(ld, jac, dz, dd, s, n, j);
+            rhoz[o] = a;
+            rhoc[o] = c;
+            v[0] = fmax(v[0], fabs(a));
+            v[1] = fmax(v[1], fabs(c));
+            v[3] = fmax(v[3], fabs(rz[o]));
+            v[4] = fmax(v[4], fabs(rc[o]));
+            if (a != a || c != c) v[0] = NAN;
+        }
     }
+    v[0] = group_max(v[0]);
+    v[1] = group_max(v[1]);
+    v[3] = group_max(v[3]);
+    v[4] = group_max(v[4]);
+    if (!live || gq != 0) return;
     v[2] = dl[(int64_t)(NR * n + R_H) * ld + s];
     store_partials<5>(v, part, ld, s, n);
 }

@@ -269,3 +269,24 @@ def test_full_size_s5000_mixed_precision_properties(B):
     # one active hydraulic row: the binding scenario's multiplier carries the objective
     lh = lam.reshape(5000, model.N, model.NV)[:, :, model.NV - 1]
     assert abs(lh.sum() * P["u_max"] * math.pi * d / 2.0 - 1.0) <= 1e-6
+
+
+def test_paper_layout_and_scenario_status(B):
+    # the paper's 300-entry layout, bit for bit the oracle's restatement of it; the fixed
+    # entries exactly zero; every scenario's factorization healthy after a solve
+    import torch
+    F = ai.make_feeds(37, 5)
+    prob, res, Z, d, lam = _gpu_solve(B, F)
+    assert res.status == 0
+    x = dev(prob.to_soa(Z, d))
+    out = torch.zeros(1 + 300 * 37, dtype=torch.float64, device="cuda")
+    prob.paper_layout(x, out)
+    o = host(out)
+    assert o[0] == d
+    ref = model.full_layout(P, Z)
+    assert np.array_equal(o[1:].reshape(37, model.N, 30), ref)
+    fixed = np.zeros(30, dtype=bool)
+    fixed[9:11] = True            # x of N2, O2
+    fixed[11:18] = True           # y of the 7 non-volatile species
+    assert np.all(o[1:].reshape(37, model.N, 30)[:, :, fixed] == 0.0)
+    assert np.all(prob.scenario_status() == 0)
