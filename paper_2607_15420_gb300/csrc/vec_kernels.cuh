@@ -114,14 +114,14 @@ __global__ void __launch_bounds__(128) rhs_kernel(const Params P, int S, int64_t
         const double xv = x[o];
         double sg = 0.0, gb = 0.0;
         if (has_lo(j)) {
-            const double sl = xv - lo_of(P, j);
-            sg += zL[o] / sl;
-            gb -= mu / sl;
+            const double inv = 1.0 / (xv - lo_of(P, j));   // one division per bound
+            sg += zL[o] * inv;
+            gb -= mu * inv;
         }
         if (has_hi(j)) {
-            const double su = hi_of(P, j) - xv;
-            sg += zU[o] / su;
-            gb += mu / su;
+            const double inv = 1.0 / (hi_of(P, j) - xv);
+            sg += zU[o] * inv;
+            gb += mu * inv;
         }
         sig[o] = sg;
         rz[o] = -(jtl[o] + gb);
@@ -248,36 +248,58 @@ __global__ void __launch_bounds__(128) step_kernel(const Params P, int S, int64_
     const int pr = live_prob(b, s, S, PS_ACT);
     if (pr < 0) return;
     const double mu = psv(b, PS_MU, pr), tau = psv(b, PS_TAU, pr);
-    double v[4] = {1.0, 1.0, 0.0, 0.0};
+    // the minima of tau s / |d| (primal) and tau z / |dz| (dual), and the maximum of
+    // |d| / (1 + |x|), are carried as fractions num / den (den > 0) compared by
+    // cross-multiplication: one division per bound (1 / slack) and one per ratio at the end
+    double an = 1.0, ad = 1.0, zn = 1.0, zd = 1.0, rn = 0.0, rd = 1.0;
+    double gphi = 0.0;
+    bool dnan = false;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const int64_t o = (int64_t)(NV * n + j) * ld + s;
         const double xv = x[o], d = dz[o];
-        v[3] = fmax(v[3], fabs(d) / (1.0 + fabs(xv)));
-        if (d != d) v[3] = NAN;
+        const double ad_ = fabs(d), ax = 1.0 + fabs(xv);
+        if (ad_ * rd > rn * ax) {
+            rn = ad_;
+            rd = ax;
+        }
+        dnan = dnan || d != d;
         if (has_lo(j)) {
-            const double sl = xv - lo_of(P, j);
+            const double sl = xv - lo_of(P, j), inv = 1.0 / sl;
             const double z = zL[o];
-            const double dzl = mu / sl - z - (z / sl) * d;
+            const double dzl = mu * inv - z - (z * inv) * d;
             dzL[o] = dzl;
-            if (d < 0.0) v[0] = fmin(v[0], -tau * sl / d);
-            if (dzl < 0.0) v[1] = fmin(v[1], -tau * z / dzl);
-            v[2] += (-mu / sl) * d;
+            if (d < 0.0 && tau * sl * ad < an * -d) {
+                an = tau * sl;
+                ad = -d;
+            }
+            if (dzl < 0.0 && tau * z * zd < zn * -dzl) {
+                zn = tau * z;
+                zd = -dzl;
+            }
+            gphi += (-mu * inv) * d;
         } else {
             dzL[o] = 0.0;
         }
         if (has_hi(j)) {
-            const double su = hi_of(P, j) - xv;
+            const double su = hi_of(P, j) - xv, inv = 1.0 / su;
             const double z = zU[o];
-            const double dzu = mu / su - z + (z / su) * d;
+            const double dzu = mu * inv - z + (z * inv) * d;
             dzU[o] = dzu;
-            if (d > 0.0) v[0] = fmin(v[0], tau * su / d);
-            if (dzu < 0.0) v[1] = fmin(v[1], -tau * z / dzu);
-            v[2] += (mu / su) * d;
+            if (d > 0.0 && tau * su * ad < an * d) {
+                an = tau * su;
+                ad = d;
+            }
+            if (dzu < 0.0 && tau * z * zd < zn * -dzu) {
+                zn = tau * z;
+                zd = -dzu;
+            }
+            gphi += (mu * inv) * d;
         } else {
             dzU[o] = 0.0;
         }
     }
+    const double v[4] = {an / ad, zn / zd, gphi, dnan ? NAN : rn / rd};
     store_partials<4>(v, part, ld, s, n);
 }
 
@@ -290,15 +312,29 @@ __global__ void __launch_bounds__(128) ftb_kernel(const Params P, int S, int64_t
     const int pr = live_prob(b, s, S, PS_LSACT);
     if (pr < 0) return;
     const double tau = psv(b, PS_TAU, pr);
-    double v[1] = {1.0};
+    double an = 1.0, ad = 1.0;   // min of tau s / |d| as a fraction (see step_kernel)
+    bool dnan = false;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const int64_t o = (int64_t)(NV * n + j) * ld + s;
         const double xv = x[o], d = dz[o];
-        if (has_lo(j) && d < 0.0) v[0] = fmin(v[0], -tau * (xv - lo_of(P, j)) / d);
-        if (has_hi(j) && d > 0.0) v[0] = fmin(v[0], tau * (hi_of(P, j) - xv) / d);
-        if (d != d) v[0] = NAN;
+        if (has_lo(j) && d < 0.0) {
+            const double sl = xv - lo_of(P, j);
+            if (tau * sl * ad < an * -d) {
+                an = tau * sl;
+                ad = -d;
+            }
+        }
+        if (has_hi(j) && d > 0.0) {
+            const double su = hi_of(P, j) - xv;
+            if (tau * su * ad < an * d) {
+                an = tau * su;
+                ad = d;
+            }
+        }
+        dnan = dnan || d != d;
     }
+    const double v[1] = {dnan ? NAN : an / ad};
     store_partials<1>(v, part, ld, s, n);
 }
 
@@ -314,6 +350,7 @@ __global__ void __launch_bounds__(128) accept_kernel(const Params P, int S, int6
     const int pr = live_prob(b, s, S, PS_ACT);
     if (pr < 0) return;
     const double alpha = psv(b, PS_ALPHA, pr), alpha_z = psv(b, PS_ALPHAZ, pr), mu = psv(b, PS_MU, pr);
+    const double mlo = mu / ksig, mhi = ksig * mu;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const int64_t o = (int64_t)(NV * n + j) * ld + s;
@@ -321,14 +358,14 @@ __global__ void __launch_bounds__(128) accept_kernel(const Params P, int S, int6
         x[o] = xv;
         lam[o] += alpha * dl[o];
         if (has_lo(j)) {
-            const double sl = xv - lo_of(P, j);
+            const double inv = 1.0 / (xv - lo_of(P, j));
             const double z = zL[o] + alpha_z * dzL[o];
-            zL[o] = fmin(fmax(z, mu / (ksig * sl)), ksig * mu / sl);
+            zL[o] = fmin(fmax(z, mlo * inv), mhi * inv);
         }
         if (has_hi(j)) {
-            const double su = hi_of(P, j) - xv;
+            const double inv = 1.0 / (hi_of(P, j) - xv);
             const double z = zU[o] + alpha_z * dzU[o];
-            zU[o] = fmin(fmax(z, mu / (ksig * su)), ksig * mu / su);
+            zU[o] = fmin(fmax(z, mlo * inv), mhi * inv);
         }
     }
 }
