@@ -160,10 +160,16 @@ __host__ __device__ inline void stage_eval(const Params& P, const StageIn& in, c
 
     // ---- (9a) water saturation pressure ---------------------------------------------
     const double Tc = T + P.psat_c;
-    const double ps = exp(P.psat_a - P.psat_b / Tc);
-    const double bT2 = P.psat_b / (Tc * Tc);
-    const double ps1 = ps * bT2;                                  // dPsat/dT
-    const double ps2 = ps * (bT2 * bT2 - 2.0 * P.psat_b / (Tc * Tc * Tc));  // d2Psat/dT2
+    const double iTc = 1.0 / Tc;
+    const double ps = exp(P.psat_a - P.psat_b * iTc);
+    const double bT2 = P.psat_b * iTc * iTc;
+    const double ps1 = ps * bT2;                                        // dPsat/dT
+    const double ps2 = ps * (bT2 * bT2 - 2.0 * P.psat_b * iTc * iTc * iTc);  // d2Psat/dT2
+    const double iPr = 1.0 / Pr;
+    // reciprocals of the scaled liquid fractions (derivatives of their logarithms)
+    double iq[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) iq[c] = (E::want_jac || E::want_hes) ? 1.0 / in.q[LX + c] : 0.0;
 
     // ---- (9b) Henry coefficient --------------------------------------------------------
     double am = 0, ac = 0, aw = 0;
@@ -223,7 +229,7 @@ __host__ __device__ inline void stage_eval(const Params& P, const StageIn& in, c
         e.res(R_SX, sx_);
         e.res(R_SY, sy_);
         e.res(R_E, L * HL + V * HV - La * HLa - Vb * HVb);
-        e.res(R_H, V * P.R * T / Pr - P.u_max * M_PI * in.d * in.d * 0.25 + in.q[LS]);
+        e.res(R_H, V * P.R * T * iPr - P.u_max * M_PI * in.d * in.d * 0.25 + in.q[LS]);
     }
 
     // ---- Jacobian ----------------------------------------------------------------------
@@ -266,7 +272,7 @@ __host__ __device__ inline void stage_eval(const Params& P, const StageIn& in, c
         for (int k = 0; k < 5; ++k) {
 #pragma unroll
             for (int c = 0; c < 9; ++c)
-                if (nu(c, k) != 0) e.jac(R_RX + k, LX + c, nu(c, k) / in.q[LX + c]);
+                if (nu(c, k) != 0) e.jac(R_RX + k, LX + c, nu(c, k) * iq[c]);
             e.jac(R_RX + k, LT, -sT * (-P.KE_B[k] * invT * invT + P.KE_C[k] * invT + P.KE_D[k]));
         }
         // (4)
@@ -295,8 +301,8 @@ __host__ __device__ inline void stage_eval(const Params& P, const StageIn& in, c
             e.jac(R_E, BT, -sT * Vb * CVb);
         }
         // (10b)
-        e.jac(R_H, LV, P.R * T / Pr);
-        e.jac(R_H, LT, V * P.R * sT / Pr);
+        e.jac(R_H, LV, P.R * T * iPr);
+        e.jac(R_H, LT, V * P.R * sT * iPr);
         e.jac(R_H, LS, 1.0);
         e.jac(R_H, LD_, -P.u_max * M_PI * in.d * 0.5);
     }
@@ -343,8 +349,7 @@ __host__ __device__ inline void stage_eval(const Params& P, const StageIn& in, c
                             any = true;
                         }
                     if (any) {
-                        const double qk = in.q[LX + k];
-                        v += -a / (qk * qk);
+                        v += -a * iq[k] * iq[k];
                         present = true;
                     }
                 }
@@ -368,7 +373,7 @@ __host__ __device__ inline void stage_eval(const Params& P, const StageIn& in, c
 #pragma unroll
         for (int j = 0; j < 4; ++j) e.hes(LT, LY + j, sT * P.sy[j] * muEV * V * cpV[j]);
         e.hes(LT, LL, sT * muEL * CL);
-        e.hes(LT, LV, sT * muEV * CV + lH * P.R * sT / Pr);
+        e.hes(LT, LV, sT * muEV * CV + lH * P.R * sT * iPr);
         // (T, T)
         {
             double dCL = 0.0, dCV = 0.0;
