@@ -721,7 +721,7 @@ abs_status solve_j(abs_problem* h, int prec, const double* jac, const double* x,
 template <class T, int W>
 void solve_t_w(abs_problem* h, const double* jac, const double* g, double* out, cudaStream_t st) {
     solve_t_warp_kernel<T, W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (const T*)h->LU, h->piv,
-                                                               g, out);
+                                                               (const T*)h->G, g, out);
 }
 
 template <class T>
@@ -1488,7 +1488,7 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
     CK(cudaMemcpyAsync(sol_x + od, &dd, sizeof(double), cudaMemcpyHostToDevice, st));
     dz_kernel<<<gq, kThr, 0, st>>>((int)S, ld, bv, hess_vals, sigma, true, pv, qv, rhs_x, sol_x, gv);
     NA_LAUNCHED();
-    solve_t_warp_kernel<double><<<gs, 32 * WPB_S, 0, st>>>((int)S, ld, bv, jac_vals, LU, piv, gv, sol_c);
+    solve_t_warp_kernel<double><<<gs, 32 * WPB_S, 0, st>>>((int)S, ld, bv, jac_vals, LU, piv, G, gv, sol_c);
     NA_LAUNCHED();
 #undef NA_LAUNCHED
     // dd lives on this stack frame until the copy above has completed

@@ -484,13 +484,23 @@ __global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, in
     }
 }
 
-// J_s^T v = g, one warp per scenario; g and out in primal layout (no d)
+// stage unknown j -> its index among the 11 stream-from-above unknowns (-1: none)
+__host__ __device__ constexpr int abv_index(int j) { return j < 9 ? j : (j == LL ? 9 : (j == LT ? 10 : -1)); }
+
+// J_s^T v = g, one warp per scenario; g in primal layout (no d), out in row layout.
+// With the block LU J = L U (L: diagonal blocks At_n, sub-diagonal C_n; U: identity
+// diagonal, super-diagonal G_n = At_n^-1 B_n), J^T = U^T L^T:
+//   forward   w_0 = g_0,  w_{n+1} = g_{n+1} - G_n^T w_n   (into stage n+1's 11 unknowns
+//             that stage n reads: products with the stored G blocks, no block solve)
+//   backward  v_9 = At_9^-T w_9,  v_n = At_n^-T (w_n - C_{n+1}^T v_{n+1})
+// one transposed block solve per stage.
 template <class T, int WPB = WPB_S>
 __global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t ld, const BView b,
-                                                                  const double* __restrict__ jac,
-                                                                  const T* __restrict__ LU,
-                                                                  const unsigned char* __restrict__ piv,
-                                                                  const double* __restrict__ g, double* out) {
+                                                                const double* __restrict__ jac,
+                                                                const T* __restrict__ LU,
+                                                                const unsigned char* __restrict__ piv,
+                                                                const T* __restrict__ G,
+                                                                const double* __restrict__ g, double* out) {
     __shared__ T sL[WPB][NV][PADL];
     __shared__ unsigned char sP[WPB][NV + 2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -499,53 +509,51 @@ __global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t l
     T(*A)[PADL] = sL[warp];
     unsigned char* pv = sP[warp];
     const bool row = lane < NV;
-    T u = T(0);
+    const int my_abv = abv_index(lane);   // lane j takes the product of column abv_index(j)
+    // forward sweep with the G blocks (fetched one stage ahead); w_n kept in out
+    T w = row ? (T)g[(int64_t)lane * ld + s] : T(0);
+    if (row) out[(int64_t)lane * ld + s] = (double)w;
+    T gn[NV];
+    auto fetch_g = [&](int n) {
+        const T* Gn = G + g_off(s, n);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) gn[i] = lane < NABV ? Gn[i * NABV + lane] : T(0);
+    };
+    fetch_g(0);
+    for (int n = 1; n < N_STAGES; ++n) {
+        T gc[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) gc[i] = gn[i];
+        if (n + 1 < N_STAGES) fetch_g(n);
+        const T gnext = row ? (T)g[(int64_t)(NV * n + lane) * ld + s] : T(0);
+        // lane a < 11: (G_{n-1}^T w_{n-1})_a = sum_i G_{n-1}[i][a] w_{n-1,i}
+        T acc = T(0);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc += gc[i] * shfl(w, i);
+        const T t = shfl(acc, my_abv >= 0 ? my_abv : 0);
+        w = gnext - (my_abv >= 0 ? t : T(0));
+        if (row) out[(int64_t)(NV * n + lane) * ld + s] = (double)w;
+    }
+    // backward sweep: one transposed block solve per stage
     LUPrefetch<T> pre;
-    pre.fetch(LU, piv, s, 0, lane);
-    T gnext = row ? (T)g[(int64_t)lane * ld + s] : T(0);
-    // forward (U^T of the block LU): u_n = At_n^-T (g_n - B_{n-1}^T u_{n-1})
-    for (int n = 0; n < N_STAGES; ++n) {
+    pre.fetch(LU, piv, s, N_STAGES - 1, lane);
+    T v = T(0);
+    for (int n = N_STAGES - 1; n >= 0; --n) {
         pre.commit(A, pv, lane);
-        T w = gnext;
+        T rhs = row ? (T)out[(int64_t)(NV * n + lane) * ld + s] : T(0);
+        if (n > 0) pre.fetch(LU, piv, s, n - 1, lane);
         if (n + 1 < N_STAGES) {
-            pre.fetch(LU, piv, s, n + 1, lane);
-            gnext = row ? (T)g[(int64_t)(NV * (n + 1) + lane) * ld + s] : T(0);
-        } else {
-            pre.fetch(LU, piv, s, N_STAGES - 2, lane);   // first stage of the backward pass
-        }
-        if (n > 0) {
-            const int tb = stage_type(n - 1), bb = c_segJ[n - 1];
-            const int nq = c_nabv[tb];
-            const T cvq = load_coupling<T>(c_abv[tb], nq, bb, jac, ld, s, lane);
-            const T pq = cvq * shfl(u, lane < nq ? (int)c_abv[tb][lane].r : 0);
+            const int ta = stage_type(n + 1), ba = c_segJ[n + 1];
+            const int nq = c_nblw[ta];
+            const T cvq = load_coupling<T>(c_blw[ta], nq, ba, jac, ld, s, lane);
+            const T pq = cvq * shfl(v, lane < nq ? (int)c_blw[ta][lane].r : 0);
             for (int q = 0; q < nq; ++q) {
                 const T pp = shfl(pq, q);
-                if (lane == abv_var(c_abv[tb][q].c)) w -= pp;
+                if (lane == blw_var(c_blw[ta][q].c)) rhs -= pp;
             }
         }
         __syncwarp();
-        u = lu_apply_t_warp<T>(A, pv, lane, w);
-        if (row) out[(int64_t)(NR * n + lane) * ld + s] = (double)u;
-        __syncwarp();
-    }
-    // backward (L^T): v_n = u_n - At_n^-T C_{n+1}^T v_{n+1}   (u holds v_9 = u_9)
-    T v = u;
-    for (int n = N_STAGES - 2; n >= 0; --n) {
-        pre.commit(A, pv, lane);
-        const T un = row ? (T)out[(int64_t)(NR * n + lane) * ld + s] : T(0);
-        if (n > 0) pre.fetch(LU, piv, s, n - 1, lane);
-        const int ta = stage_type(n + 1), ba = c_segJ[n + 1];
-        const int nq = c_nblw[ta];
-        const T cvq = load_coupling<T>(c_blw[ta], nq, ba, jac, ld, s, lane);
-        const T pq = cvq * shfl(v, lane < nq ? (int)c_blw[ta][lane].r : 0);
-        T w = T(0);
-        for (int q = 0; q < nq; ++q) {
-            const T pp = shfl(pq, q);
-            if (lane == blw_var(c_blw[ta][q].c)) w += pp;
-        }
-        __syncwarp();
-        w = lu_apply_t_warp<T>(A, pv, lane, w);
-        v = un - w;
+        v = lu_apply_t_warp<T>(A, pv, lane, rhs);
         if (row) out[(int64_t)(NR * n + lane) * ld + s] = (double)v;
         __syncwarp();
     }
