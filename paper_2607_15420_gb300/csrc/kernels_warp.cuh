@@ -176,7 +176,11 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
         const T tiny = assemble_stage<T>(n, ld, s, lane, jac, pivtol, A, Gp);
         const unsigned long long ktiny = abs_key(tiny);
         unsigned char* pv = piv + pv_off(s, n);
-        // LU with partial pivoting, row operations on all 33 columns
+        // LU with partial pivoting, row operations on all 33 columns.  FP64: fully unrolled
+        // (static shared-memory offsets, independent row updates; measured 3 % faster);
+        // FP32: rolled (the unrolled body's size costs more than it gains)
+        constexpr int UNR = sizeof(T) == 8 ? NV : 1;
+#pragma unroll UNR
         for (int k = 0; k < NV; ++k) {
             // key 0 marks lanes outside the candidate rows (an exact zero candidate also has
             // key 0 and loses ties to lower rows: the singular test below catches it)
@@ -203,7 +207,8 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
             const int j = k + 1 + lane;
             if (j < NCA) {
                 const T akj = A[k][j];
-#pragma unroll 4
+                constexpr int UNI = sizeof(T) == 8 ? NV : 4;
+#pragma unroll UNI
                 for (int i = k + 1; i < NV; ++i) A[i][j] -= A[i][k] * akj;
             }
             if (lane == 0) A[k][k] = inv;
@@ -212,11 +217,13 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
         // U G = L^-1 P B: lanes 0..21 = (column a = lane % 11, row parity lane / 11)
         if (n + 1 < N_STAGES) {
             const int a = lane % NABV, grp = lane / NABV;
+#pragma unroll UNR
             for (int i = NV - 1; i >= 0; --i) {
                 const T g = A[i][NV + a] * A[i][i];
                 __syncwarp();
                 if (grp < 2) {
-#pragma unroll 4
+                    constexpr int UNG = sizeof(T) == 8 ? NV : 4;
+#pragma unroll UNG
                     for (int r = grp; r < i; r += 2) A[r][NV + a] -= A[r][i] * g;
                     if (grp == 0) A[i][NV + a] = g;
                 }
