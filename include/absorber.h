@@ -261,7 +261,11 @@ typedef struct abs_options {
     int32_t graphs;        /* 1: the Schur-reduced KKT solve (7 launches) is captured into a
                               CUDA graph on the engine's stream at its second use with a
                               given set of vectors and replayed from then on */
-    int32_t reserved_opt;
+    int32_t factor_tile;   /* FP32 factor launches only: 0 shape from autotune; 1, 2, 4, 8:
+                              the shared-memory kernel with that many warps per block;
+                              17, 18, 20, 24: the register-resident kernel with 1, 2, 4, 8
+                              warps per block (identical results); other values are
+                              rejected with ABS_ERR_ARG */
 } abs_options;
 
 void abs_default_options(abs_options* o);

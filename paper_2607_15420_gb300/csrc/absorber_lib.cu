@@ -221,11 +221,15 @@ bool build_pattern(PatternTables& T, std::string& err) {
         ptr[NV] = (short)m;
     };
     for (int t = 0; t < 3; ++t) {
-        for (int k = 1; k < T.nown[t]; ++k)
-            if (T.own[t][k].r < T.own[t][k - 1].r) {
-                err = "own table not in row order";
-                return false;
-            }
+        auto rowsorted = [](const Ent* tab, int cnt) {
+            for (int k = 1; k < cnt; ++k)
+                if (tab[k].r < tab[k - 1].r) return false;
+            return true;
+        };
+        if (!rowsorted(T.own[t], T.nown[t]) || !rowsorted(T.abv[t], T.nabv[t]) || !rowsorted(T.blw[t], T.nblw[t])) {
+            err = "stage table not in row order";
+            return false;
+        }
         rowptr(T.own[t], T.nown[t], T.ownRp[t]);
         rowptr(T.abv[t], T.nabv[t], T.abvRp[t]);
         rowptr(T.blw[t], T.nblw[t], T.blwRp[t]);
@@ -298,6 +302,10 @@ cudaError_t upload_tables(int dev) {
     UP(c_blwCp, T.blwCp);
     UP(c_hesF, T.hesF);
     UP(c_hesFp, T.hesFp);
+    UP(g_own, T.own);
+    UP(g_abv, T.abv);
+    UP(g_blw, T.blw);
+    UP(g_blwRp, T.blwRp);
 #undef UP
     g_uploaded[dev] = true;
     return cudaSuccess;
@@ -346,6 +354,7 @@ struct abs_problem {
     int nchunk = 0;
     int* pchunk = nullptr;       // [NP + 1]
     double* cred = nullptr;      // [KMAX][nchunk]
+    int* rcnt = nullptr;         // [NP] chunk arrivals of the running reduction (zero between launches)
     double* red = nullptr;       // [KMAX][NP]
     double* hred = nullptr;      // pinned [KMAX][NP] + [2][NP] fetched scalars
     double* ps = nullptr;        // device per-problem scalars [PS_NFIELDS][NP]
@@ -365,6 +374,7 @@ struct abs_problem {
     } fac;
     Prof prof;
     int autotune = 1;                // tile autotuner on (options.autotune)
+    int factor_tile = 0;             // forced FP32 factor shape (options.factor_tile; 0: none)
     // the engine's own stream (stream capture needs a non-default stream) and the event
     // that orders it after the caller's stream
     cudaStream_t stream = nullptr;
@@ -482,6 +492,8 @@ abs_status ensure_buffers(abs_problem* h) {
     CK(cudaMalloc(&h->pchunk, sizeof(int) * pc.size()));
     CK(cudaMemcpy(h->pchunk, pc.data(), sizeof(int) * pc.size(), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&h->cred, sizeof(double) * (size_t)KMAX * h->nchunk));
+    CK(cudaMalloc(&h->rcnt, sizeof(int) * (size_t)h->NP));
+    CK(cudaMemset(h->rcnt, 0, sizeof(int) * (size_t)h->NP));
     CK(cudaMalloc(&h->red, sizeof(double) * (size_t)KMAX * h->NP));
     CK(cudaMallocHost(&h->hred, sizeof(double) * (size_t)(KMAX + 2) * h->NP));
     CK(cudaMalloc(&h->ps, sizeof(double) * (size_t)PS_NFIELDS * h->NP));
@@ -550,12 +562,10 @@ RedOps make_ops(std::initializer_list<int> l) {
 // h->hred + KMAX * NP, in one round trip
 abs_status reduce(abs_problem* h, cudaStream_t st, int K, const RedOps& ops, int flag, bool fetch,
                   const double* dslots = nullptr) {
-    chunk_reduce_kernel<<<(unsigned)h->nchunk, RED_T, 0, st>>>(h->part, h->ld, K, ops, h->chunks, h->nchunk, h->ps,
-                                                               h->NP, flag, h->cred);
+    reduce_kernel<<<(unsigned)h->nchunk, RED_T, 0, st>>>(h->part, h->ld, K, ops, h->chunks, h->nchunk, h->pchunk,
+                                                         h->ps, h->NP, flag, h->cred, h->rcnt, h->red);
     abs_status r = launch_check(h);
     if (r != ABS_OK) return r;
-    problem_reduce_kernel<<<(unsigned)h->NP, 32, 0, st>>>(h->cred, h->nchunk, K, ops, h->pchunk, h->NP, h->red);
-    if ((r = launch_check(h)) != ABS_OK) return r;
     if (!fetch) return ABS_OK;
     CK(cudaMemcpyAsync(h->hred, h->red, sizeof(double) * (size_t)K * h->NP, cudaMemcpyDeviceToHost, st));
     if (dslots)
@@ -676,7 +686,10 @@ abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaS
         return launch_check(h);
     };
     abs_status r;
-    if (std::is_same<T, float>::value)
+    if (std::is_same<T, float>::value && h->factor_tile != 0) {
+        h->tile[TK_FACTOR] = h->factor_tile;
+        r = go(h->factor_tile);
+    } else if (std::is_same<T, float>::value)
         r = tuned_launch(h, TK_FACTOR, sizeof(T),
                          {1, 2, 4, 8, FACTOR_REG + 1, FACTOR_REG + 2, FACTOR_REG + 4, FACTOR_REG + 8}, WPB_F, go, st);
     else
@@ -1105,6 +1118,7 @@ void absorber_destroy(abs_problem* h) {
     cudaFree(h->chunks);
     cudaFree(h->pchunk);
     cudaFree(h->cred);
+    cudaFree(h->rcnt);
     cudaFree(h->red);
     cudaFreeHost(h->hred);
     cudaFree(h->ps);

@@ -38,6 +38,12 @@ __constant__ Ent c_blw[3][MAXBLW];
 __constant__ Ent c_hes[NHS];
 __constant__ int c_nown[3], c_nabv[3], c_nblw[3];
 __constant__ int c_dslot[3];           // the d entry of the stage's hydraulic row
+// Global-memory copies of the stage tables for reads in which every lane takes a
+// different entry (a constant-cache read with 32 different addresses is serialized).
+__device__ Ent g_own[3][MAXOWN];
+__device__ Ent g_abv[3][MAXABV];
+__device__ Ent g_blw[3][MAXBLW];
+__device__ short g_blwRp[3][NV + 1];
 // The same entries grouped by destination, so that the sparse products below accumulate
 // into statically indexed registers (table-indexed register arrays would live in local
 // memory): row pointers of the row-ordered tables (J v), copies ordered by the unknown
@@ -91,8 +97,8 @@ __device__ inline int live_prob(const BView& b, int s, int S, int flag) {
 
 // ------------------------------------------------------------------------------------
 // reductions: every (scenario, stage) thread stores its K partial values at
-// part[k * plane + n * ld + s] (plane = N_STAGES * ld); chunk_reduce / problem_reduce
-// (vec_kernels.cuh) combine them per problem in a fixed order (deterministic)
+// part[k * plane + n * ld + s] (plane = N_STAGES * ld); reduce_kernel (vec_kernels.cuh)
+// combines them per problem in a fixed order (deterministic)
 // ------------------------------------------------------------------------------------
 enum RedOp { RSUM = 0, RMAX = 1, RMIN = 2 };
 

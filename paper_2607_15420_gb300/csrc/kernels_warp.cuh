@@ -80,6 +80,10 @@ __device__ inline double recip(double a) {
 }
 __device__ inline float recip(float a) { return 1.0f / a; }
 
+// x - a b with one rounding (the factor variants must round identically)
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
 // the coefficients of a stage-coupling table (<= 32 entries) for scenario s, entry q on
 // lane q: one parallel load instead of a dependent load per entry inside the
 // sequential coupling loops
@@ -127,12 +131,12 @@ __device__ inline T assemble_stage(int n, int64_t ld, int s, int lane, const dou
     for (int e = lane; e < NV * NCA; e += 32) A[e / NCA][e % NCA] = T(0);
     __syncwarp();
     for (int k = lane; k < c_nown[t]; k += 32) {
-        const Ent e = c_own[t][k];
+        const Ent e = g_own[t][k];
         A[e.r][e.c] = (T)jac[(int64_t)(base + e.slot) * ld + s];
     }
     if (n + 1 < N_STAGES) {
         for (int k = lane; k < c_nabv[t]; k += 32) {
-            const Ent e = c_abv[t][k];
+            const Ent e = g_abv[t][k];
             A[e.r][NV + e.c] = (T)jac[(int64_t)(base + e.slot) * ld + s];
         }
     }
@@ -140,11 +144,11 @@ __device__ inline T assemble_stage(int n, int64_t ld, int s, int lane, const dou
     // Schur update with the previous stage: A_n -= C_n G_{n-1}
     if (n > 0) {
         const int nq = c_nblw[t];
-        const T cvq = load_coupling<T>(c_blw[t], nq, base, jac, ld, s, lane);
+        const T cvq = load_coupling<T>(g_blw[t], nq, base, jac, ld, s, lane);
         for (int k = 0; k < nq; ++k) {
             const Ent e = c_blw[t][k];
             const T cv = shfl(cvq, k);
-            if (lane < NABV) A[e.r][abv_var(lane)] -= cv * Gp[blw_var(e.c)][lane];
+            if (lane < NABV) A[e.r][abv_var(lane)] = fma_t(-cv, Gp[blw_var(e.c)][lane], A[e.r][abv_var(lane)]);
             __syncwarp();
         }
     }
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
                 const T akj = A[k][j];
                 constexpr int UNI = sizeof(T) == 8 ? NV : 4;
 #pragma unroll UNI
-                for (int i = k + 1; i < NV; ++i) A[i][j] -= A[i][k] * akj;
+                for (int i = k + 1; i < NV; ++i) A[i][j] = fma_t(-A[i][k], akj, A[i][j]);
             }
             if (lane == 0) A[k][k] = inv;
             __syncwarp();
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
                 if (grp < 2) {
                     constexpr int UNG = sizeof(T) == 8 ? NV : 4;
 #pragma unroll UNG
-                    for (int r = grp; r < i; r += 2) A[r][NV + a] -= A[r][i] * g;
+                    for (int r = grp; r < i; r += 2) A[r][NV + a] = fma_t(-A[r][i], g, A[r][NV + a]);
                     if (grp == 0) A[i][NV + a] = g;
                 }
                 __syncwarp();
@@ -243,92 +247,170 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
     if (lane == 0) sing[s] = singular;
 }
 
-// FP32 variant with the block in registers: lane i < 22 holds row i of [A_n | B_n] (33
-// values); the pivot search is a warp max over the rows' keys, the row swap and the pivot
-// row's broadcast are shuffles, the rank-1 update runs on registers, and G_n comes from a
-// shuffle-driven back substitution.  Same operations in the same order as
-// factor_warp_kernel (identical results), without its shared-memory traffic: the FP32
-// kernel is issue-bound, the FP64 one is bound by the FP64 pipe and keeps the
-// columns-on-lanes form, which fills more lanes per FP64 instruction.
+// FP32 variant with the block in registers: lane i < 22 keeps row i of [A_n | B_n] (33
+// values as 17 float pairs) for the whole elimination.  Rows are never moved: each lane
+// tracks the position its row holds in the row-swap sequence (LAPACK order, stored as
+// for factor_warp_kernel), the pivot search takes the largest |value| among the rows not
+// yet chosen and breaks ties by that position, the chosen row's remaining columns are
+// broadcast through shared memory, and the rank-1 update runs as paired FP32 FMAs.  G_n
+// comes from a back substitution with the U rows in registers.  Every entry sees the same
+// operations in the same order as in factor_warp_kernel, so both give identical factors.
+constexpr int NPR = (NCA + 1) / 2;   // float pairs per augmented row (column 33: padding)
+
+__device__ __forceinline__ float& rv(float2* r, int j) { return (j & 1) ? r[j >> 1].y : r[j >> 1].x; }
+
 template <int WPB = WPB_F>
 __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld, const BView b,
                                                               const double* __restrict__ jac, float* __restrict__ LU,
                                                               unsigned char* __restrict__ piv, float* __restrict__ G,
                                                               int* __restrict__ sing, double pivtol) {
-    __shared__ float sA[WPB][NV][PADA];
-    __shared__ float sG[WPB][NV][NABV];
+    // per warp: the assembly block (reused as the row-major LU block on the way out), G_n
+    // by unknown (the next stage's Schur update reads it), the broadcast pivot row, and
+    // the row of each position
+    __shared__ __align__(16) float sA[WPB][NV * PADA];
+    __shared__ __align__(16) float sG[WPB][NV * NABV + 2];
+    __shared__ __align__(16) float sU[WPB][2 * NPR + 2];
+    __shared__ unsigned char sQ[WPB][32];
+    const unsigned full = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * WPB + warp;
     if (live_prob(b, s, S, PS_ACT) < 0) return;   // whole warps leave together
-    float(*A)[PADA] = sA[warp];
-    float(*Gp)[NABV] = sG[warp];
+    float* A = sA[warp];
+    float* Gs = sG[warp];
+    float* U = sU[warp];
     const bool rowlane = lane < NV;
     int singular = 0;
+#pragma unroll 1
     for (int n = 0; n < N_STAGES; ++n) {
-        const float tiny = assemble_stage<float>(n, ld, s, lane, jac, pivtol, A, Gp);
-        const unsigned long long ktiny = abs_key(tiny);
-        unsigned char* pv = piv + pv_off(s, n);
-        float row[NCA];
-        __syncwarp();
+        const int t = stage_type(n);
+        const int base = c_segJ[n];
+        // assemble: rows zeroed, the stage's entries scattered, rows to registers
+        if (rowlane) {
 #pragma unroll
-        for (int j = 0; j < NCA; ++j) row[j] = rowlane ? A[lane][j] : 0.0f;
+            for (int m = 0; m < NPR; ++m) *reinterpret_cast<float2*>(&A[lane * PADA + 2 * m]) = make_float2(0.f, 0.f);
+        }
+        __syncwarp();
+        for (int k = lane; k < c_nown[t]; k += 32) {
+            const Ent e = g_own[t][k];
+            A[e.r * PADA + e.c] = (float)jac[(int64_t)(base + e.slot) * ld + s];
+        }
+        if (n + 1 < N_STAGES) {
+            for (int k = lane; k < c_nabv[t]; k += 32) {
+                const Ent e = g_abv[t][k];
+                A[e.r * PADA + NV + e.c] = (float)jac[(int64_t)(base + e.slot) * ld + s];
+            }
+        }
+        __syncwarp();
+        float2 r2[NPR];
+#pragma unroll
+        for (int m = 0; m < NPR; ++m)
+            r2[m] = rowlane ? *reinterpret_cast<const float2*>(&A[lane * PADA + 2 * m]) : make_float2(0.f, 0.f);
+        // Schur update with the previous stage, A_n -= C_n G_{n-1}: each row applies its own
+        // entries of C_n in table order
+        if (n > 0 && rowlane) {
+            const int q1 = g_blwRp[t][lane + 1];
+            for (int q = g_blwRp[t][lane]; q < q1; ++q) {
+                const Ent e = g_blw[t][q];
+                const float cv = (float)jac[(int64_t)(base + e.slot) * ld + s];
+                const float* gr = Gs + blw_var(e.c) * NABV;
+#pragma unroll
+                for (int a = 0; a < NABV; ++a) rv(r2, abv_var(a)) = fmaf(-cv, gr[a], rv(r2, abv_var(a)));
+            }
+        }
+        // the largest |entry| of the block gives the singularity threshold
+        unsigned km = 0u;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) km = max(km, __float_as_uint(rv(r2, j)) & 0x7fffffffu);
+        km = __reduce_max_sync(full, km);
+        const float tiny = (float)pivtol * __uint_as_float(km);
+        const unsigned ktiny = __float_as_uint(tiny) & 0x7fffffffu;
+        int cur = lane;             // position of this lane's row in the swap sequence
+        bool done = !rowlane;       // row already chosen (lanes >= 22 never take part)
+        int myq = 0;                // lane k: the lane whose row is chosen at step k
+        unsigned char mypv = 0;     // lane k: the swap of step k
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            const bool cand = lane >= k && rowlane;
-            int p = warp_argmax_key(cand ? abs_key(row[k]) : 0ull, cand);
-            if (p < 0 || p >= NV) p = k;
-            if (lane == 0) pv[k] = (unsigned char)p;
-            if (p != k) {
-                const int src = lane == k ? p : (lane == p ? k : lane);
-#pragma unroll
-                for (int j = 0; j < NCA; ++j) row[j] = __shfl_sync(0xffffffffu, row[j], src);
+            const unsigned key = done ? 0u : (__float_as_uint(rv(r2, k)) & 0x7fffffffu);
+            const unsigned mx = __reduce_max_sync(full, key);
+            const unsigned pos = __reduce_min_sync(full, (!done && key == mx) ? (unsigned)cur : 0xffu);
+            int p = __ffs((int)__ballot_sync(full, !done && (unsigned)cur == pos)) - 1;
+            p = p < 0 ? 0 : p;
+            if (lane == k) {
+                mypv = (unsigned char)pos;
+                myq = p;
             }
-            float ukk = __shfl_sync(0xffffffffu, row[k], k);
-            if (!(abs_key(ukk) > ktiny) || ukk != ukk) {
+            if (cur == k) cur = (int)pos;
+            if (lane == p) {
+                cur = k;
+                done = true;
+            }
+            float ukk = __shfl_sync(full, rv(r2, k), p);
+            if (!((__float_as_uint(ukk) & 0x7fffffffu) > ktiny) || ukk != ukk) {
                 singular = 1;
                 ukk = (ukk < 0.0f ? -1.0f : 1.0f) * (tiny > 0.0f ? tiny : 1.0f);
             }
             const float inv = recip(ukk);
-            const bool below = lane > k && rowlane;
-            if (below) row[k] *= inv;
-            const float l = row[k];
+            if (lane == p) {
 #pragma unroll
-            for (int j = k + 1; j < NCA; ++j) {
-                const float u = __shfl_sync(0xffffffffu, row[j], k);
-                if (below) row[j] -= l * u;
+                for (int m = k / 2; m < NPR; ++m) *reinterpret_cast<float2*>(&U[2 * m]) = r2[m];
             }
-            if (lane == k) row[k] = inv;
+            __syncwarp();
+            if (!done) {
+                const float l = rv(r2, k) * inv;
+                rv(r2, k) = l;
+                if ((k & 1) == 0) r2[k / 2].y = fmaf(-l, U[k + 1], r2[k / 2].y);
+                const float2 nl = make_float2(-l, -l);
+#pragma unroll
+                for (int m = k / 2 + 1; m < NPR; ++m)
+                    r2[m] = __ffma2_rn(nl, *reinterpret_cast<const float2*>(&U[2 * m]), r2[m]);
+            }
+            __syncwarp();
+            if (lane == p) rv(r2, k) = inv;
         }
-        // U G = L^-1 P B (the B columns of the rows), i from the bottom up
+        if (rowlane) sQ[warp][lane] = (unsigned char)myq;
+        __syncwarp();
+        // U G = L^-1 P B, positions from the bottom up: the row at position i scales its B
+        // columns by 1 / U_ii (kept on its diagonal), the rows above subtract
         if (n + 1 < N_STAGES) {
 #pragma unroll
             for (int i = NV - 1; i >= 0; --i) {
-                const float dinv = __shfl_sync(0xffffffffu, row[i], i);   // 1 / U_ii
+                const int q = sQ[warp][i];
+                if (lane == q) {
+                    const float d = rv(r2, i);
 #pragma unroll
-                for (int a = 0; a < NABV; ++a) {
-                    const float g = __shfl_sync(0xffffffffu, row[NV + a], i) * dinv;
-                    if (lane < i) row[NV + a] -= row[i] * g;
-                    if (lane == i) row[NV + a] = g;
+                    for (int m = NV / 2; m < NPR; ++m) r2[m] = __fmul2_rn(r2[m], make_float2(d, d));
+                }
+                float2 g2[NPR - NV / 2];
+#pragma unroll
+                for (int m = 0; m < NPR - NV / 2; ++m) {
+                    g2[m].x = __shfl_sync(full, r2[NV / 2 + m].x, q);
+                    g2[m].y = (2 * m + 1 < NABV) ? __shfl_sync(full, r2[NV / 2 + m].y, q) : 0.0f;
+                }
+                if (cur < i) {
+                    const float nu = -rv(r2, i);
+                    const float2 nu2 = make_float2(nu, nu);
+#pragma unroll
+                    for (int m = 0; m < NPR - NV / 2; ++m) r2[NV / 2 + m] = __ffma2_rn(nu2, g2[m], r2[NV / 2 + m]);
                 }
             }
         }
-        __syncwarp();
-        // rows to shared memory, then coalesced stores of LU and G
+        // rows to shared memory at their positions, then coalesced stores
         if (rowlane) {
 #pragma unroll
-            for (int j = 0; j < NCA; ++j) A[lane][j] = row[j];
+            for (int m = 0; m < NV / 2; ++m) *reinterpret_cast<float2*>(&A[cur * NV + 2 * m]) = r2[m];
+            if (n + 1 < N_STAGES) {
+#pragma unroll
+                for (int a = 0; a < NABV; ++a) Gs[cur * NABV + a] = rv(r2, NV + a);
+            }
+            piv[pv_off(s, n) + lane] = mypv;
         }
         __syncwarp();
+        float4* Ln = reinterpret_cast<float4*>(LU + lu_off(s, n));
+        for (int e = lane; e < NV * NV / 4; e += 32) Ln[e] = reinterpret_cast<const float4*>(A)[e];
         if (n + 1 < N_STAGES) {
-            float* Gn = G + g_off(s, n);
-            for (int e = lane; e < NV * NABV; e += 32) {
-                const float g = A[e / NABV][NV + e % NABV];
-                Gn[e] = g;
-                Gp[e / NABV][e % NABV] = g;
-            }
+            float2* Gn = reinterpret_cast<float2*>(G + g_off(s, n));
+            for (int e = lane; e < NV * NABV / 2; e += 32) Gn[e] = reinterpret_cast<const float2*>(Gs)[e];
         }
-        float* Ln = LU + lu_off(s, n);
-        for (int e = lane; e < NV * NV; e += 32) Ln[e] = A[e / NV][e % NV];
         __syncwarp();
     }
     if (lane == 0) sing[s] = singular;
@@ -439,8 +521,8 @@ __global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, in
             // products of C_n's entries (entry q on lane q) with y_{n-1}, then added to
             // their rows in entry order
             const int nq = c_nblw[t];
-            const T cvq = load_coupling<T>(c_blw[t], nq, base, jac, ld, s, lane);
-            const int src = lane < nq ? blw_var(c_blw[t][lane].c) : 0;
+            const T cvq = load_coupling<T>(g_blw[t], nq, base, jac, ld, s, lane);
+            const int src = lane < nq ? blw_var(g_blw[t][lane].c) : 0;
 #pragma unroll
             for (int k = 0; k < NRHS; ++k) {
                 const T pq = cvq * shfl(y[k], src);
@@ -552,8 +634,8 @@ __global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t l
         if (n + 1 < N_STAGES) {
             const int ta = stage_type(n + 1), ba = c_segJ[n + 1];
             const int nq = c_nblw[ta];
-            const T cvq = load_coupling<T>(c_blw[ta], nq, ba, jac, ld, s, lane);
-            const T pq = cvq * shfl(v, lane < nq ? (int)c_blw[ta][lane].r : 0);
+            const T cvq = load_coupling<T>(g_blw[ta], nq, ba, jac, ld, s, lane);
+            const T pq = cvq * shfl(v, lane < nq ? (int)g_blw[ta][lane].r : 0);
             for (int q = 0; q < nq; ++q) {
                 const T pp = shfl(pq, q);
                 if (lane == blw_var(c_blw[ta][q].c)) rhs -= pp;

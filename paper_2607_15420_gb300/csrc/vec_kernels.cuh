@@ -4,7 +4,7 @@
 // the method (mu, tau, step sizes, delta_w, the diameter d and its step) is per problem:
 // scalars from ps (BView), d and its step from the problem's d slot [NSC * ld + p] of
 // the primal vectors.  Reductions store per-thread partials (store_partials) that
-// chunk_reduce_kernel + problem_reduce_kernel combine per problem in a fixed order.
+// reduce_kernel combines them per problem in a fixed order.
 #pragma once
 
 #include "kernels.cuh"
@@ -532,13 +532,21 @@ __device__ inline double warp_red(int op, double a) {
     return a;
 }
 
-// one block per chunk of a problem's (stage, slot) elements: every plane k < K reduced in
-// a fixed order (4 elements per thread, xor trees within warps, warps in order)
-__global__ void __launch_bounds__(RED_T) chunk_reduce_kernel(const double* __restrict__ part, int64_t ld, int K,
-                                                             const RedOps ops, const int* __restrict__ ch,
-                                                             int nchunk, const double* __restrict__ ps, int NP,
-                                                             int flag, double* __restrict__ out) {
+// One block per chunk of a problem's (stage, slot) elements: every plane k < K reduced in
+// a fixed order (4 elements per thread, xor trees within warps, warps in order) into
+// cout[k][c].  The problem's chunk block that finishes last (a per-problem arrival
+// counter; no block waits for another) then combines the problem's chunk results, chunk c
+// on lane (c - c0) % 32 in increasing c, then an xor tree, into out[k][p] and re-arms the
+// counter.  Every combination order depends on the problem's own size only.  All of a
+// thread's loads are issued before the first combination (one memory latency per block
+// instead of one per plane).
+__global__ void __launch_bounds__(RED_T) reduce_kernel(const double* __restrict__ part, int64_t ld, int K,
+                                                       const RedOps ops, const int* __restrict__ ch, int nchunk,
+                                                       const int* __restrict__ pchunk, const double* __restrict__ ps,
+                                                       int NP, int flag, double* cout, int* cnt,
+                                                       double* __restrict__ out) {
     __shared__ double sm[RED_T / 32][RED_KMAX];
+    __shared__ int last;
     const int c = blockIdx.x;
     const int p = ch[5 * c + 0], off = ch[5 * c + 1], Sp = ch[5 * c + 2], i0 = ch[5 * c + 3], i1 = ch[5 * c + 4];
     const bool live = !ps || ps[(int64_t)flag * NP + p] != 0.0;
@@ -551,13 +559,20 @@ __global__ void __launch_bounds__(RED_T) chunk_reduce_kernel(const double* __res
         ok[t] = live && i < i1;
         idx[t] = ok[t] ? (int64_t)(i / Sp) * ld + off + i % Sp : 0;
     }
+    double v[RED_KMAX][RED_PER];
+#pragma unroll
+    for (int k = 0; k < RED_KMAX; ++k)
+#pragma unroll
+        for (int t = 0; t < RED_PER; ++t) v[k][t] = (k < K && ok[t]) ? part[(int64_t)k * plane + idx[t]] : 0.0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int k = 0; k < RED_KMAX; ++k) {
+        if (k >= K) break;
         const int op = ops.op[k];
         double a = red_id(op);
 #pragma unroll
         for (int t = 0; t < RED_PER; ++t)
-            if (ok[t]) a = red_op(op, a, part[(int64_t)k * plane + idx[t]]);
+            if (ok[t]) a = red_op(op, a, v[k][t]);
         a = warp_red(op, a);
         if (lane == 0) sm[warp][k] = a;
     }
@@ -567,21 +582,21 @@ __global__ void __launch_bounds__(RED_T) chunk_reduce_kernel(const double* __res
         double a = red_id(op);
 #pragma unroll
         for (int w = 0; w < RED_T / 32; ++w) a = red_op(op, a, sm[w][k]);
-        out[(int64_t)k * nchunk + c] = a;
+        cout[(int64_t)k * nchunk + c] = a;
     }
-}
-
-// one warp per problem: combine its chunks in a fixed order; out[k * NP + p]
-__global__ void __launch_bounds__(32) problem_reduce_kernel(const double* __restrict__ cout, int nchunk, int K,
-                                                            const RedOps ops, const int* __restrict__ pchunk, int NP,
-                                                            double* __restrict__ out) {
-    const int p = blockIdx.x, lane = threadIdx.x;
-    if (p >= NP) return;
     const int c0 = pchunk[p], c1 = pchunk[p + 1];
-    for (int k = 0; k < K; ++k) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&cnt[p], 1) == c1 - c0 - 1;
+    __syncthreads();
+    if (!last) return;
+    if (threadIdx.x == 0) cnt[p] = 0;
+    __threadfence();
+    // the problem's chunk results: plane k on warp k % 4 (L2 reads: other blocks wrote them)
+    for (int k = warp; k < K; k += RED_T / 32) {
         const int op = ops.op[k];
         double a = red_id(op);
-        for (int c = c0 + lane; c < c1; c += 32) a = red_op(op, a, cout[(int64_t)k * nchunk + c]);
+        for (int cc = c0 + lane; cc < c1; cc += 32) a = red_op(op, a, __ldcg(&cout[(int64_t)k * nchunk + cc]));
         a = warp_red(op, a);
         if (lane == 0) out[(int64_t)k * NP + p] = a;
     }

@@ -158,3 +158,24 @@ def test_graph_replay_gives_identical_results(B):
     assert outs[0][3] == 0 and outs[1][3] > outs[1][0]
     assert outs[0][0] == outs[1][0] and outs[0][1] == outs[1][1]
     assert np.array_equal(outs[0][2], outs[1][2])
+
+
+@pytest.mark.parametrize("S", [37, 600])
+def test_every_fp32_factor_shape_gives_identical_results(B, S):
+    # the shared-memory factor (rows swapped in place) and the register-resident factor
+    # (rows never moved, positions tracked per lane) apply the same operations in the same
+    # order: every launch shape gives the same solve bit for bit
+    import torch
+    F = ai.make_feeds(S, 2)
+    prob = B.Problem(P, F)
+    outs = []
+    for tile in (4, 1, 2, 8, 17, 18, 20, 24):
+        x = torch.zeros(prob.n_primal, dtype=torch.float64, device="cuda")
+        o = B.default_options(precision=1, max_refine=8, factor_tile=tile)
+        r = prob.ipm_solve(o, x_out=x)
+        assert r.status == 0, (tile, r.status)
+        assert r.tiles[0] == tile
+        outs.append((r.iters, r.d, _host(x)))
+    for t, o in zip((1, 2, 8, 17, 18, 20, 24), outs[1:]):
+        assert o[0] == outs[0][0] and o[1] == outs[0][1], t
+        assert np.array_equal(o[2], outs[0][2]), t
