@@ -240,9 +240,12 @@ def train_network(B, ai, n_train=20000, epochs=100):
     return net, info
 
 
+FACTOR_TILE = 0   # --factor-tile: a fixed FP32 factor launch shape (0: autotuned)
+
+
 def options(B, prec, profile=0, graphs=1):
     return B.default_options(precision=prec, max_refine=(8 if prec == B.PREC_FP32 else 0), profile=profile,
-                             graphs=graphs)
+                             graphs=graphs, factor_tile=FACTOR_TILE)
 
 
 def solve_form(B, prob, net, form, profile=0, graphs=1, x_out=None):
@@ -307,8 +310,13 @@ def main():
     ap.add_argument("--capture-iters", type=int, default=0,
                     help="profiling case: only N interior-point iterations of the workload from the inlet "
                          "start (no expected-value solve), then exit without a JSON line")
+    ap.add_argument("--factor-tile", type=int, default=0,
+                    help="fixed FP32 factor launch shape (1/2/4/8 shared-memory kernel, 17/18/20/24 register "
+                         "kernel; 0: autotuned) -- for profiling one variant")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    global FACTOR_TILE
+    FACTOR_TILE = args.factor_tile
 
     import absorber_inputs as ai
     S_full = ai.WORKLOADS[args.workload]["S"]
@@ -340,7 +348,7 @@ def main():
 
     if args.capture_iters > 0:
         r = prob.ipm_solve(B.default_options(precision=prec, max_refine=(8 if prec == B.PREC_FP32 else 0),
-                                             max_iter=args.capture_iters, init=1))
+                                             max_iter=args.capture_iters, init=1, factor_tile=FACTOR_TILE))
         torch.cuda.synchronize()
         print(f"capture case: {r.iters} iterations, status {B.STATUS.get(r.status)}", flush=True)
         return

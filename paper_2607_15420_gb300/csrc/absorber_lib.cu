@@ -233,6 +233,11 @@ bool build_pattern(PatternTables& T, std::string& err) {
         rowptr(T.own[t], T.nown[t], T.ownRp[t]);
         rowptr(T.abv[t], T.nabv[t], T.abvRp[t]);
         rowptr(T.blw[t], T.nblw[t], T.blwRp[t]);
+        for (int r = 0; r < NV; ++r)
+            if (T.blwRp[t][r + 1] - T.blwRp[t][r] > 6) {   // one entry per unknown of the stage below
+                err = "coupling row with more than 6 entries";
+                return false;
+            }
         bydest(T.own[t], T.nown[t], 0, T.ownC[t], T.ownCp[t]);
         bydest(T.abv[t], T.nabv[t], 1, T.abvC[t], T.abvCp[t]);
         bydest(T.blw[t], T.nblw[t], 2, T.blwC[t], T.blwCp[t]);
@@ -302,10 +307,16 @@ cudaError_t upload_tables(int dev) {
     UP(c_blwCp, T.blwCp);
     UP(c_hesF, T.hesF);
     UP(c_hesFp, T.hesFp);
-    UP(g_own, T.own);
-    UP(g_abv, T.abv);
-    UP(g_blw, T.blw);
-    UP(g_blwRp, T.blwRp);
+    {
+        static LaneTables lt;
+        std::memset(&lt, 0, sizeof(lt));
+        std::memcpy(lt.own, T.own, sizeof(lt.own));
+        std::memcpy(lt.abv, T.abv, sizeof(lt.abv));
+        std::memcpy(lt.blw, T.blw, sizeof(lt.blw));
+        for (int t = 0; t < 3; ++t)
+            for (int r = 0; r <= NV; ++r) lt.blwRp[t][r] = T.blwRp[t][r];
+        UP(g_lt, lt);
+    }
 #undef UP
     g_uploaded[dev] = true;
     return cudaSuccess;

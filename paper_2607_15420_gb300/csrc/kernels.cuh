@@ -38,12 +38,17 @@ __constant__ Ent c_blw[3][MAXBLW];
 __constant__ Ent c_hes[NHS];
 __constant__ int c_nown[3], c_nabv[3], c_nblw[3];
 __constant__ int c_dslot[3];           // the d entry of the stage's hydraulic row
-// Global-memory copies of the stage tables for reads in which every lane takes a
-// different entry (a constant-cache read with 32 different addresses is serialized).
-__device__ Ent g_own[3][MAXOWN];
-__device__ Ent g_abv[3][MAXABV];
-__device__ Ent g_blw[3][MAXBLW];
-__device__ short g_blwRp[3][NV + 1];
+// The stage tables that the factor and solve kernels read with a different entry on
+// every lane (a constant-cache read with 32 different addresses is serialized): one
+// global-memory copy, which each factor block stages into shared memory.
+struct __align__(16) LaneTables {
+    Ent own[3][MAXOWN];
+    Ent abv[3][MAXABV];
+    Ent blw[3][MAXBLW];
+    short blwRp[3][NV + 2];   // row pointers of blw (NV + 1 used; padded to 16 bytes)
+};
+static_assert(sizeof(LaneTables) % 16 == 0, "LaneTables is copied as 16-byte words");
+__device__ LaneTables g_lt;
 // The same entries grouped by destination, so that the sparse products below accumulate
 // into statically indexed registers (table-indexed register arrays would live in local
 // memory): row pointers of the row-ordered tables (J v), copies ordered by the unknown

@@ -25,7 +25,7 @@ constexpr int WPB_S = 4;          // default warps (scenarios) per block, solves
 // static shared memory of the factor kernel with W warps per block (must stay <= 48 KB)
 template <class T, int W>
 constexpr bool factor_fits() {
-    return (size_t)W * (NV * PADA + NV * NABV) * sizeof(T) <= 48 * 1024;
+    return (size_t)W * (NV * PADA + NV * NABV) * sizeof(T) + sizeof(LaneTables) <= 48 * 1024;
 }
 
 __host__ __device__ constexpr int64_t lu_off(int64_t s, int n) { return (s * N_STAGES + n) * (int64_t)(NV * NV); }
@@ -65,6 +65,15 @@ __device__ inline int warp_argmax_key(unsigned long long key, bool cand) {
     const unsigned won = __ballot_sync(0xffffffffu, cand && key == m);
     return __ffs((int)won) - 1;
 }
+
+// FP32 pivot key: |a| with its 5 lowest mantissa bits replaced by 31 - position, so that
+// one warp maximum both finds the pivot and breaks ties: the candidate of largest |a| up
+// to a relative 2^-18, the lowest position among those (threshold partial pivoting; an
+// all-zero column takes its lowest position, a NaN always wins)
+__device__ __forceinline__ unsigned pivot_key32(float a, int pos) {
+    return (__float_as_uint(a) & 0x7fffffe0u) | (unsigned)(31 - pos);
+}
+__device__ __forceinline__ int key_position(unsigned key) { return 31 - (int)(key & 31u); }
 
 // reciprocal: FP32 seed refined by two Newton steps r <- r (2 - a r) in T (|a| in the
 // normal FP32 range; exact division otherwise)
@@ -120,37 +129,83 @@ struct LUPrefetch {
     }
 };
 
+// the per-lane stage tables, copied once per block into shared memory (every thread of
+// the block takes part; call before any warp leaves)
+__device__ inline void stage_lane_tables(LaneTables& lt) {
+    const int4* src = reinterpret_cast<const int4*>(&g_lt);
+    int4* dst = reinterpret_cast<int4*>(&lt);
+    constexpr int NW = (int)(sizeof(LaneTables) / sizeof(int4));
+    for (int i = threadIdx.x; i < NW; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+}
+
+constexpr int OWN_PER_LANE = MAXOWN / 32, ABV_PER_LANE = MAXABV / 32;
+
+// the Jacobian values of stage n's own and super-diagonal entries that lane `lane`
+// scatters (entries lane, lane + 32, ...), every load issued before the first use
+struct StageLoads {
+    Ent eo[OWN_PER_LANE];
+    double vo[OWN_PER_LANE];
+    Ent ea[ABV_PER_LANE];
+    double va[ABV_PER_LANE];
+    int no, na;
+    __device__ inline void fetch(const LaneTables& lt, int n, int64_t ld, int s, int lane,
+                                 const double* __restrict__ jac) {
+        const int t = stage_type(n);
+        const int base = c_segJ[n];
+        no = c_nown[t];
+        na = n + 1 < N_STAGES ? c_nabv[t] : 0;
+#pragma unroll
+        for (int i = 0; i < OWN_PER_LANE; ++i) {
+            const int k = lane + 32 * i;
+            eo[i] = lt.own[t][k < no ? k : 0];
+        }
+#pragma unroll
+        for (int i = 0; i < ABV_PER_LANE; ++i) {
+            const int k = lane + 32 * i;
+            ea[i] = lt.abv[t][k < na ? k : 0];
+        }
+#pragma unroll
+        for (int i = 0; i < OWN_PER_LANE; ++i)
+            vo[i] = lane + 32 * i < no ? jac[(int64_t)(base + eo[i].slot) * ld + s] : 0.0;
+#pragma unroll
+        for (int i = 0; i < ABV_PER_LANE; ++i)
+            va[i] = lane + 32 * i < na ? jac[(int64_t)(base + ea[i].slot) * ld + s] : 0.0;
+    }
+    // scatter into the augmented block (row stride P, B_n from column NV)
+    template <class T, int P>
+    __device__ inline void scatter(T* A, int lane) const {
+#pragma unroll
+        for (int i = 0; i < OWN_PER_LANE; ++i)
+            if (lane + 32 * i < no) A[eo[i].r * P + eo[i].c] = (T)vo[i];
+#pragma unroll
+        for (int i = 0; i < ABV_PER_LANE; ++i)
+            if (lane + 32 * i < na) A[ea[i].r * P + NV + ea[i].c] = (T)va[i];
+    }
+};
+
 // assemble stage n's augmented block [A_n | B_n] of scenario s in shared memory (own
 // entries, the super-diagonal coupling B_n, the Schur update A_n -= C_n G_{n-1}) and
 // return the threshold below which a pivot marks the block singular
 template <class T>
 __device__ inline T assemble_stage(int n, int64_t ld, int s, int lane, const double* __restrict__ jac, double pivtol,
-                                   T (*A)[PADA], const T (*Gp)[NABV]) {
+                                   const LaneTables& lt, T (*A)[PADA], const T (*Gp)[NABV]) {
     const int t = stage_type(n);
     const int base = c_segJ[n];
+    StageLoads L;
+    L.fetch(lt, n, ld, s, lane, jac);
+    const int nq = n > 0 ? c_nblw[t] : 0;
+    const T cvq = load_coupling<T>(lt.blw[t], nq, base, jac, ld, s, lane);
     for (int e = lane; e < NV * NCA; e += 32) A[e / NCA][e % NCA] = T(0);
     __syncwarp();
-    for (int k = lane; k < c_nown[t]; k += 32) {
-        const Ent e = g_own[t][k];
-        A[e.r][e.c] = (T)jac[(int64_t)(base + e.slot) * ld + s];
-    }
-    if (n + 1 < N_STAGES) {
-        for (int k = lane; k < c_nabv[t]; k += 32) {
-            const Ent e = g_abv[t][k];
-            A[e.r][NV + e.c] = (T)jac[(int64_t)(base + e.slot) * ld + s];
-        }
-    }
+    L.scatter<T, PADA>(&A[0][0], lane);
     __syncwarp();
     // Schur update with the previous stage: A_n -= C_n G_{n-1}
-    if (n > 0) {
-        const int nq = c_nblw[t];
-        const T cvq = load_coupling<T>(g_blw[t], nq, base, jac, ld, s, lane);
-        for (int k = 0; k < nq; ++k) {
-            const Ent e = c_blw[t][k];
-            const T cv = shfl(cvq, k);
-            if (lane < NABV) A[e.r][abv_var(lane)] = fma_t(-cv, Gp[blw_var(e.c)][lane], A[e.r][abv_var(lane)]);
-            __syncwarp();
-        }
+    for (int k = 0; k < nq; ++k) {
+        const Ent e = lt.blw[t][k];
+        const T cv = shfl(cvq, k);
+        if (lane < NABV) A[e.r][abv_var(lane)] = fma_t(-cv, Gp[blw_var(e.c)][lane], A[e.r][abv_var(lane)]);
+        __syncwarp();
     }
     // largest entry of the block (for the singularity test)
     unsigned long long kmax = 0ull;
@@ -169,6 +224,8 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
                                                                  int* __restrict__ sing, double pivtol) {
     __shared__ T sA[WPB][NV][PADA];
     __shared__ T sG[WPB][NV][NABV];
+    __shared__ LaneTables lt;
+    stage_lane_tables(lt);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * WPB + warp;
     // whole warps leave together; no block-level barriers below
@@ -177,7 +234,7 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
     T(*Gp)[NABV] = sG[warp];
     int singular = 0;
     for (int n = 0; n < N_STAGES; ++n) {
-        const T tiny = assemble_stage<T>(n, ld, s, lane, jac, pivtol, A, Gp);
+        const T tiny = assemble_stage<T>(n, ld, s, lane, jac, pivtol, lt, A, Gp);
         const unsigned long long ktiny = abs_key(tiny);
         unsigned char* pv = piv + pv_off(s, n);
         // LU with partial pivoting, row operations on all 33 columns.  FP64: fully unrolled
@@ -186,11 +243,17 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
         constexpr int UNR = sizeof(T) == 8 ? NV : 1;
 #pragma unroll UNR
         for (int k = 0; k < NV; ++k) {
-            // key 0 marks lanes outside the candidate rows (an exact zero candidate also has
-            // key 0 and loses ties to lower rows: the singular test below catches it)
+            // key 0 marks lanes outside the candidate rows.  FP64: exact |value| keys, ties to
+            // the lowest row (an exact zero candidate also has key 0: the singular test below
+            // catches it); FP32: pivot_key32 (the same choice as factor_reg_kernel)
             const bool cand = lane >= k && lane < NV;
-            int p = warp_argmax_key(cand ? abs_key(A[lane][k]) : 0ull, cand);
-            if (p < 0 || p >= NV) p = k;
+            int p;
+            if constexpr (sizeof(T) == 4) {
+                p = key_position(__reduce_max_sync(0xffffffffu, cand ? pivot_key32(A[lane][k], lane) : 0u));
+            } else {
+                p = warp_argmax_key(cand ? abs_key(A[lane][k]) : 0ull, cand);
+                if (p < 0 || p >= NV) p = k;
+            }
             if (lane == 0) pv[k] = (unsigned char)p;
             if (p != k) {
                 for (int j = lane; j < NCA; j += 32) {
@@ -250,12 +313,14 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
 // FP32 variant with the block in registers: lane i < 22 keeps row i of [A_n | B_n] (33
 // values as 17 float pairs) for the whole elimination.  Rows are never moved: each lane
 // tracks the position its row holds in the row-swap sequence (LAPACK order, stored as
-// for factor_warp_kernel), the pivot search takes the largest |value| among the rows not
-// yet chosen and breaks ties by that position, the chosen row's remaining columns are
-// broadcast through shared memory, and the rank-1 update runs as paired FP32 FMAs.  G_n
+// for factor_warp_kernel); the pivot is one warp maximum of pivot_key32 over the rows not
+// yet chosen (position-tagged keys: no second search for ties); the chosen row tests its
+// pivot, forms the reciprocal and broadcasts its remaining columns through shared memory;
+// the rank-1 update runs as paired FP32 FMAs.  G_n
 // comes from a back substitution with the U rows in registers.  Every entry sees the same
 // operations in the same order as in factor_warp_kernel, so both give identical factors.
 constexpr int NPR = (NCA + 1) / 2;   // float pairs per augmented row (column 33: padding)
+constexpr int NBLWV = 6;             // unknowns of the stage below in a row's coupling (C_n)
 
 __device__ __forceinline__ float& rv(float2* r, int j) { return (j & 1) ? r[j >> 1].y : r[j >> 1].x; }
 
@@ -271,6 +336,8 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
     __shared__ __align__(16) float sG[WPB][NV * NABV + 2];
     __shared__ __align__(16) float sU[WPB][2 * NPR + 2];
     __shared__ unsigned char sQ[WPB][32];
+    __shared__ LaneTables lt;
+    stage_lane_tables(lt);
     const unsigned full = 0xffffffffu;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * WPB + warp;
@@ -284,35 +351,40 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
     for (int n = 0; n < N_STAGES; ++n) {
         const int t = stage_type(n);
         const int base = c_segJ[n];
-        // assemble: rows zeroed, the stage's entries scattered, rows to registers
+        // assemble: every Jacobian load of the lane first (its scatter entries and its row's
+        // entries of C_n), rows zeroed, entries scattered, rows to registers
+        StageLoads L;
+        L.fetch(lt, n, ld, s, lane, jac);
+        int q0 = 0, nb = 0;
+        if (n > 0 && rowlane) {
+            q0 = lt.blwRp[t][lane];
+            nb = lt.blwRp[t][lane + 1] - q0;
+        }
+        Ent eb[NBLWV];
+        double vb[NBLWV];
+#pragma unroll
+        for (int i = 0; i < NBLWV; ++i) {
+            eb[i] = lt.blw[t][i < nb ? q0 + i : 0];
+            vb[i] = i < nb ? jac[(int64_t)(base + eb[i].slot) * ld + s] : 0.0;
+        }
         if (rowlane) {
 #pragma unroll
             for (int m = 0; m < NPR; ++m) *reinterpret_cast<float2*>(&A[lane * PADA + 2 * m]) = make_float2(0.f, 0.f);
         }
         __syncwarp();
-        for (int k = lane; k < c_nown[t]; k += 32) {
-            const Ent e = g_own[t][k];
-            A[e.r * PADA + e.c] = (float)jac[(int64_t)(base + e.slot) * ld + s];
-        }
-        if (n + 1 < N_STAGES) {
-            for (int k = lane; k < c_nabv[t]; k += 32) {
-                const Ent e = g_abv[t][k];
-                A[e.r * PADA + NV + e.c] = (float)jac[(int64_t)(base + e.slot) * ld + s];
-            }
-        }
+        L.scatter<float, PADA>(A, lane);
         __syncwarp();
         float2 r2[NPR];
 #pragma unroll
         for (int m = 0; m < NPR; ++m)
             r2[m] = rowlane ? *reinterpret_cast<const float2*>(&A[lane * PADA + 2 * m]) : make_float2(0.f, 0.f);
         // Schur update with the previous stage, A_n -= C_n G_{n-1}: each row applies its own
-        // entries of C_n in table order
-        if (n > 0 && rowlane) {
-            const int q1 = g_blwRp[t][lane + 1];
-            for (int q = g_blwRp[t][lane]; q < q1; ++q) {
-                const Ent e = g_blw[t][q];
-                const float cv = (float)jac[(int64_t)(base + e.slot) * ld + s];
-                const float* gr = Gs + blw_var(e.c) * NABV;
+        // entries of C_n in table order (at most one per unknown of the stage below)
+#pragma unroll
+        for (int i = 0; i < NBLWV; ++i) {
+            if (i < nb) {
+                const float cv = (float)vb[i];
+                const float* gr = Gs + blw_var(eb[i].c) * NABV;
 #pragma unroll
                 for (int a = 0; a < NABV; ++a) rv(r2, abv_var(a)) = fmaf(-cv, gr[a], rv(r2, abv_var(a)));
             }
@@ -326,37 +398,35 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
         const unsigned ktiny = __float_as_uint(tiny) & 0x7fffffffu;
         int cur = lane;             // position of this lane's row in the swap sequence
         bool done = !rowlane;       // row already chosen (lanes >= 22 never take part)
-        int myq = 0;                // lane k: the lane whose row is chosen at step k
         unsigned char mypv = 0;     // lane k: the swap of step k
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            const unsigned key = done ? 0u : (__float_as_uint(rv(r2, k)) & 0x7fffffffu);
+            // one warp maximum picks the pivot (keys are unique: the position is part of them)
+            const unsigned key = done ? 0u : pivot_key32(rv(r2, k), cur);
             const unsigned mx = __reduce_max_sync(full, key);
-            const unsigned pos = __reduce_min_sync(full, (!done && key == mx) ? (unsigned)cur : 0xffu);
-            int p = __ffs((int)__ballot_sync(full, !done && (unsigned)cur == pos)) - 1;
-            p = p < 0 ? 0 : p;
-            if (lane == k) {
-                mypv = (unsigned char)pos;
-                myq = p;
-            }
-            if (cur == k) cur = (int)pos;
-            if (lane == p) {
+            const int pos = key_position(mx);
+            const bool isp = !done && key == mx;
+            if (lane == k) mypv = (unsigned char)pos;
+            if (cur == k) cur = pos;
+            if (isp) {
                 cur = k;
                 done = true;
-            }
-            float ukk = __shfl_sync(full, rv(r2, k), p);
-            if (!((__float_as_uint(ukk) & 0x7fffffffu) > ktiny) || ukk != ukk) {
-                singular = 1;
-                ukk = (ukk < 0.0f ? -1.0f : 1.0f) * (tiny > 0.0f ? tiny : 1.0f);
-            }
-            const float inv = recip(ukk);
-            if (lane == p) {
+                // the pivot row: singular test, reciprocal, its columns from k to shared memory
+                float ukk = rv(r2, k);
+                if (!((__float_as_uint(ukk) & 0x7fffffffu) > ktiny) || ukk != ukk) {
+                    singular = 1;
+                    ukk = (ukk < 0.0f ? -1.0f : 1.0f) * (tiny > 0.0f ? tiny : 1.0f);
+                }
+                const float inv = recip(ukk);
 #pragma unroll
                 for (int m = k / 2; m < NPR; ++m) *reinterpret_cast<float2*>(&U[2 * m]) = r2[m];
+                U[2 * NPR] = inv;
+                rv(r2, k) = inv;
+                sQ[warp][k] = (unsigned char)lane;
             }
             __syncwarp();
             if (!done) {
-                const float l = rv(r2, k) * inv;
+                const float l = rv(r2, k) * U[2 * NPR];
                 rv(r2, k) = l;
                 if ((k & 1) == 0) r2[k / 2].y = fmaf(-l, U[k + 1], r2[k / 2].y);
                 const float2 nl = make_float2(-l, -l);
@@ -365,10 +435,7 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
                     r2[m] = __ffma2_rn(nl, *reinterpret_cast<const float2*>(&U[2 * m]), r2[m]);
             }
             __syncwarp();
-            if (lane == p) rv(r2, k) = inv;
         }
-        if (rowlane) sQ[warp][lane] = (unsigned char)myq;
-        __syncwarp();
         // U G = L^-1 P B, positions from the bottom up: the row at position i scales its B
         // columns by 1 / U_ii (kept on its diagonal), the rows above subtract
         if (n + 1 < N_STAGES) {
@@ -413,6 +480,7 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
         }
         __syncwarp();
     }
+    singular = __any_sync(0xffffffffu, singular);
     if (lane == 0) sing[s] = singular;
 }
 
@@ -521,8 +589,8 @@ __global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, in
             // products of C_n's entries (entry q on lane q) with y_{n-1}, then added to
             // their rows in entry order
             const int nq = c_nblw[t];
-            const T cvq = load_coupling<T>(g_blw[t], nq, base, jac, ld, s, lane);
-            const int src = lane < nq ? blw_var(g_blw[t][lane].c) : 0;
+            const T cvq = load_coupling<T>(g_lt.blw[t], nq, base, jac, ld, s, lane);
+            const int src = lane < nq ? blw_var(g_lt.blw[t][lane].c) : 0;
 #pragma unroll
             for (int k = 0; k < NRHS; ++k) {
                 const T pq = cvq * shfl(y[k], src);
@@ -634,8 +702,8 @@ __global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t l
         if (n + 1 < N_STAGES) {
             const int ta = stage_type(n + 1), ba = c_segJ[n + 1];
             const int nq = c_nblw[ta];
-            const T cvq = load_coupling<T>(g_blw[ta], nq, ba, jac, ld, s, lane);
-            const T pq = cvq * shfl(v, lane < nq ? (int)g_blw[ta][lane].r : 0);
+            const T cvq = load_coupling<T>(g_lt.blw[ta], nq, ba, jac, ld, s, lane);
+            const T pq = cvq * shfl(v, lane < nq ? (int)g_lt.blw[ta][lane].r : 0);
             for (int q = 0; q < nq; ++q) {
                 const T pp = shfl(pq, q);
                 if (lane == blw_var(c_blw[ta][q].c)) rhs -= pp;
