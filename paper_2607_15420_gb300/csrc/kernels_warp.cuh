@@ -321,6 +321,7 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
 // operations in the same order as in factor_warp_kernel, so both give identical factors.
 constexpr int NPR = (NCA + 1) / 2;   // float pairs per augmented row (column 33: padding)
 constexpr int NBLWV = 6;             // unknowns of the stage below in a row's coupling (C_n)
+constexpr int PADQ = 36;             // assembly row stride (rows 16-byte aligned)
 
 __device__ __forceinline__ float& rv(float2* r, int j) { return (j & 1) ? r[j >> 1].y : r[j >> 1].x; }
 
@@ -330,12 +331,11 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
                                                               unsigned char* __restrict__ piv, float* __restrict__ G,
                                                               int* __restrict__ sing, double pivtol) {
     // per warp: the assembly block (reused as the row-major LU block on the way out), G_n
-    // by unknown (the next stage's Schur update reads it), the broadcast pivot row, and
-    // the row of each position
-    __shared__ __align__(16) float sA[WPB][NV * PADA];
+    // by unknown (the next stage's Schur update reads it), and the broadcast row
+    __shared__ __align__(16) float sA[WPB][NV * PADQ];
     __shared__ __align__(16) float sG[WPB][NV * NABV + 2];
     __shared__ __align__(16) float sU[WPB][2 * NPR + 2];
-    __shared__ unsigned char sQ[WPB][32];
+    __shared__ unsigned char sQ[WPB][32];   // the lane whose row holds each position
     __shared__ LaneTables lt;
     stage_lane_tables(lt);
     const unsigned full = 0xffffffffu;
@@ -369,15 +369,24 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
         }
         if (rowlane) {
 #pragma unroll
-            for (int m = 0; m < NPR; ++m) *reinterpret_cast<float2*>(&A[lane * PADA + 2 * m]) = make_float2(0.f, 0.f);
+            for (int q = 0; q < PADQ / 4; ++q) *reinterpret_cast<float4*>(&A[lane * PADQ + 4 * q]) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncwarp();
-        L.scatter<float, PADA>(A, lane);
+        L.scatter<float, PADQ>(A, lane);
         __syncwarp();
         float2 r2[NPR];
+        if (rowlane) {
 #pragma unroll
-        for (int m = 0; m < NPR; ++m)
-            r2[m] = rowlane ? *reinterpret_cast<const float2*>(&A[lane * PADA + 2 * m]) : make_float2(0.f, 0.f);
+            for (int q = 0; q < NPR / 2; ++q) {
+                const float4 a4 = *reinterpret_cast<const float4*>(&A[lane * PADQ + 4 * q]);
+                r2[2 * q] = make_float2(a4.x, a4.y);
+                r2[2 * q + 1] = make_float2(a4.z, a4.w);
+            }
+            r2[NPR - 1] = *reinterpret_cast<const float2*>(&A[lane * PADQ + 2 * (NPR - 1)]);
+        } else {
+#pragma unroll
+            for (int m = 0; m < NPR; ++m) r2[m] = make_float2(0.f, 0.f);
+        }
         // Schur update with the previous stage, A_n -= C_n G_{n-1}: each row applies its own
         // entries of C_n in table order (at most one per unknown of the stage below)
 #pragma unroll
@@ -419,7 +428,10 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
                 }
                 const float inv = recip(ukk);
 #pragma unroll
-                for (int m = k / 2; m < NPR; ++m) *reinterpret_cast<float2*>(&U[2 * m]) = r2[m];
+                for (int q = k / 4; q < NPR / 2; ++q)
+                    *reinterpret_cast<float4*>(&U[4 * q]) = make_float4(r2[2 * q].x, r2[2 * q].y, r2[2 * q + 1].x,
+                                                                        r2[2 * q + 1].y);
+                *reinterpret_cast<float2*>(&U[2 * (NPR - 1)]) = r2[NPR - 1];
                 U[2 * NPR] = inv;
                 rv(r2, k) = inv;
                 sQ[warp][k] = (unsigned char)lane;
@@ -431,8 +443,12 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
                 if ((k & 1) == 0) r2[k / 2].y = fmaf(-l, U[k + 1], r2[k / 2].y);
                 const float2 nl = make_float2(-l, -l);
 #pragma unroll
-                for (int m = k / 2 + 1; m < NPR; ++m)
-                    r2[m] = __ffma2_rn(nl, *reinterpret_cast<const float2*>(&U[2 * m]), r2[m]);
+                for (int q = (k / 2 + 1) / 2; q < NPR / 2; ++q) {
+                    const float4 u4 = *reinterpret_cast<const float4*>(&U[4 * q]);
+                    if (2 * q >= k / 2 + 1) r2[2 * q] = __ffma2_rn(nl, make_float2(u4.x, u4.y), r2[2 * q]);
+                    r2[2 * q + 1] = __ffma2_rn(nl, make_float2(u4.z, u4.w), r2[2 * q + 1]);
+                }
+                r2[NPR - 1] = __ffma2_rn(nl, *reinterpret_cast<const float2*>(&U[2 * (NPR - 1)]), r2[NPR - 1]);
             }
             __syncwarp();
         }

@@ -21,32 +21,34 @@ struct RedOps {
     int op[12];
 };
 
-// Kernels below with QS threads per (scenario, stage): thread q of a group handles the
-// stage's unknowns j = q, q + QS, ...; the QS threads are adjacent lanes, so their
-// partial values combine with xor shuffles (every lane of the group ends with the same
-// value, in a fixed order).  Four times the warps of one thread per (scenario, stage):
-// these kernels wait on global loads, and 5000 scenarios x 10 stages alone fill only a
-// quarter of the GPU's warp slots.
+// Kernels below with QS = 4 threads per (scenario, stage): a 128-thread block covers 32
+// scenarios, lane = scenario and warp q of the block handles the stage's unknowns
+// j = q, q + QS, ...  Every lane of a warp works on the same rows, so the sparse-product
+// loops have warp-uniform trip counts and table reads, and every load is coalesced over
+// 32 scenarios.  Four times the warps of one thread per (scenario, stage): these kernels
+// wait on global loads, and 5000 scenarios x 10 stages alone fill only a quarter of the
+// GPU's warp slots.  The QS partial values of a (scenario, stage) combine through shared
+// memory as (v0 op v1) op (v2 op v3).
 constexpr int QS = 4;
-constexpr int QS_SCEN = 128 / QS;   // scenarios per 128-thread block
+constexpr int QS_SCEN = 32;   // scenarios per 128-thread block
 
-__device__ inline double group_max(double a) {
+__device__ __forceinline__ double comb(int op, double a, double b) {
+    return op == RSUM ? a + b : (op == RMAX ? ((b > a || b != b) ? b : a) : fmin(a, b));
+}
+
+// combine v[0..NC) over the block's QS warps (ops[k]: RSUM, RMAX or RMIN); warp 0 ends
+// with the combined values.  Every thread of the block must call it.
+template <int K, int NC>
+__device__ __forceinline__ void group_combine(double (&v)[K], double (*sm)[NC][32], const int (&ops)[NC]) {
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-    for (int o = 1; o < QS; o <<= 1) {
-        const double b = __shfl_xor_sync(0xffffffffu, a, o);
-        a = (b > a || b != b) ? b : a;
+    for (int k = 0; k < NC; ++k) sm[q][k][lane] = v[k];
+    __syncthreads();
+    if (q == 0) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+            v[k] = comb(ops[k], comb(ops[k], sm[0][k][lane], sm[1][k][lane]), comb(ops[k], sm[2][k][lane], sm[3][k][lane]));
     }
-    return a;
-}
-__device__ inline double group_min(double a) {
-#pragma unroll
-    for (int o = 1; o < QS; o <<= 1) a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-    return a;
-}
-__device__ inline double group_sum(double a) {
-#pragma unroll
-    for (int o = 1; o < QS; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    return a;
 }
 
 // J^T lambda for the stage's unknowns and the optimality-error partials:
@@ -58,10 +60,11 @@ __global__ void __launch_bounds__(128) dual_kernel(const Params P, int S, int64_
                                                    const double* __restrict__ x, const double* __restrict__ zL,
                                                    const double* __restrict__ zU, double* __restrict__ jtl,
                                                    double* part) {
-    const int q = threadIdx.x % QS;
-    const int s = blockIdx.x * QS_SCEN + threadIdx.x / QS;
+    __shared__ double sm[QS][5][32];
+    const int q = threadIdx.x >> 5;
+    const int s = blockIdx.x * QS_SCEN + (threadIdx.x & 31);
     const int n = blockIdx.y;
-    const bool live = live_prob(b, s, S, PS_ACT) >= 0;   // the same for the whole group
+    const bool live = live_prob(b, s, S, PS_ACT) >= 0;
     double v[6] = {0.0, 0.0, 0.0, -INFINITY, INFINITY, 0.0};
     if (live) {
 #pragma unroll 1
@@ -87,11 +90,8 @@ __global__ void __launch_bounds__(128) dual_kernel(const Params P, int S, int64_
             }
         }
     }
-    v[0] = group_max(v[0]);
-    v[1] = group_sum(v[1]);
-    v[2] = group_sum(v[2]);
-    v[3] = group_max(v[3]);
-    v[4] = group_min(v[4]);
+    constexpr int ops[5] = {RMAX, RSUM, RSUM, RMAX, RMIN};
+    group_combine<6, 5>(v, sm, ops);
     if (!live || q != 0) return;
     v[5] = lam[(int64_t)(NR * n + R_H) * ld + s];
     store_partials<6>(v, part, ld, s, n);
@@ -137,8 +137,9 @@ __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BVi
                                                     const double* __restrict__ p, const double* __restrict__ q,
                                                     const double* __restrict__ r, const int* __restrict__ sing,
                                                     double* part) {
-    const int g = threadIdx.x % QS;
-    const int s = blockIdx.x * QS_SCEN + threadIdx.x / QS;
+    __shared__ double sm[QS][4][32];
+    const int g = threadIdx.x >> 5;
+    const int s = blockIdx.x * QS_SCEN + (threadIdx.x & 31);
     const int n = blockIdx.y;
     const bool live = live_prob(b, s, S, PS_ACT) >= 0;
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -156,8 +157,8 @@ __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BVi
             }
         }
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = group_sum(v[k]);
+    constexpr int ops[4] = {RSUM, RSUM, RSUM, RSUM};
+    group_combine<6, 4>(v, sm, ops);
     if (!live || g != 0) return;
     if (n == 0) {
         if (use_w) v[4] = hes[(int64_t)(NHS * N_STAGES) * ld + s];
@@ -168,13 +169,13 @@ __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BVi
 
 // dz = p - q dd ;  g = r - (W + Sigma + dw I) dz ;  dd, dw of the slot's problem.
 // QS threads per (scenario, stage); each writes its unknowns of dz, then (after the
-// group's writes) its entries of g, which read the whole stage's dz.
+// block's writes) its entries of g, which read the whole stage's dz.
 __global__ void __launch_bounds__(128) dz_kernel(int S, int64_t ld, const BView b, const double* __restrict__ hes,
                                                  const double* __restrict__ sig, bool use_w,
                                                  const double* __restrict__ p, const double* __restrict__ q,
                                                  const double* __restrict__ r, double* dz, double* __restrict__ g) {
-    const int gq = threadIdx.x % QS;
-    const int s = blockIdx.x * QS_SCEN + threadIdx.x / QS;
+    const int gq = threadIdx.x >> 5;
+    const int s = blockIdx.x * QS_SCEN + (threadIdx.x & 31);
     const int n = blockIdx.y;
     const int pr = live_prob(b, s, S, PS_ACT);
     const bool live = pr >= 0;
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(128) dz_kernel(int S, int64_t ld, const BView 
             dz[o] = p[o] - q[o] * dd;
         }
     }
-    __syncwarp();   // the group's dz entries are visible to its lanes below
+    __syncthreads();   // the block's dz entries are visible to all its threads below
     if (!live) return;
     const double dw = b.ps ? psv(b, PS_DW, pr) : 0.0;
     for (int j = gq; j < NV; j += QS) {
@@ -205,8 +206,9 @@ __global__ void __launch_bounds__(128) kkt_residual_kernel(int S, int64_t ld, co
                                                            const double* __restrict__ rz, const double* __restrict__ rc,
                                                            double* __restrict__ rhoz, double* __restrict__ rhoc,
                                                            double* part) {
-    const int gq = threadIdx.x % QS;
-    const int s = blockIdx.x * QS_SCEN + threadIdx.x / QS;
+    __shared__ double sm[QS][5][32];
+    const int gq = threadIdx.x >> 5;
+    const int s = blockIdx.x * QS_SCEN + (threadIdx.x & 31);
     const int n = blockIdx.y;
     const int pr = live_prob(b, s, S, PS_ACT);
     const bool live = pr >= 0;
@@ -227,10 +229,8 @@ __global__ void __launch_bounds__(128) kkt_residual_kernel(int S, int64_t ld, co
             if (a != a || c != c) v[0] = NAN;
         }
     }
-    v[0] = group_max(v[0]);
-    v[1] = group_max(v[1]);
-    v[3] = group_max(v[3]);
-    v[4] = group_max(v[4]);
+    constexpr int ops[5] = {RMAX, RMAX, RSUM, RMAX, RMAX};   // [2] is set below
+    group_combine<5, 5>(v, sm, ops);
     if (!live || gq != 0) return;
     v[2] = dl[(int64_t)(NR * n + R_H) * ld + s];
     store_partials<5>(v, part, ld, s, n);
