@@ -478,7 +478,7 @@ abs_status ensure_buffers(abs_problem* h) {
     CK(cudaMalloc(&h->hes, sizeof(double) * (size_t)h->nnzH * ld));
     CK(cudaMalloc(&h->vec, sizeof(double) * (size_t)vsize(h) * V_COUNT));
     CK(cudaMemset(h->vec, 0, sizeof(double) * (size_t)vsize(h) * V_COUNT));
-    CK(cudaMalloc(&h->piv, (size_t)N_STAGES * NV * ld));
+    CK(cudaMalloc(&h->piv, (size_t)N_STAGES * PIV_BYTES * ld));
     CK(cudaMalloc(&h->sing, sizeof(int) * (size_t)ld));
     CK(cudaMemset(h->sing, 0, sizeof(int) * (size_t)ld));
     CK(cudaMalloc(&h->part, sizeof(double) * (size_t)KMAX * N_STAGES * ld));
@@ -1409,7 +1409,7 @@ constexpr size_t NA_G = (size_t)N_STAGES * NV * NABV * NA_LD;
 constexpr size_t NA_VEC = (size_t)NSC * NA_LD + NA_LD;
 constexpr int NA_K = 6;                                     // Schur partial planes
 constexpr size_t NA_PART = (size_t)NA_K * N_STAGES * NA_LD;
-constexpr size_t NA_PIV = ((size_t)N_STAGES * NV * NA_LD + 7) / 8;   // bytes as doubles
+constexpr size_t NA_PIV = ((size_t)N_STAGES * PIV_BYTES * NA_LD + 7) / 8;   // bytes as doubles
 constexpr size_t NA_SING = (NA_LD + 1) / 2;                         // ints as doubles
 constexpr size_t NA_PS = PS_NFIELDS;                                // one problem's scalars
 constexpr size_t NA_TOTAL = NA_LU + NA_G + 3 * NA_VEC + NA_PART + NA_PIV + NA_SING + NA_PS;

@@ -1,15 +1,17 @@
 // kernels_warp.cuh -- warp-cooperative stage-block LU and block solves (A4, A6).
 //
-// One warp per scenario.  Each 22 x 22 stage block lives in shared memory while the
-// warp works on it: pivot search with rows on lanes, the trailing update with columns
-// on lanes (each lane keeps its pivot-row entry in a register and walks the rows), the
-// super-diagonal block B_n appended as 11 extra columns so that the elimination yields
-// L^-1 P B_n, then U G_n = L^-1 P B_n by backward substitution.  Vectors of the solves
-// live one entry per lane; broadcasts are warp shuffles.
+// One warp per scenario.  factor_warp_kernel keeps each 22 x 22 stage block in shared
+// memory while the warp works on it: pivot search with rows on lanes, the trailing
+// update with columns on lanes (each lane keeps its pivot-row entry in a register and
+// walks the rows), the super-diagonal block B_n appended as 11 extra columns so that the
+// elimination yields L^-1 P B_n, then U G_n = L^-1 P B_n by backward substitution.
+// factor_reg_kernel (FP32) keeps row i of the block in lane i's registers instead.
+// Vectors of the solves live one entry per lane; broadcasts are warp shuffles.
 //
 // Factor storage is per scenario and contiguous (internal layout, not part of the C
-// ABI): LU[s][n][22][22], G[s][n][22][11], piv[s][n][22], so every warp access to the
-// factors is coalesced.  The reciprocal of each pivot is kept on U's diagonal.
+// ABI): LU[s][n][22][22], G[s][n][22][11] and the row order piv[s][n][22][2] (see
+// PIV_BYTES), so every warp access to the factors is coalesced.  The reciprocal of each
+// pivot is kept on U's diagonal.
 #pragma once
 
 #include "kernels.cuh"
@@ -30,7 +32,10 @@ constexpr bool factor_fits() {
 
 __host__ __device__ constexpr int64_t lu_off(int64_t s, int n) { return (s * N_STAGES + n) * (int64_t)(NV * NV); }
 __host__ __device__ constexpr int64_t g_off(int64_t s, int n) { return (s * N_STAGES + n) * (int64_t)(NV * NABV); }
-__host__ __device__ constexpr int64_t pv_off(int64_t s, int n) { return (s * N_STAGES + n) * (int64_t)NV; }
+// row order of a factored stage block: (perm[i], ipos[i]) byte pairs for i < 22, perm[i]
+// the block row at position i of P A = L U and ipos[j] the position of block row j
+constexpr int PIV_BYTES = 2 * NV;
+__host__ __device__ constexpr int64_t pv_off(int64_t s, int n) { return (s * N_STAGES + n) * (int64_t)PIV_BYTES; }
 
 template <class T>
 __device__ inline T shfl(T v, int src) {
@@ -102,13 +107,14 @@ __device__ inline T load_coupling(const Ent* tab, int cnt, int base, const doubl
     return lane < cnt ? (T)jac[(int64_t)(base + tab[lane].slot) * ld + s] : T(0);
 }
 
-// a stage's LU block and pivots fetched into registers ahead of use (the next stage's
-// loads overlap the current stage's work), then committed to shared memory
+// a stage's LU block and row order fetched into registers ahead of use (the next
+// stage's loads overlap the current stage's work), then committed: the block to shared
+// memory, lane i's (perm[i], ipos[i]) to registers (lanes >= 22: i itself)
 constexpr int LU_PER_LANE = (NV * NV + 31) / 32;
 template <class T>
 struct LUPrefetch {
     T v[LU_PER_LANE];
-    unsigned char p;
+    uchar2 p;
     __device__ inline void fetch(const T* __restrict__ LU, const unsigned char* __restrict__ piv, int64_t s, int n,
                                  int lane) {
         const T* src = LU + lu_off(s, n);
@@ -117,15 +123,17 @@ struct LUPrefetch {
             const int e = lane + 32 * i;
             v[i] = e < NV * NV ? src[e] : T(0);
         }
-        p = lane < NV ? piv[pv_off(s, n) + lane] : (unsigned char)0;
+        p = lane < NV ? reinterpret_cast<const uchar2*>(piv + pv_off(s, n))[lane]
+                      : make_uchar2((unsigned char)lane, (unsigned char)lane);
     }
-    __device__ inline void commit(T (*A)[PADL], unsigned char* pv, int lane) const {
+    __device__ inline void commit(T (*A)[PADL], int& perm, int& ipos, int lane) const {
 #pragma unroll
         for (int i = 0; i < LU_PER_LANE; ++i) {
             const int e = lane + 32 * i;
             if (e < NV * NV) A[e / NV][e % NV] = v[i];
         }
-        if (lane < NV) pv[lane] = p;
+        perm = p.x;
+        ipos = p.y;
     }
 };
 
@@ -237,6 +245,7 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
         const T tiny = assemble_stage<T>(n, ld, s, lane, jac, pivtol, lt, A, Gp);
         const unsigned long long ktiny = abs_key(tiny);
         unsigned char* pv = piv + pv_off(s, n);
+        int orig = lane;   // block row now at position lane
         // LU with partial pivoting, row operations on all 33 columns.  FP64: fully unrolled
         // (static shared-memory offsets, independent row updates; measured 3 % faster);
         // FP32: rolled (the unrolled body's size costs more than it gains)
@@ -254,13 +263,15 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
                 p = warp_argmax_key(cand ? abs_key(A[lane][k]) : 0ull, cand);
                 if (p < 0 || p >= NV) p = k;
             }
-            if (lane == 0) pv[k] = (unsigned char)p;
             if (p != k) {
                 for (int j = lane; j < NCA; j += 32) {
                     const T a = A[k][j];
                     A[k][j] = A[p][j];
                     A[p][j] = a;
                 }
+                const int ok = __shfl_sync(0xffffffffu, orig, k), op = __shfl_sync(0xffffffffu, orig, p);
+                if (lane == k) orig = op;
+                if (lane == p) orig = ok;
             }
             __syncwarp();
             T ukk = A[k][k];
@@ -305,6 +316,10 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
         }
         T* Ln = LU + lu_off(s, n);
         for (int e = lane; e < NV * NV; e += 32) Ln[e] = A[e / NV][e % NV];
+        if (lane < NV) {
+            pv[2 * lane] = (unsigned char)orig;
+            pv[2 * orig + 1] = (unsigned char)lane;
+        }
         __syncwarp();
     }
     if (lane == 0) sing[s] = singular;
@@ -407,7 +422,6 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
         const unsigned ktiny = __float_as_uint(tiny) & 0x7fffffffu;
         int cur = lane;             // position of this lane's row in the swap sequence
         bool done = !rowlane;       // row already chosen (lanes >= 22 never take part)
-        unsigned char mypv = 0;     // lane k: the swap of step k
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             // one warp maximum picks the pivot (keys are unique: the position is part of them)
@@ -415,7 +429,6 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
             const unsigned mx = __reduce_max_sync(full, key);
             const int pos = key_position(mx);
             const bool isp = !done && key == mx;
-            if (lane == k) mypv = (unsigned char)pos;
             if (cur == k) cur = pos;
             if (isp) {
                 cur = k;
@@ -485,7 +498,8 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
 #pragma unroll
                 for (int a = 0; a < NABV; ++a) Gs[cur * NABV + a] = rv(r2, NV + a);
             }
-            piv[pv_off(s, n) + lane] = mypv;
+            piv[pv_off(s, n) + 2 * cur] = (unsigned char)lane;
+            piv[pv_off(s, n) + 2 * lane + 1] = (unsigned char)cur;
         }
         __syncwarp();
         float4* Ln = reinterpret_cast<float4*>(LU + lu_off(s, n));
@@ -507,24 +521,17 @@ __device__ inline void stage_lu(const T* __restrict__ src, T (*dst)[PADL], int l
     __syncwarp();
 }
 
-// w <- At^-1 w, lane i holding w_i (lanes >= 22 carry zeros)
+// w <- At^-1 w, lane i holding w_i (lanes >= 22 carry zeros): P w in one shuffle, then
+// L forward and U backward (unrolled: the loads of A run ahead of the shuffle chain)
 template <class T>
-__device__ inline T lu_apply_warp(const T (*A)[PADL], const unsigned char* pv, int lane, T w) {
-#pragma unroll 1
-    for (int k = 0; k < NV; ++k) {
-        const int p = pv[k];
-        if (p != k) {
-            const T wk = shfl(w, k), wp = shfl(w, p);
-            if (lane == k) w = wp;
-            if (lane == p) w = wk;
-        }
-    }
-#pragma unroll 1
+__device__ inline T lu_apply_warp(const T (*A)[PADL], int perm, int lane, T w) {
+    w = shfl(w, perm);
+#pragma unroll
     for (int k = 0; k < NV - 1; ++k) {
         const T wk = shfl(w, k);
         if (lane > k && lane < NV) w -= A[lane][k] * wk;
     }
-#pragma unroll 1
+#pragma unroll
     for (int k = NV - 1; k >= 0; --k) {
         if (lane == k) w *= A[k][k];
         const T wk = shfl(w, k);
@@ -533,30 +540,21 @@ __device__ inline T lu_apply_warp(const T (*A)[PADL], const unsigned char* pv, i
     return w;
 }
 
-// w <- At^-T w:  U^T forward, L^T backward, then the row swaps in reverse
+// w <- At^-T w:  U^T forward, L^T backward, then P^T w in one shuffle
 template <class T>
-__device__ inline T lu_apply_t_warp(const T (*A)[PADL], const unsigned char* pv, int lane, T w) {
-#pragma unroll 1
+__device__ inline T lu_apply_t_warp(const T (*A)[PADL], int ipos, int lane, T w) {
+#pragma unroll
     for (int k = 0; k < NV; ++k) {
         if (lane == k) w *= A[k][k];
         const T wk = shfl(w, k);
         if (lane > k && lane < NV) w -= A[k][lane] * wk;
     }
-#pragma unroll 1
+#pragma unroll
     for (int k = NV - 1; k > 0; --k) {
         const T wk = shfl(w, k);
         if (lane < k) w -= A[k][lane] * wk;
     }
-#pragma unroll 1
-    for (int k = NV - 1; k >= 0; --k) {
-        const int p = pv[k];
-        if (p != k) {
-            const T wk = shfl(w, k), wp = shfl(w, p);
-            if (lane == k) w = wp;
-            if (lane == p) w = wk;
-        }
-    }
-    return w;
+    return shfl(w, ipos);
 }
 
 // J_s x = r (NRHS right-hand sides; a null r[k] means b = dc/dd), one warp per scenario
@@ -568,13 +566,12 @@ __global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, in
                                                                 const double* r0, const double* r1, double* o0,
                                                                 double* o1) {
     __shared__ T sL[WPB][NV][PADL];
-    __shared__ unsigned char sP[WPB][NV + 2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * WPB + warp;
     const int pr = live_prob(b, s, S, PS_ACT);
     if (pr < 0) return;
     T(*A)[PADL] = sL[warp];
-    unsigned char* pv = sP[warp];
+    int perm = lane, ipos = lane;
     const double* rr[2] = {r0, r1};
     double* oo[2] = {o0, o1};
     const T bval = (T)(-P.u_max * M_PI * 0.5 * x[(int64_t)NSC * ld + pr]);   // b = dc/dd of the problem
@@ -591,7 +588,7 @@ __global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, in
     for (int n = 0; n < N_STAGES; ++n) {
         const int t = stage_type(n);
         const int base = c_segJ[n];
-        pre.commit(A, pv, lane);
+        pre.commit(A, perm, ipos, lane);
         T w[NRHS];
 #pragma unroll
         for (int k = 0; k < NRHS; ++k) w[k] = rr[k] ? rnext[k] : ((lane == R_H) ? bval : T(0));
@@ -619,7 +616,7 @@ __global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, in
         __syncwarp();
 #pragma unroll
         for (int k = 0; k < NRHS; ++k) {
-            y[k] = lu_apply_warp<T>(A, pv, lane, w[k]);
+            y[k] = lu_apply_warp<T>(A, perm, lane, w[k]);
             if (row) oo[k][(int64_t)(NV * n + lane) * ld + s] = (double)y[k];
         }
         __syncwarp();
@@ -675,12 +672,11 @@ __global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t l
                                                                 const T* __restrict__ G,
                                                                 const double* __restrict__ g, double* out) {
     __shared__ T sL[WPB][NV][PADL];
-    __shared__ unsigned char sP[WPB][NV + 2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * WPB + warp;
     if (live_prob(b, s, S, PS_ACT) < 0) return;
     T(*A)[PADL] = sL[warp];
-    unsigned char* pv = sP[warp];
+    int perm = lane, ipos = lane;
     const bool row = lane < NV;
     const int my_abv = abv_index(lane);   // lane j takes the product of column abv_index(j)
     // forward sweep with the G blocks (fetched one stage ahead); w_n kept in out
@@ -712,7 +708,7 @@ __global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t l
     pre.fetch(LU, piv, s, N_STAGES - 1, lane);
     T v = T(0);
     for (int n = N_STAGES - 1; n >= 0; --n) {
-        pre.commit(A, pv, lane);
+        pre.commit(A, perm, ipos, lane);
         T rhs = row ? (T)out[(int64_t)(NV * n + lane) * ld + s] : T(0);
         if (n > 0) pre.fetch(LU, piv, s, n - 1, lane);
         if (n + 1 < N_STAGES) {
@@ -726,7 +722,7 @@ __global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t l
             }
         }
         __syncwarp();
-        v = lu_apply_t_warp<T>(A, pv, lane, rhs);
+        v = lu_apply_t_warp<T>(A, ipos, lane, rhs);
         if (row) out[(int64_t)(NR * n + lane) * ld + s] = (double)v;
         __syncwarp();
     }
