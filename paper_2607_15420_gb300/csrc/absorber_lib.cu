@@ -238,6 +238,14 @@ bool build_pattern(PatternTables& T, std::string& err) {
                 err = "coupling row with more than 6 entries";
                 return false;
             }
+        for (int j = 0; j < NBLW; ++j) {
+            int cnt = 0;
+            for (int q = 0; q < T.nblw[t]; ++q) cnt += T.blw[t][q].c == j;
+            if (cnt > 8) {   // the transposed block solve sums at most 8 entries per unknown
+                err = "coupling column with more than 8 entries";
+                return false;
+            }
+        }
         bydest(T.own[t], T.nown[t], 0, T.ownC[t], T.ownCp[t]);
         bydest(T.abv[t], T.nabv[t], 1, T.abvC[t], T.abvCp[t]);
         bydest(T.blw[t], T.nblw[t], 2, T.blwC[t], T.blwCp[t]);
@@ -313,8 +321,16 @@ cudaError_t upload_tables(int dev) {
         std::memcpy(lt.own, T.own, sizeof(lt.own));
         std::memcpy(lt.abv, T.abv, sizeof(lt.abv));
         std::memcpy(lt.blw, T.blw, sizeof(lt.blw));
-        for (int t = 0; t < 3; ++t)
+        for (int t = 0; t < 3; ++t) {
             for (int r = 0; r <= NV; ++r) lt.blwRp[t][r] = T.blwRp[t][r];
+            int m = 0;
+            for (int j = 0; j < NV; ++j) {
+                lt.blwCp[t][j] = (short)m;
+                for (int q = 0; q < T.nblw[t]; ++q)
+                    if (blw_var(T.blw[t][q].c) == j) lt.blwQ[t][m++] = (unsigned char)q;
+            }
+            lt.blwCp[t][NV] = (short)m;
+        }
         UP(g_lt, lt);
     }
 #undef UP
@@ -393,7 +409,7 @@ struct abs_problem {
     int graphs = 1;                  // replay captured launch sequences (options.graphs)
     struct GraphEntry {
         const void* ptr[9];
-        int prec, use_w, tiles[4];
+        int prec, use_w, have_p, tiles[4];
         int runs;                    // eager runs so far (capture happens on the second)
         cudaGraphExec_t exec;
         int64_t nkern;
@@ -595,6 +611,9 @@ struct KKTSys {
     const double* sig;
     bool use_w;
     int prec;
+    // set before kkt_factor_core: p = J^-1 rc is solved together with q = J^-1 b (one
+    // two-right-hand-side launch) and the first KKT solve with this rc reuses it
+    const double* pre_rc = nullptr;
     std::vector<double> Kdd, A0, Q2, Sd, dw, rd, wdd, d;   // per problem (host)
     std::vector<int> nsing;
 };
@@ -742,6 +761,13 @@ abs_status solve_j(abs_problem* h, int prec, const double* jac, const double* x,
     return solve_launch<double, 1>(h, jac, x, r0, nullptr, o0, nullptr, st);
 }
 
+// two right-hand sides in one launch (a null r means b = dc/dd)
+abs_status solve_j2(abs_problem* h, int prec, const double* jac, const double* x, const double* r0, const double* r1,
+                    double* o0, double* o1, cudaStream_t st) {
+    if (prec == ABS_PREC_FP32) return solve_launch<float, 2>(h, jac, x, r0, r1, o0, o1, st);
+    return solve_launch<double, 2>(h, jac, x, r0, r1, o0, o1, st);
+}
+
 template <class T, int W>
 void solve_t_w(abs_problem* h, const double* jac, const double* g, double* out, cudaStream_t st) {
     solve_t_warp_kernel<T, W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (const T*)h->LU, h->piv,
@@ -782,7 +808,9 @@ abs_status kkt_factor_core(abs_problem* h, KKTSys& K, const double* x, cudaStrea
     if (K.prec == ABS_PREC_FP32) r = factor_launch<float>(h, K.jac, pivtol, st);
     else r = factor_launch<double>(h, K.jac, pivtol, st);
     if (r != ABS_OK) return r;
-    if ((r = solve_j(h, K.prec, K.jac, x, nullptr, V(h, V_Q), st)) != ABS_OK) return r;
+    r = K.pre_rc ? solve_j2(h, K.prec, K.jac, x, K.pre_rc, nullptr, V(h, V_P), V(h, V_Q), st)
+                 : solve_j(h, K.prec, K.jac, x, nullptr, V(h, V_Q), st);
+    if (r != ABS_OK) return r;
     schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, nullptr, V(h, V_Q),
                                              nullptr, h->sing, h->part);
     if ((r = launch_check(h)) != ABS_OK) return r;
@@ -804,11 +832,12 @@ abs_status kkt_factor_core(abs_problem* h, KKTSys& K, const double* x, cudaStrea
 double schur_value(const KKTSys& K, int p, double dw) { return K.Kdd[p] + dw + K.A0[p] + dw * K.Q2[p]; }
 
 // one Schur-reduced solve for every active problem: rz (z part), rc -> dz (d slots set),
-// dl.  PS_RD, PS_SD, PS_DW must be on the device.  No host round trip.
+// dl.  PS_RD, PS_SD, PS_DW must be on the device.  No host round trip.  have_p: V_P
+// already holds J^-1 rc (solved with q in kkt_factor_core).
 abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, const double* rz, const double* rc,
-                              double* dz, double* dl, cudaStream_t st) {
+                              double* dz, double* dl, cudaStream_t st, bool have_p = false) {
     abs_status r;
-    if ((r = solve_j(h, K.prec, K.jac, x, rc, V(h, V_P), st)) != ABS_OK) return r;
+    if (!have_p && (r = solve_j(h, K.prec, K.jac, x, rc, V(h, V_P), st)) != ABS_OK) return r;
     schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q),
                                              rz, nullptr, h->part);
     if ((r = launch_check(h)) != ABS_OK) return r;
@@ -826,14 +855,14 @@ abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, 
 // with a given set of vectors and replayed from then on; the per-problem scalars it
 // depends on are read from device memory at replay time
 abs_status kkt_solve_once(abs_problem* h, const KKTSys& K, const double* x, const double* rz, const double* rc,
-                          double* dz, double* dl, cudaStream_t st) {
+                          double* dz, double* dl, cudaStream_t st, bool have_p = false) {
     if (!h->graphs || h->prof.on || !h->stream || st != h->stream)
-        return kkt_solve_launches(h, K, x, rz, rc, dz, dl, st);
+        return kkt_solve_launches(h, K, x, rz, rc, dz, dl, st, have_p);
     const void* key[9] = {K.jac, K.hes, K.sig, x, rz, rc, dz, dl, h->LU};
     abs_problem::GraphEntry* ge = nullptr;
     for (auto& g : h->gcache)
         if (std::memcmp(g.ptr, key, sizeof(key)) == 0 && g.prec == K.prec && g.use_w == (int)K.use_w &&
-            std::memcmp(g.tiles, h->tile, sizeof(g.tiles)) == 0) {
+            g.have_p == (int)have_p && std::memcmp(g.tiles, h->tile, sizeof(g.tiles)) == 0) {
             ge = &g;
             break;
         }
@@ -842,20 +871,21 @@ abs_status kkt_solve_once(abs_problem* h, const KKTSys& K, const double* x, cons
         std::memcpy(g.ptr, key, sizeof(key));
         g.prec = K.prec;
         g.use_w = (int)K.use_w;
+        g.have_p = (int)have_p;
         std::memcpy(g.tiles, h->tile, sizeof(g.tiles));
         h->gcache.push_back(g);
         ge = &h->gcache.back();
     }
     if (!ge->exec && ge->runs < 1) {   // first use: eager (tunes the tile shapes if needed)
         ge->runs++;
-        abs_status r = kkt_solve_launches(h, K, x, rz, rc, dz, dl, st);
+        abs_status r = kkt_solve_launches(h, K, x, rz, rc, dz, dl, st, have_p);
         std::memcpy(ge->tiles, h->tile, sizeof(ge->tiles));
         return r;
     }
     if (!ge->exec) {
         const int64_t n0 = h->nlaunch;
         CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        abs_status r = kkt_solve_launches(h, K, x, rz, rc, dz, dl, st);
+        abs_status r = kkt_solve_launches(h, K, x, rz, rc, dz, dl, st, have_p);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(st, &graph);
         if (r != ABS_OK) {
@@ -884,7 +914,7 @@ abs_status kkt_solve_refined(abs_problem* h, KKTSys& K, const double* x, const d
                              double* dz, double* dl, int max_refine, double tol, int* steps,
                              std::vector<double>* resid, cudaStream_t st) {
     abs_status r;
-    if ((r = kkt_solve_once(h, K, x, rz, rc, dz, dl, st)) != ABS_OK) return r;
+    if ((r = kkt_solve_once(h, K, x, rz, rc, dz, dl, st, K.pre_rc == rc)) != ABS_OK) return r;
     int k = 0;
     const int NP = h->NP;
     if (resid) resid->assign(NP, 0.0);

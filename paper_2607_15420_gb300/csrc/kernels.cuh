@@ -45,7 +45,9 @@ struct __align__(16) LaneTables {
     Ent own[3][MAXOWN];
     Ent abv[3][MAXABV];
     Ent blw[3][MAXBLW];
-    short blwRp[3][NV + 2];   // row pointers of blw (NV + 1 used; padded to 16 bytes)
+    short blwRp[3][NV + 2];        // row pointers of blw (NV + 1 used; padded to 16 bytes)
+    short blwCp[3][NV + 2];        // pointers into blwQ by the stage-below unknown fed
+    unsigned char blwQ[3][MAXBLW]; // blw entry indices grouped by that unknown (table order)
 };
 static_assert(sizeof(LaneTables) % 16 == 0, "LaneTables is copied as 16-byte words");
 __device__ LaneTables g_lt;

@@ -557,6 +557,32 @@ __device__ inline T lu_apply_t_warp(const T (*A)[PADL], int ipos, int lane, T w)
     return shfl(w, ipos);
 }
 
+// the coupling of stage n to the stage below (C_n: entry q on lane q), fetched a stage
+// ahead of use: the entry's Jacobian value (kept in double until used, so that the load
+// does not stall the fetch), the stage-below unknown it multiplies (row solves) or its
+// row (transposed solves), and lane j's group of entries -- those of row j (row solves)
+// or those feeding stage-below unknown j (transposed solves), in table order
+constexpr int NBLWC = 8;   // entries feeding one stage-below unknown, at most
+struct CouplingFetch {
+    double cv;
+    int src, q0, nb;
+    unsigned char qi[NBLWC];   // transposed solves: the group's entry indices
+    template <bool TRANS>
+    __device__ inline void fetch(int n, int64_t ld, int s, int lane, const double* __restrict__ jac) {
+        const int t = stage_type(n), base = c_segJ[n], nq = c_nblw[t];
+        const Ent e = g_lt.blw[t][lane < nq ? lane : 0];
+        cv = lane < nq ? jac[(int64_t)(base + e.slot) * ld + s] : 0.0;
+        src = lane < nq ? (TRANS ? (int)e.r : blw_var(e.c)) : 0;
+        const short* ptr = TRANS ? g_lt.blwCp[t] : g_lt.blwRp[t];
+        q0 = lane < NV ? ptr[lane] : 0;
+        nb = lane < NV ? ptr[lane + 1] - q0 : 0;
+        if (TRANS) {
+#pragma unroll
+            for (int i = 0; i < NBLWC; ++i) qi[i] = g_lt.blwQ[t][i < nb ? q0 + i : 0];
+        }
+    }
+};
+
 // J_s x = r (NRHS right-hand sides; a null r[k] means b = dc/dd), one warp per scenario
 template <class T, int NRHS, int WPB = WPB_S>
 __global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, int S, int64_t ld, const BView b,
@@ -581,35 +607,36 @@ __global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, in
     for (int k = 0; k < NRHS; ++k) y[k] = T(0);
     LUPrefetch<T> pre;
     pre.fetch(LU, piv, s, 0, lane);
-    T rnext[NRHS];
+    double rnext[NRHS];
 #pragma unroll
-    for (int k = 0; k < NRHS; ++k) rnext[k] = (rr[k] && row) ? (T)rr[k][(int64_t)lane * ld + s] : T(0);
+    for (int k = 0; k < NRHS; ++k) rnext[k] = (rr[k] && row) ? rr[k][(int64_t)lane * ld + s] : 0.0;
+    CouplingFetch cnext;
+    cnext.fetch<false>(1, ld, s, lane, jac);
     // forward: w_n = r_n - C_n y_{n-1},  y_n = At_n^-1 w_n
     for (int n = 0; n < N_STAGES; ++n) {
-        const int t = stage_type(n);
-        const int base = c_segJ[n];
         pre.commit(A, perm, ipos, lane);
+        const CouplingFetch cc = cnext;
         T w[NRHS];
 #pragma unroll
-        for (int k = 0; k < NRHS; ++k) w[k] = rr[k] ? rnext[k] : ((lane == R_H) ? bval : T(0));
+        for (int k = 0; k < NRHS; ++k) w[k] = rr[k] ? (T)rnext[k] : ((lane == R_H) ? bval : T(0));
         if (n + 1 < N_STAGES) {
             pre.fetch(LU, piv, s, n + 1, lane);
 #pragma unroll
             for (int k = 0; k < NRHS; ++k)
-                rnext[k] = (rr[k] && row) ? (T)rr[k][(int64_t)(NR * (n + 1) + lane) * ld + s] : T(0);
+                rnext[k] = (rr[k] && row) ? rr[k][(int64_t)(NR * (n + 1) + lane) * ld + s] : 0.0;
+            cnext.fetch<false>(n + 1, ld, s, lane, jac);
         }
         if (n > 0) {
-            // products of C_n's entries (entry q on lane q) with y_{n-1}, then added to
-            // their rows in entry order
-            const int nq = c_nblw[t];
-            const T cvq = load_coupling<T>(g_lt.blw[t], nq, base, jac, ld, s, lane);
-            const int src = lane < nq ? blw_var(g_lt.blw[t][lane].c) : 0;
+            // products of C_n's entries (entry q on lane q) with y_{n-1}, then subtracted in
+            // each row in entry order
+            const T cv = (T)cc.cv;
 #pragma unroll
             for (int k = 0; k < NRHS; ++k) {
-                const T pq = cvq * shfl(y[k], src);
-                for (int q = 0; q < nq; ++q) {
-                    const T pp = shfl(pq, q);
-                    if (lane == c_blw[t][q].r) w[k] -= pp;
+                const T pq = cv * shfl(y[k], cc.src);
+#pragma unroll
+                for (int i = 0; i < NBLWV; ++i) {
+                    const T pp = shfl(pq, (cc.q0 + i) & 31);
+                    if (i < cc.nb) w[k] -= pp;
                 }
             }
         }
@@ -706,19 +733,27 @@ __global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t l
     // backward sweep: one transposed block solve per stage
     LUPrefetch<T> pre;
     pre.fetch(LU, piv, s, N_STAGES - 1, lane);
+    double rnext = row ? out[(int64_t)(NV * (N_STAGES - 1) + lane) * ld + s] : 0.0;
+    CouplingFetch cnext;
+    cnext.fetch<true>(N_STAGES - 1, ld, s, lane, jac);
     T v = T(0);
     for (int n = N_STAGES - 1; n >= 0; --n) {
         pre.commit(A, perm, ipos, lane);
-        T rhs = row ? (T)out[(int64_t)(NV * n + lane) * ld + s] : T(0);
-        if (n > 0) pre.fetch(LU, piv, s, n - 1, lane);
+        T rhs = (T)rnext;
+        const CouplingFetch cc = cnext;
+        if (n > 0) {
+            pre.fetch(LU, piv, s, n - 1, lane);
+            rnext = row ? out[(int64_t)(NV * (n - 1) + lane) * ld + s] : 0.0;
+            cnext.fetch<true>(n, ld, s, lane, jac);
+        }
         if (n + 1 < N_STAGES) {
-            const int ta = stage_type(n + 1), ba = c_segJ[n + 1];
-            const int nq = c_nblw[ta];
-            const T cvq = load_coupling<T>(g_lt.blw[ta], nq, ba, jac, ld, s, lane);
-            const T pq = cvq * shfl(v, lane < nq ? (int)g_lt.blw[ta][lane].r : 0);
-            for (int q = 0; q < nq; ++q) {
-                const T pp = shfl(pq, q);
-                if (lane == blw_var(c_blw[ta][q].c)) rhs -= pp;
+            // C_{n+1}^T v_{n+1}: entry q's product (lane q) subtracted from the stage-n
+            // unknown it multiplies, each unknown's entries in table order
+            const T pq = (T)cc.cv * shfl(v, cc.src);
+#pragma unroll
+            for (int i = 0; i < NBLWC; ++i) {
+                const T pp = shfl(pq, cc.qi[i]);
+                if (i < cc.nb) rhs -= pp;
             }
         }
         __syncwarp();
