@@ -812,7 +812,7 @@ abs_status kkt_factor_core(abs_problem* h, KKTSys& K, const double* x, cudaStrea
                  : solve_j(h, K.prec, K.jac, x, nullptr, V(h, V_Q), st);
     if (r != ABS_OK) return r;
     schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, nullptr, V(h, V_Q),
-                                             nullptr, h->sing, h->part);
+                                             nullptr, h->sing, h->part, SCHUR_DD);
     if ((r = launch_check(h)) != ABS_OK) return r;
     if ((r = reduce(h, st, 6, make_ops({RSUM, RSUM, RSUM, RSUM, RSUM, RSUM}), PS_ACT, true)) != ABS_OK) return r;
     const int NP = h->NP;
@@ -839,7 +839,7 @@ abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, 
     abs_status r;
     if (!have_p && (r = solve_j(h, K.prec, K.jac, x, rc, V(h, V_P), st)) != ABS_OK) return r;
     schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q),
-                                             rz, nullptr, h->part);
+                                             rz, nullptr, h->part, SCHUR_RHS);
     if ((r = launch_check(h)) != ABS_OK) return r;
     if ((r = reduce(h, st, 4, make_ops({RSUM, RSUM, RSUM, RSUM}), PS_ACT, false)) != ABS_OK) return r;
     finalize_dd_kernel<<<(unsigned)((h->NP + 127) / 128), 128, 0, st>>>(h->ld, view(h), h->red, dz);
@@ -1516,7 +1516,8 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
     solve_warp_kernel<double, 2><<<gs, 32 * WPB_S, 0, st>>>(P, (int)S, ld, bv, jac_vals, LU, piv, G, x, rhs_c, nullptr,
                                                             pv, qv);
     NA_LAUNCHED();
-    schur_kernel<<<gq, kThr, 0, st>>>((int)S, ld, bv, hess_vals, sigma, true, pv, qv, rhs_x, sing, part);
+    schur_kernel<<<gq, kThr, 0, st>>>((int)S, ld, bv, hess_vals, sigma, true, pv, qv, rhs_x, sing, part,
+                                      SCHUR_DD | SCHUR_RHS);
     NA_LAUNCHED();
     double hx[3] = {0.0, 0.0, 0.0};
     const int64_t plane = (int64_t)N_STAGES * ld;

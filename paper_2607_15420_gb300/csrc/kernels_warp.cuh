@@ -425,8 +425,16 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             // one warp maximum picks the pivot (keys are unique: the position is part of them)
-            const unsigned key = done ? 0u : pivot_key32(rv(r2, k), cur);
+            const float xk = rv(r2, k);
+            const unsigned key = done ? 0u : pivot_key32(xk, cur);
             const unsigned mx = __reduce_max_sync(full, key);
+            // every lane forms the reciprocal of its candidate while the maximum is found
+            // (off the step's dependency chain); operands outside [2^-60, 2^60] are replaced
+            // so that no lane takes the division's slow path, and the pivot row recomputes
+            // in that case
+            const float ax = fabsf(xk);
+            const bool easy = ax > 0x1p-60f && ax < 0x1p60f;
+            const float sinv = recip(easy ? xk : 1.0f);
             const int pos = key_position(mx);
             const bool isp = !done && key == mx;
             if (cur == k) cur = pos;
@@ -434,12 +442,15 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
                 cur = k;
                 done = true;
                 // the pivot row: singular test, reciprocal, its columns from k to shared memory
-                float ukk = rv(r2, k);
+                float ukk = xk;
+                float inv = sinv;
                 if (!((__float_as_uint(ukk) & 0x7fffffffu) > ktiny) || ukk != ukk) {
                     singular = 1;
                     ukk = (ukk < 0.0f ? -1.0f : 1.0f) * (tiny > 0.0f ? tiny : 1.0f);
+                    inv = recip(ukk);
+                } else if (!easy) {
+                    inv = recip(ukk);
                 }
-                const float inv = recip(ukk);
 #pragma unroll
                 for (int q = k / 4; q < NPR / 2; ++q)
                     *reinterpret_cast<float4*>(&U[4 * q]) = make_float4(r2[2 * q].x, r2[2 * q].y, r2[2 * q + 1].x,

@@ -129,14 +129,16 @@ __global__ void __launch_bounds__(128) rhs_kernel(const Params P, int S, int64_t
     }
 }
 
-// Schur partial sums with H = W + Sigma (W optional): [0] q^T H q, [1] q^T q,
-// [2] q^T (r - H p), [3] q^T p, [4] the scenario's d-d Hessian entry, [5] singular flag.
+// Schur partial sums with H = W + Sigma (W optional): with SCHUR_DD [0] q^T H q,
+// [1] q^T q; with SCHUR_RHS [2] q^T (r - H p), [3] q^T p; always [4] the scenario's d-d
+// Hessian entry and [5] the singular flag.  Terms not asked for are 0.
+enum { SCHUR_DD = 1, SCHUR_RHS = 2 };
 // QS threads per (scenario, stage).
 __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BView b, const double* __restrict__ hes,
                                                     const double* __restrict__ sig, bool use_w,
                                                     const double* __restrict__ p, const double* __restrict__ q,
                                                     const double* __restrict__ r, const int* __restrict__ sing,
-                                                    double* part) {
+                                                    double* part, int terms) {
     __shared__ double sm[QS][4][32];
     const int g = threadIdx.x >> 5;
     const int s = blockIdx.x * QS_SCEN + (threadIdx.x & 31);
@@ -150,10 +152,14 @@ __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BVi
             if (j < NV) {
                 const int64_t o = (int64_t)(NV * n + j) * ld + s;
                 const double qj = q[o];
-                v[0] += qj * hv_one(ld, hes, sig, 0.0, use_w, q, s, n, j);
-                v[1] += qj * qj;
-                if (r) v[2] += qj * (r[o] - (p ? hv_one(ld, hes, sig, 0.0, use_w, p, s, n, j) : 0.0));
-                if (p) v[3] += qj * p[o];
+                if (terms & SCHUR_DD) {
+                    v[0] += qj * hv_one(ld, hes, sig, 0.0, use_w, q, s, n, j);
+                    v[1] += qj * qj;
+                }
+                if (terms & SCHUR_RHS) {
+                    if (r) v[2] += qj * (r[o] - (p ? hv_one(ld, hes, sig, 0.0, use_w, p, s, n, j) : 0.0));
+                    if (p) v[3] += qj * p[o];
+                }
             }
         }
     }
