@@ -949,9 +949,7 @@ abs_status kkt_solve_refined(abs_problem* h, KKTSys& K, const double* x, const d
         for (int p = 0; p < NP; ++p) PSV(h, PS_RD, p) = rhod[p];
         if ((r = upload_ps(h, st)) != ABS_OK) return r;
         if ((r = kkt_solve_once(h, K, x, V(h, V_RHOZ), V(h, V_RHOC), V(h, V_CZ), V(h, V_CL), st)) != ABS_OK) return r;
-        axpy_d_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), V(h, V_CZ), dz, true);
-        if ((r = launch_check(h)) != ABS_OK) return r;
-        axpy_d_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), V(h, V_CL), dl, false);
+        axpy2_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), V(h, V_CZ), dz, V(h, V_CL), dl);
         if ((r = launch_check(h)) != ABS_OK) return r;
         ++k;
     }

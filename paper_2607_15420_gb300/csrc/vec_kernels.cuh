@@ -494,18 +494,19 @@ __global__ void axpby_kernel(int S, int64_t ld, const BView b, int flag, int afi
     }
 }
 
-// y += x on the per-scenario part and, with d_slots, on the problems' d slots
-__global__ void axpy_d_kernel(int S, int64_t ld, const BView b, const double* __restrict__ xv,
-                              double* __restrict__ y, bool d_slots) {
+// y1 += x1 (per-scenario part and the problems' d slots) and y2 += x2 (per-scenario part)
+__global__ void axpy2_kernel(int S, int64_t ld, const BView b, const double* __restrict__ x1,
+                             double* __restrict__ y1, const double* __restrict__ x2, double* __restrict__ y2) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
-    if (d_slots && n == 0 && s < b.NP && (!b.ps || psv(b, PS_ACT, s) != 0.0))
-        y[(int64_t)NSC * ld + s] += xv[(int64_t)NSC * ld + s];
+    if (n == 0 && s < b.NP && (!b.ps || psv(b, PS_ACT, s) != 0.0))
+        y1[(int64_t)NSC * ld + s] += x1[(int64_t)NSC * ld + s];
     if (live_prob(b, s, S, PS_ACT) < 0) return;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const int64_t o = (int64_t)(NV * n + j) * ld + s;
-        y[o] += xv[o];
+        y1[o] += x1[o];
+        y2[o] += x2[o];
     }
 }
 
@@ -526,7 +527,7 @@ __global__ void max_abs_kernel(int S, int64_t ld, const BView b, const double* _
 // chunk c covers elements [i0, i1) of problem p (element i: stage i / S_p, slot off_p +
 // i % S_p); one block per chunk, fixed-order tree; out[k * nchunk + c]
 constexpr int RED_T = 128;                  // threads per chunk block
-constexpr int RED_PER = 4;                  // elements per thread and plane
+constexpr int RED_PER = 2;                  // elements per thread and plane
 constexpr int RED_CHUNK = RED_T * RED_PER;  // elements per chunk
 constexpr int RED_KMAX = 12;
 
@@ -539,7 +540,7 @@ __device__ inline double warp_red(int op, double a) {
 }
 
 // One block per chunk of a problem's (stage, slot) elements: every plane k < K reduced in
-// a fixed order (4 elements per thread, xor trees within warps, warps in order) into
+// a fixed order (RED_PER elements per thread, xor trees within warps, warps in order) into
 // cout[k][c].  The problem's chunk block that finishes last (a per-problem arrival
 // counter; no block waits for another) then combines the problem's chunk results, chunk c
 // on lane (c - c0) % 32 in increasing c, then an xor tree, into out[k][p] and re-arms the
