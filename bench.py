@@ -311,8 +311,8 @@ def main():
                     help="profiling case: only N interior-point iterations of the workload from the inlet "
                          "start (no expected-value solve), then exit without a JSON line")
     ap.add_argument("--factor-tile", type=int, default=0,
-                    help="fixed FP32 factor launch shape (1/2/4/8 shared-memory kernel, 17/18/20/24 register "
-                         "kernel; 0: autotuned) -- for profiling one variant")
+                    help="fixed FP32 factor launch shape (1/2/4/8 warps per block; 0: autotuned) -- for "
+                         "profiling one shape")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     global FACTOR_TILE

@@ -262,10 +262,8 @@ typedef struct abs_options {
                               CUDA graph on the engine's stream at its second use with a
                               given set of vectors and replayed from then on */
     int32_t factor_tile;   /* FP32 factor launches only: 0 shape from autotune; 1, 2, 4, 8:
-                              the shared-memory kernel with that many warps per block;
-                              17, 18, 20, 24: the register-resident kernel with 1, 2, 4, 8
-                              warps per block (identical results); other values are
-                              rejected with ABS_ERR_ARG */
+                              that many warps (scenarios) per block (identical results);
+                              other values are rejected with ABS_ERR_ARG */
 } abs_options;
 
 void abs_default_options(abs_options* o);

@@ -685,16 +685,14 @@ abs_status tuned_launch(abs_problem* h, int kind, int es, std::initializer_list<
     return launch(w);
 }
 
-// factor launch shape: W warps per block; for FP32, W + FACTOR_REG selects the
-// register-resident variant (same arithmetic in the same order)
-constexpr int FACTOR_REG = 16;
-
-template <class T, int W, bool REG>
+// factor launch shape: W warps per block.  FP32: stage-block inverses and G by
+// Gauss-Jordan (factor_gj_kernel); FP64: LU factors, row order and G (factor_warp_kernel)
+template <class T, int W>
 void factor_w(abs_problem* h, const double* jac, double pivtol, cudaStream_t st) {
-    if constexpr (REG && std::is_same<T, float>::value)
-        factor_reg_kernel<W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (float*)h->LU, h->piv,
-                                                             (float*)h->G, h->sing, pivtol);
-    else if constexpr (!REG && factor_fits<T, W>())
+    if constexpr (std::is_same<T, float>::value)
+        factor_gj_kernel<W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (float*)h->LU, h->piv,
+                                                            (float*)h->G, h->sing, pivtol);
+    else if constexpr (factor_fits<T, W>())
         factor_warp_kernel<T, W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (T*)h->LU, h->piv,
                                                                 (T*)h->G, h->sing, pivtol);
 }
@@ -704,14 +702,10 @@ abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaS
     prof_begin(h, K_FACTOR, st);
     auto go = [&](int w) {
         switch (w) {
-            case 1: factor_w<T, 1, false>(h, jac, pivtol, st); break;
-            case 2: factor_w<T, 2, false>(h, jac, pivtol, st); break;
-            case 8: factor_w<T, 8, false>(h, jac, pivtol, st); break;
-            case FACTOR_REG + 1: factor_w<T, 1, true>(h, jac, pivtol, st); break;
-            case FACTOR_REG + 2: factor_w<T, 2, true>(h, jac, pivtol, st); break;
-            case FACTOR_REG + 4: factor_w<T, 4, true>(h, jac, pivtol, st); break;
-            case FACTOR_REG + 8: factor_w<T, 8, true>(h, jac, pivtol, st); break;
-            default: factor_w<T, 4, false>(h, jac, pivtol, st); break;
+            case 1: factor_w<T, 1>(h, jac, pivtol, st); break;
+            case 2: factor_w<T, 2>(h, jac, pivtol, st); break;
+            case 8: factor_w<T, 8>(h, jac, pivtol, st); break;
+            default: factor_w<T, 4>(h, jac, pivtol, st); break;
         }
         return launch_check(h);
     };
@@ -720,8 +714,7 @@ abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaS
         h->tile[TK_FACTOR] = h->factor_tile;
         r = go(h->factor_tile);
     } else if (std::is_same<T, float>::value)
-        r = tuned_launch(h, TK_FACTOR, sizeof(T),
-                         {1, 2, 4, 8, FACTOR_REG + 1, FACTOR_REG + 2, FACTOR_REG + 4, FACTOR_REG + 8}, WPB_F, go, st);
+        r = tuned_launch(h, TK_FACTOR, sizeof(T), {1, 2, 4, 8}, WPB_F, go, st);
     else
         r = factor_fits<T, 8>() ? tuned_launch(h, TK_FACTOR, sizeof(T), {1, 2, 4, 8}, WPB_F, go, st)
                                 : tuned_launch(h, TK_FACTOR, sizeof(T), {1, 2, 4}, WPB_F, go, st);
@@ -732,7 +725,7 @@ abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaS
 template <class T, int NR_, int W>
 void solve_w(abs_problem* h, const double* jac, const double* x, const double* r0, const double* r1, double* o0,
              double* o1, cudaStream_t st) {
-    solve_warp_kernel<T, NR_, W><<<gridw(h, W), 32 * W, 0, st>>>(h->P, (int)h->S, h->ld, view(h), jac,
+    solve_warp_kernel<T, NR_, W, std::is_same<T, float>::value><<<gridw(h, W), 32 * W, 0, st>>>(h->P, (int)h->S, h->ld, view(h), jac,
                                                                   (const T*)h->LU, h->piv, (const T*)h->G, x, r0, r1,
                                                                   o0, o1);
 }
@@ -770,7 +763,7 @@ abs_status solve_j2(abs_problem* h, int prec, const double* jac, const double* x
 
 template <class T, int W>
 void solve_t_w(abs_problem* h, const double* jac, const double* g, double* out, cudaStream_t st) {
-    solve_t_warp_kernel<T, W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (const T*)h->LU, h->piv,
+    solve_t_warp_kernel<T, W, std::is_same<T, float>::value><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (const T*)h->LU, h->piv,
                                                                (const T*)h->G, g, out);
 }
 

@@ -325,32 +325,35 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
     if (lane == 0) sing[s] = singular;
 }
 
-// FP32 variant with the block in registers: lane i < 22 keeps row i of [A_n | B_n] (33
-// values as 17 float pairs) for the whole elimination.  Rows are never moved: each lane
-// tracks the position its row holds in the row-swap sequence (LAPACK order, stored as
-// for factor_warp_kernel); the pivot is one warp maximum of pivot_key32 over the rows not
-// yet chosen (position-tagged keys: no second search for ties); the chosen row tests its
-// pivot, forms the reciprocal and broadcasts its remaining columns through shared memory;
-// the rank-1 update runs as paired FP32 FMAs.  G_n
-// comes from a back substitution with the U rows in registers.  Every entry sees the same
-// operations in the same order as in factor_warp_kernel, so both give identical factors.
-constexpr int NPR = (NCA + 1) / 2;   // float pairs per augmented row (column 33: padding)
+// FP32 stage-block inverses (the FP32 path's factorization): Gauss-Jordan elimination
+// in place, with partial pivoting, on [A_n | B_n] with rows in registers.  Lane i < 22
+// keeps row i (17 float pairs) for the whole elimination; rows are never moved, each lane
+// tracks the position its row takes.  Step k exchanges unknown k with the equation of the
+// pivot row p (one warp maximum of pivot_key32 over the rows not yet chosen: ties go to
+// the lowest position): with inv = 1 / a_pk, the pivot row becomes u_j = -a_pj inv
+// (j != k), u_k = inv, and every other row i becomes a_ij + a_ik u_j (j != k),
+// a_ik inv (j = k).  After the 22 exchanges the row at position i expresses unknown i:
+// its first 22 entries are row i of A_n^-1 with columns in position order (column c: the
+// equation of the row at position c) and its last 11 are row i of -G_n.  The block solves
+// take the row order (perm, ipos as for the LU factors) to match the columns.
+constexpr int NPR = (NCA + 1) / 2;   // float pairs of [A_n | B_n] per row (column 33: padding)
 constexpr int NBLWV = 6;             // unknowns of the stage below in a row's coupling (C_n)
 constexpr int PADQ = 36;             // assembly row stride (rows 16-byte aligned)
+constexpr int UINV = 36;             // broadcast buffer: the pivot's reciprocal
 
 __device__ __forceinline__ float& rv(float2* r, int j) { return (j & 1) ? r[j >> 1].y : r[j >> 1].x; }
 
+// (W <= 4: at least 24 resident warps per SM, 85 registers per thread at most)
 template <int WPB = WPB_F>
-__global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld, const BView b,
-                                                              const double* __restrict__ jac, float* __restrict__ LU,
-                                                              unsigned char* __restrict__ piv, float* __restrict__ G,
-                                                              int* __restrict__ sing, double pivtol) {
-    // per warp: the assembly block (reused as the row-major LU block on the way out), G_n
+__global__ void __launch_bounds__(32 * WPB, WPB >= 8 ? 3 : 24 / WPB) factor_gj_kernel(int S, int64_t ld, const BView b,
+                                                             const double* __restrict__ jac, float* __restrict__ AI,
+                                                             unsigned char* __restrict__ piv, float* __restrict__ G,
+                                                             int* __restrict__ sing, double pivtol) {
+    // per warp: the assembly block (reused as the row-major inverse on the way out), G_n
     // by unknown (the next stage's Schur update reads it), and the broadcast row
     __shared__ __align__(16) float sA[WPB][NV * PADQ];
     __shared__ __align__(16) float sG[WPB][NV * NABV + 2];
-    __shared__ __align__(16) float sU[WPB][2 * NPR + 2];
-    __shared__ unsigned char sQ[WPB][32];   // the lane whose row holds each position
+    __shared__ __align__(16) float sU[WPB][40];
     __shared__ LaneTables lt;
     stage_lane_tables(lt);
     const unsigned full = 0xffffffffu;
@@ -420,11 +423,10 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
         km = __reduce_max_sync(full, km);
         const float tiny = (float)pivtol * __uint_as_float(km);
         const unsigned ktiny = __float_as_uint(tiny) & 0x7fffffffu;
-        int cur = lane;             // position of this lane's row in the swap sequence
+        int cur = lane;             // position of this lane's row
         bool done = !rowlane;       // row already chosen (lanes >= 22 never take part)
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            // one warp maximum picks the pivot (keys are unique: the position is part of them)
             const float xk = rv(r2, k);
             const unsigned key = done ? 0u : pivot_key32(xk, cur);
             const unsigned mx = __reduce_max_sync(full, key);
@@ -441,7 +443,8 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
             if (isp) {
                 cur = k;
                 done = true;
-                // the pivot row: singular test, reciprocal, its columns from k to shared memory
+                // the pivot row: singular test, reciprocal, u_j = -a_pj inv, u_k = inv, to
+                // shared memory
                 float ukk = xk;
                 float inv = sinv;
                 if (!((__float_as_uint(ukk) & 0x7fffffffu) > ktiny) || ukk != ukk) {
@@ -451,69 +454,45 @@ __global__ void __launch_bounds__(32 * WPB) factor_reg_kernel(int S, int64_t ld,
                 } else if (!easy) {
                     inv = recip(ukk);
                 }
+                const float2 niv = make_float2(-inv, -inv);
 #pragma unroll
-                for (int q = k / 4; q < NPR / 2; ++q)
+                for (int m = 0; m < NPR; ++m) r2[m] = __fmul2_rn(r2[m], niv);
+                rv(r2, k) = inv;
+#pragma unroll
+                for (int q = 0; q < NPR / 2; ++q)
                     *reinterpret_cast<float4*>(&U[4 * q]) = make_float4(r2[2 * q].x, r2[2 * q].y, r2[2 * q + 1].x,
                                                                         r2[2 * q + 1].y);
                 *reinterpret_cast<float2*>(&U[2 * (NPR - 1)]) = r2[NPR - 1];
-                U[2 * NPR] = inv;
-                rv(r2, k) = inv;
-                sQ[warp][k] = (unsigned char)lane;
             }
             __syncwarp();
-            if (!done) {
-                const float l = rv(r2, k) * U[2 * NPR];
-                rv(r2, k) = l;
-                if ((k & 1) == 0) r2[k / 2].y = fmaf(-l, U[k + 1], r2[k / 2].y);
-                const float2 nl = make_float2(-l, -l);
+            if (rowlane && !isp) {
+                const float f = rv(r2, k);
+                const float2 nf = make_float2(f, f);
 #pragma unroll
-                for (int q = (k / 2 + 1) / 2; q < NPR / 2; ++q) {
+                for (int q = 0; q < NPR / 2; ++q) {
                     const float4 u4 = *reinterpret_cast<const float4*>(&U[4 * q]);
-                    if (2 * q >= k / 2 + 1) r2[2 * q] = __ffma2_rn(nl, make_float2(u4.x, u4.y), r2[2 * q]);
-                    r2[2 * q + 1] = __ffma2_rn(nl, make_float2(u4.z, u4.w), r2[2 * q + 1]);
+                    r2[2 * q] = __ffma2_rn(nf, make_float2(u4.x, u4.y), r2[2 * q]);
+                    r2[2 * q + 1] = __ffma2_rn(nf, make_float2(u4.z, u4.w), r2[2 * q + 1]);
                 }
-                r2[NPR - 1] = __ffma2_rn(nl, *reinterpret_cast<const float2*>(&U[2 * (NPR - 1)]), r2[NPR - 1]);
+                r2[NPR - 1] = __ffma2_rn(nf, *reinterpret_cast<const float2*>(&U[2 * (NPR - 1)]), r2[NPR - 1]);
+                rv(r2, k) = f * U[k];   // U[k] holds inv
             }
             __syncwarp();
         }
-        // U G = L^-1 P B, positions from the bottom up: the row at position i scales its B
-        // columns by 1 / U_ii (kept on its diagonal), the rows above subtract
-        if (n + 1 < N_STAGES) {
-#pragma unroll
-            for (int i = NV - 1; i >= 0; --i) {
-                const int q = sQ[warp][i];
-                if (lane == q) {
-                    const float d = rv(r2, i);
-#pragma unroll
-                    for (int m = NV / 2; m < NPR; ++m) r2[m] = __fmul2_rn(r2[m], make_float2(d, d));
-                }
-                float2 g2[NPR - NV / 2];
-#pragma unroll
-                for (int m = 0; m < NPR - NV / 2; ++m) {
-                    g2[m].x = __shfl_sync(full, r2[NV / 2 + m].x, q);
-                    g2[m].y = (2 * m + 1 < NABV) ? __shfl_sync(full, r2[NV / 2 + m].y, q) : 0.0f;
-                }
-                if (cur < i) {
-                    const float nu = -rv(r2, i);
-                    const float2 nu2 = make_float2(nu, nu);
-#pragma unroll
-                    for (int m = 0; m < NPR - NV / 2; ++m) r2[NV / 2 + m] = __ffma2_rn(nu2, g2[m], r2[NV / 2 + m]);
-                }
-            }
-        }
-        // rows to shared memory at their positions, then coalesced stores
+        // rows to shared memory at their positions (G_n = -(the B part)), row order, then
+        // coalesced stores
         if (rowlane) {
 #pragma unroll
             for (int m = 0; m < NV / 2; ++m) *reinterpret_cast<float2*>(&A[cur * NV + 2 * m]) = r2[m];
             if (n + 1 < N_STAGES) {
 #pragma unroll
-                for (int a = 0; a < NABV; ++a) Gs[cur * NABV + a] = rv(r2, NV + a);
+                for (int a = 0; a < NABV; ++a) Gs[cur * NABV + a] = -rv(r2, NV + a);
             }
             piv[pv_off(s, n) + 2 * cur] = (unsigned char)lane;
             piv[pv_off(s, n) + 2 * lane + 1] = (unsigned char)cur;
         }
         __syncwarp();
-        float4* Ln = reinterpret_cast<float4*>(LU + lu_off(s, n));
+        float4* Ln = reinterpret_cast<float4*>(AI + lu_off(s, n));
         for (int e = lane; e < NV * NV / 4; e += 32) Ln[e] = reinterpret_cast<const float4*>(A)[e];
         if (n + 1 < N_STAGES) {
             float2* Gn = reinterpret_cast<float2*>(G + g_off(s, n));
@@ -568,6 +547,59 @@ __device__ inline T lu_apply_t_warp(const T (*A)[PADL], int ipos, int lane, T w)
     return shfl(w, ipos);
 }
 
+// FP32 path (factor_gj_kernel): lane i's row i of the stage-block inverse, fetched a
+// stage ahead; the block solve y = A_n^-1 w is y_i = sum_j a_ij w_j (two interleaved
+// accumulations: even and odd j)
+// FP32 path (factor_gj_kernel): lane i's row i of the stage-block inverse M (columns in
+// position order) and its row-order pair, fetched a stage ahead.  The block solve
+// y = A_n^-1 w is y_i = sum_c M_ic w_perm[c] (two interleaved accumulations: even and odd c)
+constexpr int NPI = NV / 2;
+struct InvRowFetch {
+    float2 a[NPI];
+    uchar2 p;
+    __device__ inline void fetch(const float* __restrict__ AI, const unsigned char* __restrict__ piv, int64_t s,
+                                 int n, int lane) {
+        const float2* src = reinterpret_cast<const float2*>(AI + lu_off(s, n) + (lane < NV ? lane : 0) * NV);
+#pragma unroll
+        for (int m = 0; m < NPI; ++m) a[m] = lane < NV ? src[m] : make_float2(0.f, 0.f);
+        p = lane < NV ? reinterpret_cast<const uchar2*>(piv + pv_off(s, n))[lane]
+                      : make_uchar2((unsigned char)lane, (unsigned char)lane);
+    }
+    __device__ inline float apply(float w) const {
+        w = shfl(w, (int)p.x);
+        float e = 0.f, o = 0.f;
+#pragma unroll
+        for (int m = 0; m < NPI; ++m) {
+            e = fmaf(a[m].x, shfl(w, 2 * m), e);
+            o = fmaf(a[m].y, shfl(w, 2 * m + 1), o);
+        }
+        return e + o;
+    }
+};
+// ... and lane c's column c, for the transposed block solve: u_c = sum_i M_ic w_i, then
+// v_j = u_ipos[j]
+struct InvColFetch {
+    float c[NV];
+    uchar2 p;
+    __device__ inline void fetch(const float* __restrict__ AI, const unsigned char* __restrict__ piv, int64_t s,
+                                 int n, int lane) {
+        const float* src = AI + lu_off(s, n) + (lane < NV ? lane : 0);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) c[i] = lane < NV ? src[i * NV] : 0.f;
+        p = lane < NV ? reinterpret_cast<const uchar2*>(piv + pv_off(s, n))[lane]
+                      : make_uchar2((unsigned char)lane, (unsigned char)lane);
+    }
+    __device__ inline float apply(float w) const {
+        float e = 0.f, o = 0.f;
+#pragma unroll
+        for (int i = 0; i < NV; i += 2) {
+            e = fmaf(c[i], shfl(w, i), e);
+            o = fmaf(c[i + 1], shfl(w, i + 1), o);
+        }
+        return shfl(e + o, (int)p.y);
+    }
+};
+
 // the coupling of stage n to the stage below (C_n: entry q on lane q), fetched a stage
 // ahead of use: the entry's Jacobian value (kept in double until used, so that the load
 // does not stall the fetch), the stage-below unknown it multiplies (row solves) or its
@@ -594,20 +626,23 @@ struct CouplingFetch {
     }
 };
 
-// J_s x = r (NRHS right-hand sides; a null r[k] means b = dc/dd), one warp per scenario
-template <class T, int NRHS, int WPB = WPB_S>
+// J_s x = r (NRHS right-hand sides; a null r[k] means b = dc/dd), one warp per scenario.
+// INV (FP32 only): LU holds the stage-block inverses of factor_gj_kernel and each block
+// solve is a matrix-vector product; otherwise LU factors and row order.
+template <class T, int NRHS, int WPB = WPB_S, bool INV = false>
 __global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, int S, int64_t ld, const BView b,
                                                                 const double* __restrict__ jac, const T* __restrict__ LU,
                                                                 const unsigned char* __restrict__ piv,
                                                                 const T* __restrict__ G, const double* x,
                                                                 const double* r0, const double* r1, double* o0,
                                                                 double* o1) {
-    __shared__ T sL[WPB][NV][PADL];
+    static_assert(!INV || sizeof(T) == 4, "stage-block inverses are FP32");
+    __shared__ T sL[INV ? 1 : WPB][NV][PADL];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * WPB + warp;
     const int pr = live_prob(b, s, S, PS_ACT);
     if (pr < 0) return;
-    T(*A)[PADL] = sL[warp];
+    T(*A)[PADL] = sL[INV ? 0 : warp];
     int perm = lane, ipos = lane;
     const double* rr[2] = {r0, r1};
     double* oo[2] = {o0, o1};
@@ -617,7 +652,9 @@ __global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, in
 #pragma unroll
     for (int k = 0; k < NRHS; ++k) y[k] = T(0);
     LUPrefetch<T> pre;
-    pre.fetch(LU, piv, s, 0, lane);
+    InvRowFetch ipre;
+    if constexpr (INV) ipre.fetch((const float*)LU, piv, s, 0, lane);
+    else pre.fetch(LU, piv, s, 0, lane);
     double rnext[NRHS];
 #pragma unroll
     for (int k = 0; k < NRHS; ++k) rnext[k] = (rr[k] && row) ? rr[k][(int64_t)lane * ld + s] : 0.0;
@@ -625,13 +662,16 @@ __global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, in
     cnext.fetch<false>(1, ld, s, lane, jac);
     // forward: w_n = r_n - C_n y_{n-1},  y_n = At_n^-1 w_n
     for (int n = 0; n < N_STAGES; ++n) {
-        pre.commit(A, perm, ipos, lane);
+        InvRowFetch icur;
+        if constexpr (INV) icur = ipre;
+        else pre.commit(A, perm, ipos, lane);
         const CouplingFetch cc = cnext;
         T w[NRHS];
 #pragma unroll
         for (int k = 0; k < NRHS; ++k) w[k] = rr[k] ? (T)rnext[k] : ((lane == R_H) ? bval : T(0));
         if (n + 1 < N_STAGES) {
-            pre.fetch(LU, piv, s, n + 1, lane);
+            if constexpr (INV) ipre.fetch((const float*)LU, piv, s, n + 1, lane);
+            else pre.fetch(LU, piv, s, n + 1, lane);
 #pragma unroll
             for (int k = 0; k < NRHS; ++k)
                 rnext[k] = (rr[k] && row) ? rr[k][(int64_t)(NR * (n + 1) + lane) * ld + s] : 0.0;
@@ -654,7 +694,8 @@ __global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, in
         __syncwarp();
 #pragma unroll
         for (int k = 0; k < NRHS; ++k) {
-            y[k] = lu_apply_warp<T>(A, perm, lane, w[k]);
+            if constexpr (INV) y[k] = icur.apply(w[k]);
+            else y[k] = lu_apply_warp<T>(A, perm, lane, w[k]);
             if (row) oo[k][(int64_t)(NV * n + lane) * ld + s] = (double)y[k];
         }
         __syncwarp();
@@ -702,18 +743,20 @@ __host__ __device__ constexpr int abv_index(int j) { return j < 9 ? j : (j == LL
 //             that stage n reads: products with the stored G blocks, no block solve)
 //   backward  v_9 = At_9^-T w_9,  v_n = At_n^-T (w_n - C_{n+1}^T v_{n+1})
 // one transposed block solve per stage.
-template <class T, int WPB = WPB_S>
+// INV (FP32 only): LU holds the stage-block inverses (see solve_warp_kernel).
+template <class T, int WPB = WPB_S, bool INV = false>
 __global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t ld, const BView b,
                                                                 const double* __restrict__ jac,
                                                                 const T* __restrict__ LU,
                                                                 const unsigned char* __restrict__ piv,
                                                                 const T* __restrict__ G,
                                                                 const double* __restrict__ g, double* out) {
-    __shared__ T sL[WPB][NV][PADL];
+    static_assert(!INV || sizeof(T) == 4, "stage-block inverses are FP32");
+    __shared__ T sL[INV ? 1 : WPB][NV][PADL];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * WPB + warp;
     if (live_prob(b, s, S, PS_ACT) < 0) return;
-    T(*A)[PADL] = sL[warp];
+    T(*A)[PADL] = sL[INV ? 0 : warp];
     int perm = lane, ipos = lane;
     const bool row = lane < NV;
     const int my_abv = abv_index(lane);   // lane j takes the product of column abv_index(j)
@@ -743,17 +786,22 @@ __global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t l
     }
     // backward sweep: one transposed block solve per stage
     LUPrefetch<T> pre;
-    pre.fetch(LU, piv, s, N_STAGES - 1, lane);
+    InvColFetch ipre;
+    if constexpr (INV) ipre.fetch((const float*)LU, piv, s, N_STAGES - 1, lane);
+    else pre.fetch(LU, piv, s, N_STAGES - 1, lane);
     double rnext = row ? out[(int64_t)(NV * (N_STAGES - 1) + lane) * ld + s] : 0.0;
     CouplingFetch cnext;
     cnext.fetch<true>(N_STAGES - 1, ld, s, lane, jac);
     T v = T(0);
     for (int n = N_STAGES - 1; n >= 0; --n) {
-        pre.commit(A, perm, ipos, lane);
+        InvColFetch icur;
+        if constexpr (INV) icur = ipre;
+        else pre.commit(A, perm, ipos, lane);
         T rhs = (T)rnext;
         const CouplingFetch cc = cnext;
         if (n > 0) {
-            pre.fetch(LU, piv, s, n - 1, lane);
+            if constexpr (INV) ipre.fetch((const float*)LU, piv, s, n - 1, lane);
+            else pre.fetch(LU, piv, s, n - 1, lane);
             rnext = row ? out[(int64_t)(NV * (n - 1) + lane) * ld + s] : 0.0;
             cnext.fetch<true>(n, ld, s, lane, jac);
         }
@@ -768,7 +816,8 @@ __global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t l
             }
         }
         __syncwarp();
-        v = lu_apply_t_warp<T>(A, ipos, lane, rhs);
+        if constexpr (INV) v = icur.apply(rhs);
+        else v = lu_apply_t_warp<T>(A, ipos, lane, rhs);
         if (row) out[(int64_t)(NR * n + lane) * ld + s] = (double)v;
         __syncwarp();
     }
