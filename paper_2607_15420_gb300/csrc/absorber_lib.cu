@@ -916,9 +916,11 @@ abs_status kkt_solve_refined(abs_problem* h, KKTSys& K, const double* x, const d
         return ABS_OK;
     }
     std::vector<double> rhod(NP, 0.0);
+    // V_G holds r - H dz of the last block-elimination solve; dlast its dl
+    const double* dlast = dl;
     for (;;) {
-        kkt_residual_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.jac, K.hes, K.sig, K.use_w, dz,
-                                                        dl, rz, rc, V(h, V_RHOZ), V(h, V_RHOC), h->part);
+        kkt_residual_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.jac, V(h, V_G), dlast, dz, dl,
+                                                        rz, rc, V(h, V_RHOZ), V(h, V_RHOC), h->part);
         if ((r = launch_check(h)) != ABS_OK) return r;
         if ((r = reduce(h, st, 5, make_ops({RMAX, RMAX, RSUM, RMAX, RMAX}), PS_ACT, true, dz + (int64_t)NSC * h->ld)) !=
             ABS_OK)
@@ -944,6 +946,7 @@ abs_status kkt_solve_refined(abs_problem* h, KKTSys& K, const double* x, const d
         if ((r = kkt_solve_once(h, K, x, V(h, V_RHOZ), V(h, V_RHOC), V(h, V_CZ), V(h, V_CL), st)) != ABS_OK) return r;
         axpy2_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), V(h, V_CZ), dz, V(h, V_CL), dl);
         if ((r = launch_check(h)) != ABS_OK) return r;
+        dlast = V(h, V_CL);
         ++k;
     }
     if ((r = upload_ps(h, st)) != ABS_OK) return r;   // PS_RD restored

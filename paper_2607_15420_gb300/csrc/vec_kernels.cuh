@@ -202,12 +202,16 @@ __global__ void __launch_bounds__(128) dz_kernel(int S, int64_t ld, const BView 
 }
 
 // residual of the full KKT system: rho_z = r_z - (H dz + J^T dl), rho_c = r_c - (J dz + b dd).
+// The z part is formed from the last block-elimination solve of the refinement: with g =
+// r' - H dz' (its right-hand side r' and solution dz', dl' -- the first solve, or the
+// last correction), rho_z = g - J^T dl' (r' is r_z or the previous residual, so this is
+// r_z - H dz - J^T dl for the accumulated dz, dl without forming H dz again).
 // partials: [0] max|rho_z|, [1] max|rho_c|, [2] the stage's hydraulic dl, [3] max|r_z|,
 // [4] max|r_c|.  QS threads per (scenario, stage).
 __global__ void __launch_bounds__(128) kkt_residual_kernel(int S, int64_t ld, const BView b,
                                                            const double* __restrict__ jac,
-                                                           const double* __restrict__ hes,
-                                                           const double* __restrict__ sig, bool use_w,
+                                                           const double* __restrict__ g,
+                                                           const double* __restrict__ dlast,
                                                            const double* __restrict__ dz, const double* __restrict__ dl,
                                                            const double* __restrict__ rz, const double* __restrict__ rc,
                                                            double* __restrict__ rhoz, double* __restrict__ rhoc,
@@ -221,10 +225,9 @@ __global__ void __launch_bounds__(128) kkt_residual_kernel(int S, int64_t ld, co
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (live) {
         const double dd = dz[(int64_t)NSC * ld + pr];
-        const double dw = b.ps ? psv(b, PS_DW, pr) : 0.0;
         for (int j = gq; j < NV; j += QS) {
             const int64_t o = (int64_t)(NV * n + j) * ld + s;
-            const double a = rz[o] - (hv_one(ld, hes, sig, dw, use_w, dz, s, n, j) + jt_one(ld, jac, dl, s, n, j));
+            const double a = g[o] - jt_one(ld, jac, dlast, s, n, j);
             const double c = rc[o] - jv_one(ld, jac, dz, dd, s, n, j);
             rhoz[o] = a;
             rhoc[o] = c;
