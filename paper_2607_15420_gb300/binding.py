@@ -342,6 +342,10 @@ class Problem:
             self._check(st)
         return res
 
+    def last_error(self):
+        msg = lib().abs_last_error(self.h)
+        return msg.decode() if msg else ""
+
     def scenario_status(self):
         out = np.zeros(self.S, dtype=np.int32)
         self._check(lib().absorber_scenario_status(self.h, out.ctypes.data))

@@ -409,7 +409,7 @@ struct abs_problem {
     int graphs = 1;                  // replay captured launch sequences (options.graphs)
     struct GraphEntry {
         const void* ptr[9];
-        int prec, use_w, have_p, tiles[4];
+        int prec, use_w, have_p, autotune, tiles[4];
         int runs;                    // eager runs so far (capture happens on the second)
         cudaGraphExec_t exec;
         int64_t nkern;
@@ -430,7 +430,7 @@ namespace {
 // vector pool indices (each NSC * ld + ld doubles; the problems' d slots at NSC * ld + p)
 enum {
     V_X, V_LAM, V_ZL, V_ZU, V_C, V_JTL, V_SIG, V_RZ, V_RC, V_P, V_Q, V_DZ, V_DL, V_DZL, V_DZU,
-    V_G, V_RHOZ, V_RHOC, V_CZ, V_CL, V_ONE, V_CT, V_RCS, V_RCN, V_SZ, V_SL, V_COUNT
+    V_G, V_RHOZ, V_RHOC, V_CZ, V_CL, V_ONE, V_CT, V_RCS, V_RCN, V_SZ, V_SL, V_HQ, V_T, V_COUNT
 };
 
 abs_status fail(abs_problem* h, abs_status st, const std::string& msg) {
@@ -640,6 +640,10 @@ template <class Launch>
 abs_status tuned_launch(abs_problem* h, int kind, int es, std::initializer_list<int> cands, int dflt,
                         Launch&& launch, cudaStream_t st) {
     int w = dflt;
+    // no timing inside a stream capture (a capture admits no synchronization): an untuned
+    // key launches its default shape there
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusNone;
     if (h->autotune && h->S >= TUNE_MIN_S) {
         const auto key = std::make_tuple(h->dev, kind, es, size_bucket(h->S));
         bool found = false;
@@ -650,6 +654,10 @@ abs_status tuned_launch(abs_problem* h, int kind, int es, std::initializer_list<
                 w = it->second;
                 found = true;
             }
+        }
+        if (!found && cap != cudaStreamCaptureStatusNone) {
+            h->tile[kind] = w;
+            return launch(w);
         }
         if (!found) {
             cudaEvent_t e0, e1;
@@ -805,7 +813,7 @@ abs_status kkt_factor_core(abs_problem* h, KKTSys& K, const double* x, cudaStrea
                  : solve_j(h, K.prec, K.jac, x, nullptr, V(h, V_Q), st);
     if (r != ABS_OK) return r;
     schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, nullptr, V(h, V_Q),
-                                             nullptr, h->sing, h->part, SCHUR_DD);
+                                             nullptr, h->sing, h->part, SCHUR_DD, V(h, V_HQ), nullptr);
     if ((r = launch_check(h)) != ABS_OK) return r;
     if ((r = reduce(h, st, 6, make_ops({RSUM, RSUM, RSUM, RSUM, RSUM, RSUM}), PS_ACT, true)) != ABS_OK) return r;
     const int NP = h->NP;
@@ -832,13 +840,14 @@ abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, 
     abs_status r;
     if (!have_p && (r = solve_j(h, K.prec, K.jac, x, rc, V(h, V_P), st)) != ABS_OK) return r;
     schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q),
-                                             rz, nullptr, h->part, SCHUR_RHS);
+                                             rz, nullptr, h->part, SCHUR_RHS, nullptr,
+                                             V(h, V_T));
     if ((r = launch_check(h)) != ABS_OK) return r;
     if ((r = reduce(h, st, 4, make_ops({RSUM, RSUM, RSUM, RSUM}), PS_ACT, false)) != ABS_OK) return r;
     finalize_dd_kernel<<<(unsigned)((h->NP + 127) / 128), 128, 0, st>>>(h->ld, view(h), h->red, dz);
     if ((r = launch_check(h)) != ABS_OK) return r;
-    dz_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q), rz,
-                                          dz, V(h, V_G));
+    dz_fast_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), V(h, V_P), V(h, V_Q), V(h, V_T),
+                                              V(h, V_HQ), dz, V(h, V_G));
     if ((r = launch_check(h)) != ABS_OK) return r;
     return solve_jt(h, K.prec, K.jac, V(h, V_G), dl, st);
 }
@@ -855,7 +864,8 @@ abs_status kkt_solve_once(abs_problem* h, const KKTSys& K, const double* x, cons
     abs_problem::GraphEntry* ge = nullptr;
     for (auto& g : h->gcache)
         if (std::memcmp(g.ptr, key, sizeof(key)) == 0 && g.prec == K.prec && g.use_w == (int)K.use_w &&
-            g.have_p == (int)have_p && std::memcmp(g.tiles, h->tile, sizeof(g.tiles)) == 0) {
+            g.have_p == (int)have_p && g.autotune == h->autotune &&
+            std::memcmp(g.tiles, h->tile, sizeof(g.tiles)) == 0) {
             ge = &g;
             break;
         }
@@ -865,6 +875,7 @@ abs_status kkt_solve_once(abs_problem* h, const KKTSys& K, const double* x, cons
         g.prec = K.prec;
         g.use_w = (int)K.use_w;
         g.have_p = (int)have_p;
+        g.autotune = h->autotune;   // a first eager run under this tuner setting tunes the kinds used
         std::memcpy(g.tiles, h->tile, sizeof(g.tiles));
         h->gcache.push_back(g);
         ge = &h->gcache.back();
@@ -1511,7 +1522,7 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
                                                             pv, qv);
     NA_LAUNCHED();
     schur_kernel<<<gq, kThr, 0, st>>>((int)S, ld, bv, hess_vals, sigma, true, pv, qv, rhs_x, sing, part,
-                                      SCHUR_DD | SCHUR_RHS);
+                                      SCHUR_DD | SCHUR_RHS, nullptr, nullptr);
     NA_LAUNCHED();
     double hx[3] = {0.0, 0.0, 0.0};
     const int64_t plane = (int64_t)N_STAGES * ld;

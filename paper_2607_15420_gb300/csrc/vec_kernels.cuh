@@ -131,14 +131,17 @@ __global__ void __launch_bounds__(128) rhs_kernel(const Params P, int S, int64_t
 
 // Schur partial sums with H = W + Sigma (W optional): with SCHUR_DD [0] q^T H q,
 // [1] q^T q; with SCHUR_RHS [2] q^T (r - H p), [3] q^T p; always [4] the scenario's d-d
-// Hessian entry and [5] the singular flag.  Terms not asked for are 0.
+// Hessian entry and [5] the singular flag.  Terms not asked for are 0.  Optionally the
+// vectors behind them: hq = H q (SCHUR_DD), t = r - H p (SCHUR_RHS), from which
+// dz_fast_kernel forms g without another product with H.
 enum { SCHUR_DD = 1, SCHUR_RHS = 2 };
 // QS threads per (scenario, stage).
 __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BView b, const double* __restrict__ hes,
                                                     const double* __restrict__ sig, bool use_w,
                                                     const double* __restrict__ p, const double* __restrict__ q,
                                                     const double* __restrict__ r, const int* __restrict__ sing,
-                                                    double* part, int terms) {
+                                                    double* part, int terms, double* __restrict__ hq,
+                                                    double* __restrict__ tv) {
     __shared__ double sm[QS][4][32];
     const int g = threadIdx.x >> 5;
     const int s = blockIdx.x * QS_SCEN + (threadIdx.x & 31);
@@ -153,11 +156,17 @@ __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BVi
                 const int64_t o = (int64_t)(NV * n + j) * ld + s;
                 const double qj = q[o];
                 if (terms & SCHUR_DD) {
-                    v[0] += qj * hv_one(ld, hes, sig, 0.0, use_w, q, s, n, j);
+                    const double hqj = hv_one(ld, hes, sig, 0.0, use_w, q, s, n, j);
+                    if (hq) hq[o] = hqj;
+                    v[0] += qj * hqj;
                     v[1] += qj * qj;
                 }
                 if (terms & SCHUR_RHS) {
-                    if (r) v[2] += qj * (r[o] - (p ? hv_one(ld, hes, sig, 0.0, use_w, p, s, n, j) : 0.0));
+                    if (r) {
+                        const double tj = r[o] - (p ? hv_one(ld, hes, sig, 0.0, use_w, p, s, n, j) : 0.0);
+                        if (tv) tv[o] = tj;
+                        v[2] += qj * tj;
+                    }
                     if (p) v[3] += qj * p[o];
                 }
             }
@@ -198,6 +207,28 @@ __global__ void __launch_bounds__(128) dz_kernel(int S, int64_t ld, const BView 
     for (int j = gq; j < NV; j += QS) {
         const int64_t o = (int64_t)(NV * n + j) * ld + s;
         g[o] = r[o] - hv_one(ld, hes, sig, dw, use_w, dz, s, n, j);
+    }
+}
+
+// dz = p - q dd and g = r - (H + dw I) dz from the Schur pass's vectors t = r - H p and
+// hq = H q (H = W + Sigma): g = t - dw p + dd (hq + dw q), no product with H.  One thread
+// per (scenario, stage).
+__global__ void __launch_bounds__(128) dz_fast_kernel(int S, int64_t ld, const BView b, const double* __restrict__ p,
+                                                      const double* __restrict__ q, const double* __restrict__ t,
+                                                      const double* __restrict__ hq, double* __restrict__ dz,
+                                                      double* __restrict__ g) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    const int pr = live_prob(b, s, S, PS_ACT);
+    if (pr < 0) return;
+    const double dd = dz[(int64_t)NSC * ld + pr];
+    const double dw = b.ps ? psv(b, PS_DW, pr) : 0.0;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int64_t o = (int64_t)(NV * n + j) * ld + s;
+        const double pj = p[o], qj = q[o];
+        dz[o] = pj - qj * dd;
+        g[o] = t[o] - dw * pj + dd * (hq[o] + dw * qj);
     }
 }
 

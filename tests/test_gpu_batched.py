@@ -132,7 +132,7 @@ def test_autotuned_tiles_give_identical_results(B):
         x = torch.zeros(prob.n_primal, dtype=torch.float64, device="cuda")
         o = B.default_options(precision=1, max_refine=8, autotune=tune)
         r = prob.ipm_solve(o, x_out=x)
-        assert r.status == 0
+        assert r.status == 0, (tune, r.status, prob.last_error())
         outs.append((r.iters, r.d, _host(x), list(r.tiles)))
     assert outs[0][0] == outs[1][0] == outs[2][0]
     assert outs[0][1] == outs[1][1] == outs[2][1]
