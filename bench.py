@@ -33,21 +33,29 @@ if ROOT not in sys.path:
 METRIC = "Newton steps/s & solve time, 5000-scenario absorber, vs FP64 GPU path at 1e-8"
 UNIT = "Newton steps/s"
 DEFAULT_WORKLOAD = "absorber-S5000-tn5-seed2"
-# Algorithmic work per scenario and launch (derivations in DESIGN.md, "Roofline")
+# Algorithmic work per scenario and launch.  Bytes: the values a launch must read and
+# write once (Jacobian 1497 and Hessian 661 entries, 220-entry vectors, factors of 10
+# stage blocks: 22 x 22 LU or inverse, 22 x 11 G for 9 stages, 44 bytes of row order).
+# Flops: FP64 factor = block LU (7183 per stage) + G = At^-1 B (10406 per stage with B);
+# FP32 factor = Gauss-Jordan exchanges (22 steps x 21 rows x 32 columns x 2 + the pivot
+# row's 33 products, 22 columns without B on the last stage); a block solve applies a
+# 22 x 22 factor (968), the coupling (28) and G (484) per stage and right-hand side.
 EVAL_BYTES_PER_SCEN = 8 * (220 + 220 + 18 + 220 + 1497 + 661)    # read x, lambda, feed; write c, J, H
 TRIAL_BYTES_PER_SCEN = 8 * (2 * 220 + 18)                         # read x, dx, feed
-FACTOR_FLOPS_PER_SCEN = 10 * 7183 + 9 * 10406                     # stage LUs + G = At^-1 B
-SOLVE_FLOPS_PER_SCEN_RHS = 10 * (28 + 968 + 484)                  # coupling + LU apply + G product
-SOLVE_T_FLOPS_PER_SCEN = 10 * (2 * 968 + 2 * 28)                  # two LU^T applies + couplings
+FACTOR_FLOPS_PER_SCEN = {8: 10 * 7183 + 9 * 10406,                # FP64: stage LUs + G
+                         4: 9 * 22 * (21 * 32 * 2 + 33) + 22 * (21 * 21 * 2 + 22)}   # FP32: Gauss-Jordan
+SOLVE_FLOPS_PER_SCEN_RHS = 10 * (28 + 968 + 484)                  # coupling + block apply + G product
+SOLVE_T_FLOPS_PER_SCEN = 10 * (484 + 968 + 28)                    # G^T product + transposed apply + coupling
+PIV_BYTES_PER_SCEN = 10 * 44
 
 
-# DRAM bytes (read + write) per launch of the timed form's largest kernel, from the ncu
-# capture summarised in profiles/factor_warp_kernel_S5000_ncu.md, keyed by (kernel,
+# DRAM bytes (read + write) per launch of the timed form's largest kernel, from one ncu
+# capture of the 5000-scenario workload (summarised with the profiles), keyed by (kernel,
 # element size) with the sha256 of the kernel source at capture: reported only while the
 # source is unchanged
 CAPTURED_TRAFFIC = {
-    ("factor", 4): (143.824640e6, "71f8dc9650436cb30615604dadb7212426f72dd6296521908f96fc00968c13eb"),
-    ("factor", 8): (284.570624e6, "71f8dc9650436cb30615604dadb7212426f72dd6296521908f96fc00968c13eb"),
+    ("factor", 4): (146.694400e6, "b3df62c1fa155befe4d1ed1c615a2e8ac91317e53f75743c9842ebf757aee5b0"),
+    ("factor", 8): (286.098432e6, "b3df62c1fa155befe4d1ed1c615a2e8ac91317e53f75743c9842ebf757aee5b0"),
 }
 
 
@@ -64,15 +72,15 @@ def captured_traffic(kernel, es, S):
 
 
 def factor_bytes(es):
-    return es * (4840 + 9 * 242) + 8 * 1497 + 220
+    return es * (4840 + 9 * 242) + 8 * 1497 + PIV_BYTES_PER_SCEN
 
 
 def solve_bytes(es, nrhs):
-    return es * (4840 + 9 * 242) + 220 + 8 * 300 + nrhs * 8 * 2 * 220
+    return es * (4840 + 9 * 242) + PIV_BYTES_PER_SCEN + 8 * 300 + nrhs * 8 * 2 * 220
 
 
 def solve_t_bytes(es):
-    return es * 4840 + 220 + 8 * 300 + 8 * 2 * 220
+    return es * (4840 + 9 * 242) + PIV_BYTES_PER_SCEN + 8 * 300 + 8 * 2 * 220
 
 
 def load_peaks():
@@ -400,7 +408,7 @@ def main():
     work = {  # (flops, bytes) per launch
         "eval": (None, EVAL_BYTES_PER_SCEN * Sx),
         "eval_trial": (None, TRIAL_BYTES_PER_SCEN * Sx),
-        "factor": (FACTOR_FLOPS_PER_SCEN * Sx, factor_bytes(es) * Sx),
+        "factor": (FACTOR_FLOPS_PER_SCEN[es] * Sx, factor_bytes(es) * Sx),
         "solve": (SOLVE_FLOPS_PER_SCEN_RHS * Sx * 1.5, solve_bytes(es, 1.5) * Sx),
         "solve_t": (SOLVE_T_FLOPS_PER_SCEN * Sx, solve_t_bytes(es) * Sx),
     }
