@@ -54,8 +54,8 @@ PIV_BYTES_PER_SCEN = 10 * 44
 # element size) with the sha256 of the kernel source at capture: reported only while the
 # source is unchanged
 CAPTURED_TRAFFIC = {
-    ("factor", 4): (146.694400e6, "b3df62c1fa155befe4d1ed1c615a2e8ac91317e53f75743c9842ebf757aee5b0"),
-    ("factor", 8): (286.098432e6, "b3df62c1fa155befe4d1ed1c615a2e8ac91317e53f75743c9842ebf757aee5b0"),
+    ("factor", 4): (146.694400e6, "ae24436d2bbf638f93e2be105e84d56b253b19fc4f4e518160b4988fe058d4ec"),
+    ("factor", 8): (286.098432e6, "ae24436d2bbf638f93e2be105e84d56b253b19fc4f4e518160b4988fe058d4ec"),
 }
 
 

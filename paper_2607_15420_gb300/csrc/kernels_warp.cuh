@@ -504,13 +504,6 @@ __global__ void __launch_bounds__(32 * WPB, WPB >= 8 ? 3 : 24 / WPB) factor_gj_k
     if (lane == 0) sing[s] = singular;
 }
 
-// stage an LU block (contiguous in global memory) into shared memory, coalesced
-template <class T>
-__device__ inline void stage_lu(const T* __restrict__ src, T (*dst)[PADL], int lane) {
-    for (int e = lane; e < NV * NV; e += 32) dst[e / NV][e % NV] = src[e];
-    __syncwarp();
-}
-
 // w <- At^-1 w, lane i holding w_i (lanes >= 22 carry zeros): P w in one shuffle, then
 // L forward and U backward (unrolled: the loads of A run ahead of the shuffle chain)
 template <class T>
