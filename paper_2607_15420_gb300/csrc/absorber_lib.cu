@@ -430,7 +430,7 @@ namespace {
 // vector pool indices (each NSC * ld + ld doubles; the problems' d slots at NSC * ld + p)
 enum {
     V_X, V_LAM, V_ZL, V_ZU, V_C, V_JTL, V_SIG, V_RZ, V_RC, V_P, V_Q, V_DZ, V_DL, V_DZL, V_DZU,
-    V_G, V_RHOZ, V_RHOC, V_CZ, V_CL, V_ONE, V_CT, V_RCS, V_RCN, V_SZ, V_SL, V_HQ, V_T, V_COUNT
+    V_G, V_RHOZ, V_RHOC, V_CZ, V_CL, V_ONE, V_CT, V_RCS, V_RCN, V_SZ, V_SL, V_HQ, V_T, V_IL, V_IU, V_COUNT
 };
 
 abs_status fail(abs_problem* h, abs_status st, const std::string& msg) {

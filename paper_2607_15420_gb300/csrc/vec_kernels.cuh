@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(128) rhs_kernel(const Params P, int S, int64_t
                                                   const double* __restrict__ x, const double* __restrict__ zL,
                                                   const double* __restrict__ zU, const double* __restrict__ jtl,
                                                   const double* __restrict__ c, double* __restrict__ sig,
-                                                  double* __restrict__ rz, double* __restrict__ rc) {
+                                                  double* __restrict__ rz, double* __restrict__ rc,
+                                                  double* __restrict__ invL, double* __restrict__ invU) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
     const int p = live_prob(b, s, S, PS_ACT);
@@ -114,12 +115,14 @@ __global__ void __launch_bounds__(128) rhs_kernel(const Params P, int S, int64_t
         const double xv = x[o];
         double sg = 0.0, gb = 0.0;
         if (has_lo(j)) {
-            const double inv = 1.0 / (xv - lo_of(P, j));   // one division per bound
+            const double inv = 1.0 / (xv - lo_of(P, j));   // one division per bound, kept for step_kernel
+            invL[o] = inv;
             sg += zL[o] * inv;
             gb -= mu * inv;
         }
         if (has_hi(j)) {
             const double inv = 1.0 / (hi_of(P, j) - xv);
+            invU[o] = inv;
             sg += zU[o] * inv;
             gb += mu * inv;
         }
@@ -278,10 +281,12 @@ __global__ void __launch_bounds__(128) kkt_residual_kernel(int S, int64_t ld, co
 
 // bound-multiplier steps and step-size limits (mu, tau of the problem):
 // [0] min primal ratio (alpha_max), [1] min dual ratio (alpha_z),
-// [2] barrier gradient . dz, [3] max |dz| / (1 + |z|)
+// [2] barrier gradient . dz, [3] max |dz| / (1 + |z|).  invL, invU: the reciprocal slacks
+// rhs_kernel formed at the same x.
 __global__ void __launch_bounds__(128) step_kernel(const Params P, int S, int64_t ld, const BView b,
                                                    const double* __restrict__ x, const double* __restrict__ dz,
                                                    const double* __restrict__ zL, const double* __restrict__ zU,
+                                                   const double* __restrict__ invL, const double* __restrict__ invU,
                                                    double* __restrict__ dzL, double* __restrict__ dzU, double* part) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(128) step_kernel(const Params P, int S, int64_
         }
         dnan = dnan || d != d;
         if (has_lo(j)) {
-            const double sl = xv - lo_of(P, j), inv = 1.0 / sl;
+            const double sl = xv - lo_of(P, j), inv = invL[o];
             const double z = zL[o];
             const double dzl = mu * inv - z - (z * inv) * d;
             dzL[o] = dzl;
@@ -322,7 +327,7 @@ __global__ void __launch_bounds__(128) step_kernel(const Params P, int S, int64_
             dzL[o] = 0.0;
         }
         if (has_hi(j)) {
-            const double su = hi_of(P, j) - xv, inv = 1.0 / su;
+            const double su = hi_of(P, j) - xv, inv = invU[o];
             const double z = zU[o];
             const double dzu = mu * inv - z + (z * inv) * d;
             dzU[o] = dzu;
@@ -397,15 +402,16 @@ __global__ void __launch_bounds__(128) accept_kernel(const Params P, int S, int6
         const double xv = x[o] + alpha * dz[o];
         x[o] = xv;
         lam[o] += alpha * dl[o];
+        // z kept within [mu / (k_sigma s), k_sigma mu / s]: a division only when it clamps
         if (has_lo(j)) {
-            const double inv = 1.0 / (xv - lo_of(P, j));
+            const double sl = xv - lo_of(P, j);
             const double z = zL[o] + alpha_z * dzL[o];
-            zL[o] = fmin(fmax(z, mlo * inv), mhi * inv);
+            zL[o] = (z * sl < mlo || z * sl > mhi) ? fmin(fmax(z, mlo / sl), mhi / sl) : z;
         }
         if (has_hi(j)) {
-            const double inv = 1.0 / (hi_of(P, j) - xv);
+            const double su = hi_of(P, j) - xv;
             const double z = zU[o] + alpha_z * dzU[o];
-            zU[o] = fmin(fmax(z, mlo * inv), mhi * inv);
+            zU[o] = (z * su < mlo || z * su > mhi) ? fmin(fmax(z, mlo / su), mhi / su) : z;
         }
     }
 }

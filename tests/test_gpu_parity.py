@@ -162,6 +162,32 @@ def test_newton_direction_parity(B, prec):
     assert err <= 1e-10, (err, info.refine_steps, info.residual)
 
 
+def test_fp32_direction_before_and_after_refinement(B):
+    # the FP32 stage-block inverses alone give the direction to FP32 accuracy times the
+    # blocks' condition numbers; the FP64 refinement then reaches 1e-10 in a few steps
+    import torch
+    F, st, sig, sigd, rz, rd, rc, (dZ, dd, dl), fac = _direction_case(10, 0, 6)
+    prob = B.Problem(P, F)
+    _, _, _, _, _, (x, lm, c, jac, hes) = _eval_gpu(B, prob, st.Z, st.d, st.lam)
+    sg = dev(prob.to_soa(sig, sigd))
+    inert = prob.kkt_factor(x, jac, hes, sg, precision=1)
+    assert inert.n_singular == 0
+    rx = dev(prob.to_soa(rz, rd))
+    rcd = dev(prob.to_soa(rc))
+    xo = np.concatenate([[dd], dZ.ravel(), dl.ravel()])
+    errs = []
+    for mr in (0, 8):
+        sx = torch.zeros_like(rx)
+        sc = torch.zeros_like(rcd)
+        info = prob.kkt_solve(rx, rcd, sx, sc, max_refine=mr, refine_tol=1e-12)
+        gz_, gd_ = prob.from_soa(host(sx))
+        gl_, _ = prob.from_soa(host(sc))
+        xg = np.concatenate([[gd_], gz_.ravel(), gl_.ravel()])
+        errs.append((np.linalg.norm(xg - xo) / np.linalg.norm(xo), info.refine_steps, info.residual))
+    assert errs[0][0] <= 5e-2, errs
+    assert errs[1][0] <= 1e-9 and errs[1][1] <= 4, errs
+
+
 def _gpu_solve(B, F, prec=0, **opt):
     import torch
     prob = B.Problem(P, F)
