@@ -383,7 +383,9 @@ struct abs_problem {
     double* cred = nullptr;      // [KMAX][nchunk]
     int* rcnt = nullptr;         // [NP] chunk arrivals of the running reduction (zero between launches)
     double* red = nullptr;       // [KMAX][NP]
-    double* hred = nullptr;      // pinned [KMAX][NP] + [2][NP] fetched scalars
+    double* hred = nullptr;      // pinned [KMAX + 2][NP] staging for scalar copies
+    double* hmap = nullptr;      // pinned, device-mapped [RED_KMAX + 1][NP]: fetched reductions
+    double* hmap_dev = nullptr;  // (the reduction kernel writes them straight to host memory)
     double* ps = nullptr;        // device per-problem scalars [PS_NFIELDS][NP]
     double* hps = nullptr;       // host values of ps
     double* hring = nullptr;     // pinned staging ring [PS_RING][PS_NFIELDS][NP]
@@ -523,6 +525,8 @@ abs_status ensure_buffers(abs_problem* h) {
     CK(cudaMemset(h->rcnt, 0, sizeof(int) * (size_t)h->NP));
     CK(cudaMalloc(&h->red, sizeof(double) * (size_t)KMAX * h->NP));
     CK(cudaMallocHost(&h->hred, sizeof(double) * (size_t)(KMAX + 2) * h->NP));
+    CK(cudaHostAlloc(&h->hmap, sizeof(double) * (size_t)(RED_KMAX + 1) * h->NP, cudaHostAllocMapped));
+    CK(cudaHostGetDevicePointer(&h->hmap_dev, h->hmap, 0));
     CK(cudaMalloc(&h->ps, sizeof(double) * (size_t)PS_NFIELDS * h->NP));
     h->hps = new double[(size_t)PS_NFIELDS * h->NP]();
     CK(cudaMallocHost(&h->hring, sizeof(double) * (size_t)PS_RING * PS_NFIELDS * h->NP));
@@ -585,24 +589,21 @@ RedOps make_ops(std::initializer_list<int> l) {
 }
 
 // combine the K partial planes per problem (device result in h->red[k][p]); with fetch,
-// copy them to h->hred and also fetch the problems' d slots of `dslots` (if given) into
-// h->hred + KMAX * NP, in one round trip
+// the reduction kernel also writes them (and the problems' d slots of `dslots`, if given)
+// to mapped host memory, read after one stream synchronization (no copy round trip)
 abs_status reduce(abs_problem* h, cudaStream_t st, int K, const RedOps& ops, int flag, bool fetch,
                   const double* dslots = nullptr) {
     reduce_kernel<<<(unsigned)h->nchunk, RED_T, 0, st>>>(h->part, h->ld, K, ops, h->chunks, h->nchunk, h->pchunk,
-                                                         h->ps, h->NP, flag, h->cred, h->rcnt, h->red);
+                                                         h->ps, h->NP, flag, h->cred, h->rcnt, h->red,
+                                                         fetch ? h->hmap_dev : nullptr, fetch ? dslots : nullptr);
     abs_status r = launch_check(h);
     if (r != ABS_OK) return r;
     if (!fetch) return ABS_OK;
-    CK(cudaMemcpyAsync(h->hred, h->red, sizeof(double) * (size_t)K * h->NP, cudaMemcpyDeviceToHost, st));
-    if (dslots)
-        CK(cudaMemcpyAsync(h->hred + (size_t)KMAX * h->NP, dslots, sizeof(double) * (size_t)h->NP,
-                           cudaMemcpyDeviceToHost, st));
     return sync(h, st);
 }
 
-double RED(const abs_problem* h, int k, int p) { return h->hred[(size_t)k * h->NP + p]; }
-double DSLOT(const abs_problem* h, int p) { return h->hred[(size_t)KMAX * h->NP + p]; }
+double RED(const abs_problem* h, int k, int p) { return h->hmap[(size_t)k * h->NP + p]; }
+double DSLOT(const abs_problem* h, int p) { return h->hmap[(size_t)RED_KMAX * h->NP + p]; }
 
 // ---- the KKT machinery (every active problem at once) ----------------------------------
 struct KKTSys {
@@ -1167,6 +1168,7 @@ void absorber_destroy(abs_problem* h) {
     cudaFree(h->rcnt);
     cudaFree(h->red);
     cudaFreeHost(h->hred);
+    cudaFreeHost(h->hmap);
     cudaFree(h->ps);
     delete[] h->hps;
     cudaFreeHost(h->hring);

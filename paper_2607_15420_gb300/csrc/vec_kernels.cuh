@@ -583,7 +583,8 @@ __device__ inline double warp_red(int op, double a) {
 // a fixed order (RED_PER elements per thread, xor trees within warps, warps in order) into
 // cout[k][c].  The problem's chunk block that finishes last (a per-problem arrival
 // counter; no block waits for another) then combines the problem's chunk results, chunk c
-// on lane (c - c0) % 32 in increasing c, then an xor tree, into out[k][p] and re-arms the
+// on lane (c - c0) % 32 in increasing c, then an xor tree, into out[k][p] (and hout[k][p]
+// with hout[RED_KMAX][p] = dslots[p], when the host fetches them) and re-arms the
 // counter.  Every combination order depends on the problem's own size only.  All of a
 // thread's loads are issued before the first combination (one memory latency per block
 // instead of one per plane).
@@ -591,7 +592,8 @@ __global__ void __launch_bounds__(RED_T) reduce_kernel(const double* __restrict_
                                                        const RedOps ops, const int* __restrict__ ch, int nchunk,
                                                        const int* __restrict__ pchunk, const double* __restrict__ ps,
                                                        int NP, int flag, double* cout, int* cnt,
-                                                       double* __restrict__ out) {
+                                                       double* __restrict__ out, double* __restrict__ hout,
+                                                       const double* __restrict__ dslots) {
     __shared__ double sm[RED_T / 32][RED_KMAX];
     __shared__ int last;
     const int c = blockIdx.x;
@@ -645,8 +647,12 @@ __global__ void __launch_bounds__(RED_T) reduce_kernel(const double* __restrict_
         double a = red_id(op);
         for (int cc = c0 + lane; cc < c1; cc += 32) a = red_op(op, a, __ldcg(&cout[(int64_t)k * nchunk + cc]));
         a = warp_red(op, a);
-        if (lane == 0) out[(int64_t)k * NP + p] = a;
+        if (lane == 0) {
+            out[(int64_t)k * NP + p] = a;
+            if (hout) hout[(int64_t)k * NP + p] = a;
+        }
     }
+    if (hout && dslots && threadIdx.x == 0) hout[(int64_t)RED_KMAX * NP + p] = dslots[p];
 }
 
 // dd_p = (r_d - (beta - dw qp)) / S_d from the Schur sums red[2][p], red[3][p]; into the
