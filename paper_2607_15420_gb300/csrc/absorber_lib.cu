@@ -452,6 +452,8 @@ abs_status fail(abs_problem* h, abs_status st, const std::string& msg) {
 int64_t vsize(const abs_problem* h) { return (int64_t)NSC * h->ld + h->ld; }
 double* V(abs_problem* h, int k) { return h->vec + (int64_t)k * vsize(h); }
 dim3 grid2(const abs_problem* h) { return dim3((unsigned)((h->S + kThr - 1) / kThr), N_STAGES); }
+// elementwise kernels: one thread per (entry, scenario)
+dim3 gride(const abs_problem* h) { return dim3((unsigned)((h->S + kThr - 1) / kThr), NSC); }
 // kernels with QS threads per (scenario, stage)
 dim3 gridq(const abs_problem* h) { return dim3((unsigned)((h->S + QS_SCEN - 1) / QS_SCEN), N_STAGES); }
 dim3 gridw(const abs_problem* h, int wpb) { return dim3((unsigned)((h->S + wpb - 1) / wpb)); }
@@ -847,7 +849,7 @@ abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, 
     if ((r = reduce(h, st, 4, make_ops({RSUM, RSUM, RSUM, RSUM}), PS_ACT, false)) != ABS_OK) return r;
     finalize_dd_kernel<<<(unsigned)((h->NP + 127) / 128), 128, 0, st>>>(h->ld, view(h), h->red, dz);
     if ((r = launch_check(h)) != ABS_OK) return r;
-    dz_fast_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), V(h, V_P), V(h, V_Q), V(h, V_T),
+    dz_fast_kernel<<<gride(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), V(h, V_P), V(h, V_Q), V(h, V_T),
                                               V(h, V_HQ), dz, V(h, V_G));
     if ((r = launch_check(h)) != ABS_OK) return r;
     return solve_jt(h, K.prec, K.jac, V(h, V_G), dl, st);
@@ -956,7 +958,7 @@ abs_status kkt_solve_refined(abs_problem* h, KKTSys& K, const double* x, const d
         for (int p = 0; p < NP; ++p) PSV(h, PS_RD, p) = rhod[p];
         if ((r = upload_ps(h, st)) != ABS_OK) return r;
         if ((r = kkt_solve_once(h, K, x, V(h, V_RHOZ), V(h, V_RHOC), V(h, V_CZ), V(h, V_CL), st)) != ABS_OK) return r;
-        axpy2_kernel<<<grid2(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), V(h, V_CZ), dz, V(h, V_CL), dl);
+        axpy2_kernel<<<gride(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), V(h, V_CZ), dz, V(h, V_CL), dl);
         if ((r = launch_check(h)) != ABS_OK) return r;
         dlast = V(h, V_CL);
         ++k;

@@ -97,7 +97,12 @@ __global__ void __launch_bounds__(128) dual_kernel(const Params P, int S, int64_
     store_partials<6>(v, part, ld, s, n);
 }
 
-// barrier diagonal Sigma and right-hand sides r_z = -(J^T l - mu/sl + mu/su), r_c = -c
+// Elementwise kernels below: one thread per (entry v, scenario s), grid (ceil(S / 128),
+// 220): v = 22 n + j is the block's row, so the bound pattern of unknown j is the same on
+// every lane of a block, and every load and store is coalesced over scenarios.
+
+// barrier diagonal Sigma and right-hand sides r_z = -(J^T l - mu/sl + mu/su), r_c = -c;
+// the reciprocal slacks are kept for step_kernel
 __global__ void __launch_bounds__(128) rhs_kernel(const Params P, int S, int64_t ld, const BView b,
                                                   const double* __restrict__ x, const double* __restrict__ zL,
                                                   const double* __restrict__ zU, const double* __restrict__ jtl,
@@ -105,31 +110,28 @@ __global__ void __launch_bounds__(128) rhs_kernel(const Params P, int S, int64_t
                                                   double* __restrict__ rz, double* __restrict__ rc,
                                                   double* __restrict__ invL, double* __restrict__ invU) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = blockIdx.y;
+    const int v = blockIdx.y, j = v % NV;
     const int p = live_prob(b, s, S, PS_ACT);
     if (p < 0) return;
     const double mu = psv(b, PS_MU, p);
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        const int64_t o = (int64_t)(NV * n + j) * ld + s;
-        const double xv = x[o];
-        double sg = 0.0, gb = 0.0;
-        if (has_lo(j)) {
-            const double inv = 1.0 / (xv - lo_of(P, j));   // one division per bound, kept for step_kernel
-            invL[o] = inv;
-            sg += zL[o] * inv;
-            gb -= mu * inv;
-        }
-        if (has_hi(j)) {
-            const double inv = 1.0 / (hi_of(P, j) - xv);
-            invU[o] = inv;
-            sg += zU[o] * inv;
-            gb += mu * inv;
-        }
-        sig[o] = sg;
-        rz[o] = -(jtl[o] + gb);
-        rc[o] = -c[o];
+    const int64_t o = (int64_t)v * ld + s;
+    const double xv = x[o];
+    double sg = 0.0, gb = 0.0;
+    if (has_lo(j)) {
+        const double inv = 1.0 / (xv - lo_of(P, j));   // one division per bound
+        invL[o] = inv;
+        sg += zL[o] * inv;
+        gb -= mu * inv;
     }
+    if (has_hi(j)) {
+        const double inv = 1.0 / (hi_of(P, j) - xv);
+        invU[o] = inv;
+        sg += zU[o] * inv;
+        gb += mu * inv;
+    }
+    sig[o] = sg;
+    rz[o] = -(jtl[o] + gb);
+    rc[o] = -c[o];
 }
 
 // Schur partial sums with H = W + Sigma (W optional): with SCHUR_DD [0] q^T H q,
@@ -214,25 +216,20 @@ __global__ void __launch_bounds__(128) dz_kernel(int S, int64_t ld, const BView 
 }
 
 // dz = p - q dd and g = r - (H + dw I) dz from the Schur pass's vectors t = r - H p and
-// hq = H q (H = W + Sigma): g = t - dw p + dd (hq + dw q), no product with H.  One thread
-// per (scenario, stage).
+// hq = H q (H = W + Sigma): g = t - dw p + dd (hq + dw q), no product with H.  Elementwise.
 __global__ void __launch_bounds__(128) dz_fast_kernel(int S, int64_t ld, const BView b, const double* __restrict__ p,
                                                       const double* __restrict__ q, const double* __restrict__ t,
                                                       const double* __restrict__ hq, double* __restrict__ dz,
                                                       double* __restrict__ g) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = blockIdx.y;
     const int pr = live_prob(b, s, S, PS_ACT);
     if (pr < 0) return;
     const double dd = dz[(int64_t)NSC * ld + pr];
     const double dw = b.ps ? psv(b, PS_DW, pr) : 0.0;
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        const int64_t o = (int64_t)(NV * n + j) * ld + s;
-        const double pj = p[o], qj = q[o];
-        dz[o] = pj - qj * dd;
-        g[o] = t[o] - dw * pj + dd * (hq[o] + dw * qj);
-    }
+    const int64_t o = (int64_t)blockIdx.y * ld + s;
+    const double pj = p[o], qj = q[o];
+    dz[o] = pj - qj * dd;
+    g[o] = t[o] - dw * pj + dd * (hq[o] + dw * qj);
 }
 
 // residual of the full KKT system: rho_z = r_z - (H dz + J^T dl), rho_c = r_c - (J dz + b dd).
@@ -391,28 +388,25 @@ __global__ void __launch_bounds__(128) accept_kernel(const Params P, int S, int6
                                                      double* __restrict__ zL, const double* __restrict__ dzL,
                                                      double* __restrict__ zU, const double* __restrict__ dzU) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = blockIdx.y;
+    const int v = blockIdx.y, j = v % NV;
     const int pr = live_prob(b, s, S, PS_ACT);
     if (pr < 0) return;
     const double alpha = psv(b, PS_ALPHA, pr), alpha_z = psv(b, PS_ALPHAZ, pr), mu = psv(b, PS_MU, pr);
     const double mlo = mu / ksig, mhi = ksig * mu;
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        const int64_t o = (int64_t)(NV * n + j) * ld + s;
-        const double xv = x[o] + alpha * dz[o];
-        x[o] = xv;
-        lam[o] += alpha * dl[o];
-        // z kept within [mu / (k_sigma s), k_sigma mu / s]: a division only when it clamps
-        if (has_lo(j)) {
-            const double sl = xv - lo_of(P, j);
-            const double z = zL[o] + alpha_z * dzL[o];
-            zL[o] = (z * sl < mlo || z * sl > mhi) ? fmin(fmax(z, mlo / sl), mhi / sl) : z;
-        }
-        if (has_hi(j)) {
-            const double su = hi_of(P, j) - xv;
-            const double z = zU[o] + alpha_z * dzU[o];
-            zU[o] = (z * su < mlo || z * su > mhi) ? fmin(fmax(z, mlo / su), mhi / su) : z;
-        }
+    const int64_t o = (int64_t)v * ld + s;
+    const double xv = x[o] + alpha * dz[o];
+    x[o] = xv;
+    lam[o] += alpha * dl[o];
+    // z kept within [mu / (k_sigma s), k_sigma mu / s]: a division only when it clamps
+    if (has_lo(j)) {
+        const double sl = xv - lo_of(P, j);
+        const double z = zL[o] + alpha_z * dzL[o];
+        zL[o] = (z * sl < mlo || z * sl > mhi) ? fmin(fmax(z, mlo / sl), mhi / sl) : z;
+    }
+    if (has_hi(j)) {
+        const double su = hi_of(P, j) - xv;
+        const double z = zU[o] + alpha_z * dzU[o];
+        zU[o] = (z * su < mlo || z * su > mhi) ? fmin(fmax(z, mlo / su), mhi / su) : z;
     }
 }
 
@@ -534,20 +528,18 @@ __global__ void axpby_kernel(int S, int64_t ld, const BView b, int flag, int afi
     }
 }
 
-// y1 += x1 (per-scenario part and the problems' d slots) and y2 += x2 (per-scenario part)
-__global__ void axpy2_kernel(int S, int64_t ld, const BView b, const double* __restrict__ x1,
-                             double* __restrict__ y1, const double* __restrict__ x2, double* __restrict__ y2) {
+// y1 += x1 (per-scenario part and the problems' d slots) and y2 += x2 (per-scenario part).
+// Elementwise.
+__global__ void __launch_bounds__(128) axpy2_kernel(int S, int64_t ld, const BView b, const double* __restrict__ x1,
+                                                    double* __restrict__ y1, const double* __restrict__ x2,
+                                                    double* __restrict__ y2) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = blockIdx.y;
-    if (n == 0 && s < b.NP && (!b.ps || psv(b, PS_ACT, s) != 0.0))
+    if (blockIdx.y == 0 && s < b.NP && (!b.ps || psv(b, PS_ACT, s) != 0.0))
         y1[(int64_t)NSC * ld + s] += x1[(int64_t)NSC * ld + s];
     if (live_prob(b, s, S, PS_ACT) < 0) return;
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        const int64_t o = (int64_t)(NV * n + j) * ld + s;
-        y1[o] += x1[o];
-        y2[o] += x2[o];
-    }
+    const int64_t o = (int64_t)blockIdx.y * ld + s;
+    y1[o] += x1[o];
+    y2[o] += x2[o];
 }
 
 __global__ void max_abs_kernel(int S, int64_t ld, const BView b, const double* __restrict__ v, double* part) {
