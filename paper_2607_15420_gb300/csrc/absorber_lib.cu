@@ -1043,6 +1043,8 @@ abs_status init_handle(abs_problem* h, const abs_params* p, int64_t S) {
         h->P.hL0[l] = p->hL_ref[l] + p->hL_dh[l];
     }
     for (int j = 0; j < 4; ++j) h->P.hV0[j] = p->hV_ref[j] + p->hV_dh[j];
+    h->P.Tlo_s = p->T_lo / p->sT;
+    h->P.Thi_s = p->T_hi / p->sT;
     const PatternTables& T = pattern();
     h->nnzJ = (int)T.jrow.size();
     h->nnzH = (int)T.hrow.size();
@@ -1504,6 +1506,8 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
         P.hL0[l] = p->hL_ref[l] + p->hL_dh[l];
     }
     for (int j = 0; j < 4; ++j) P.hV0[j] = p->hV_ref[j] + p->hV_dh[j];
+    P.Tlo_s = p->T_lo / p->sT;
+    P.Thi_s = p->T_hi / p->sT;
     const dim3 g2((unsigned)((S + kThr - 1) / kThr), N_STAGES);
     const dim3 gq((unsigned)((S + QS_SCEN - 1) / QS_SCEN), N_STAGES);
     const int64_t od = (int64_t)NSC * ld;

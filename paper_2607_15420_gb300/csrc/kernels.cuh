@@ -274,8 +274,8 @@ __global__ void __launch_bounds__(128) eval_kernel(const Params P, int S, int64_
         };
 #pragma unroll
         for (int j = 0; j < NV; ++j) {
-            if (has_lo(j)) take(in.q[j] - (j == LT ? P.T_lo / P.sT : 0.0));
-            if (has_hi(j)) take(P.T_hi / P.sT - in.q[j]);
+            if (has_lo(j)) take(in.q[j] - (j == LT ? P.Tlo_s : 0.0));
+            if (has_hi(j)) take(P.Thi_s - in.q[j]);
         }
         blog = bad ? NAN : log(m) + (double)e2 * 0.69314718055994530942;   // ln 2
         const double v[3] = {em.asum, em.amax, blog};

@@ -84,6 +84,7 @@ struct Params {
     double lnsx[9];
     double hL0[9];   // hL_ref + hL_dh
     double hV0[4];
+    double Tlo_s, Thi_s;   // T_lo / sT, T_hi / sT: the scaled temperature bounds
 };
 
 struct StageIn {
