@@ -595,9 +595,18 @@ RedOps make_ops(std::initializer_list<int> l) {
 // to mapped host memory, read after one stream synchronization (no copy round trip)
 abs_status reduce(abs_problem* h, cudaStream_t st, int K, const RedOps& ops, int flag, bool fetch,
                   const double* dslots = nullptr) {
-    reduce_kernel<<<(unsigned)h->nchunk, RED_T, 0, st>>>(h->part, h->ld, K, ops, h->chunks, h->nchunk, h->pchunk,
-                                                         h->ps, h->NP, flag, h->cred, h->rcnt, h->red,
-                                                         fetch ? h->hmap_dev : nullptr, fetch ? dslots : nullptr);
+    double* hout = fetch ? h->hmap_dev : nullptr;
+    const double* ds = fetch ? dslots : nullptr;
+    switch (K) {
+#define RK(k)                                                                                                      \
+    case k:                                                                                                        \
+        reduce_kernel<k><<<(unsigned)h->nchunk, RED_T, 0, st>>>(h->part, h->ld, ops, h->chunks, h->nchunk, h->pchunk, \
+                                                                 h->ps, h->NP, flag, h->cred, h->rcnt, h->red, hout, ds); \
+        break;
+        RK(1) RK(2) RK(3) RK(4) RK(5) RK(6) RK(7) RK(8) RK(9)
+#undef RK
+        default: return fail(h, ABS_ERR_ARG, "reduction with more than 9 planes");
+    }
     abs_status r = launch_check(h);
     if (r != ABS_OK) return r;
     if (!fetch) return ABS_OK;

@@ -580,13 +580,15 @@ __device__ inline double warp_red(int op, double a) {
 // counter.  Every combination order depends on the problem's own size only.  All of a
 // thread's loads are issued before the first combination (one memory latency per block
 // instead of one per plane).
-__global__ void __launch_bounds__(RED_T) reduce_kernel(const double* __restrict__ part, int64_t ld, int K,
+template <int K>
+__global__ void __launch_bounds__(RED_T) reduce_kernel(const double* __restrict__ part, int64_t ld,
                                                        const RedOps ops, const int* __restrict__ ch, int nchunk,
                                                        const int* __restrict__ pchunk, const double* __restrict__ ps,
                                                        int NP, int flag, double* cout, int* cnt,
                                                        double* __restrict__ out, double* __restrict__ hout,
                                                        const double* __restrict__ dslots) {
-    __shared__ double sm[RED_T / 32][RED_KMAX];
+    static_assert(K >= 1 && K <= RED_KMAX, "planes per reduction");
+    __shared__ double sm[RED_T / 32][K];
     __shared__ int last;
     const int c = blockIdx.x;
     const int p = ch[5 * c + 0], off = ch[5 * c + 1], Sp = ch[5 * c + 2], i0 = ch[5 * c + 3], i1 = ch[5 * c + 4];
@@ -600,15 +602,14 @@ __global__ void __launch_bounds__(RED_T) reduce_kernel(const double* __restrict_
         ok[t] = live && i < i1;
         idx[t] = ok[t] ? (int64_t)(i / Sp) * ld + off + i % Sp : 0;
     }
-    double v[RED_KMAX][RED_PER];
+    double v[K][RED_PER];
 #pragma unroll
-    for (int k = 0; k < RED_KMAX; ++k)
+    for (int k = 0; k < K; ++k)
 #pragma unroll
-        for (int t = 0; t < RED_PER; ++t) v[k][t] = (k < K && ok[t]) ? part[(int64_t)k * plane + idx[t]] : 0.0;
+        for (int t = 0; t < RED_PER; ++t) v[k][t] = ok[t] ? part[(int64_t)k * plane + idx[t]] : 0.0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 0; k < RED_KMAX; ++k) {
-        if (k >= K) break;
+    for (int k = 0; k < K; ++k) {
         const int op = ops.op[k];
         double a = red_id(op);
 #pragma unroll
