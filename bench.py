@@ -54,8 +54,8 @@ PIV_BYTES_PER_SCEN = 10 * 44
 # element size) with the sha256 of the kernel source at capture: reported only while the
 # source is unchanged
 CAPTURED_TRAFFIC = {
-    ("factor", 4): (146.694400e6, "ae24436d2bbf638f93e2be105e84d56b253b19fc4f4e518160b4988fe058d4ec"),
-    ("factor", 8): (286.098432e6, "ae24436d2bbf638f93e2be105e84d56b253b19fc4f4e518160b4988fe058d4ec"),
+    ("factor", 4): (146.694400e6, "0441fcd54221915988ef5c67067e04d85227200887a2128e198ddd87f6f6ca3b"),
+    ("factor", 8): (286.098432e6, "0441fcd54221915988ef5c67067e04d85227200887a2128e198ddd87f6f6ca3b"),
 }
 
 

@@ -5,7 +5,8 @@
 // update with columns on lanes (each lane keeps its pivot-row entry in a register and
 // walks the rows), the super-diagonal block B_n appended as 11 extra columns so that the
 // elimination yields L^-1 P B_n, then U G_n = L^-1 P B_n by backward substitution.
-// factor_reg_kernel (FP32) keeps row i of the block in lane i's registers instead.
+// factor_gj_kernel (FP32) forms the stage-block inverse instead, by Gauss-Jordan exchange
+// with row i of the block in lane i's registers.
 // Vectors of the solves live one entry per lane; broadcasts are warp shuffles.
 //
 // Factor storage is per scenario and contiguous (internal layout, not part of the C
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
         for (int k = 0; k < NV; ++k) {
             // key 0 marks lanes outside the candidate rows.  FP64: exact |value| keys, ties to
             // the lowest row (an exact zero candidate also has key 0: the singular test below
-            // catches it); FP32: pivot_key32 (the same choice as factor_reg_kernel)
+            // catches it); FP32: pivot_key32 (the rule of factor_gj_kernel)
             const bool cand = lane >= k && lane < NV;
             int p;
             if constexpr (sizeof(T) == 4) {

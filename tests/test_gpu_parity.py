@@ -272,6 +272,8 @@ def test_error_paths(B):
     assert res.status == -6 and res.iters == 3               # iteration limit is reported
     o = B.default_options(tol=-1.0)
     assert prob.ipm_solve(o).status == -1
+    o = B.default_options(precision=1, max_refine=8, factor_tile=3)   # not a launch shape
+    assert prob.ipm_solve(o).status == -1
 
 
 def test_full_size_s5000_mixed_precision_properties(B):
