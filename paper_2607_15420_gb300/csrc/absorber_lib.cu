@@ -869,7 +869,7 @@ abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, 
 }
 
 // the same, replayed from a CUDA graph on the engine's stream: the launch sequence
-// (7 kernels, with the tile shapes the autotuner chose) is captured on its second use
+// (up to 6 kernels, with the tile shapes the autotuner chose) is captured on its second use
 // with a given set of vectors and replayed from then on; the per-problem scalars it
 // depends on are read from device memory at replay time
 abs_status kkt_solve_once(abs_problem* h, const KKTSys& K, const double* x, const double* rz, const double* rc,
