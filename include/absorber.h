@@ -258,7 +258,7 @@ typedef struct abs_options {
                               size bucket (S rounded down to a power of two, S >= 256) times
                               every warps-per-block candidate and keeps the fastest
                               (results are identical); 0: 4 warps per block */
-    int32_t graphs;        /* 1: the Schur-reduced KKT solve (up to 7 launches) is captured into a
+    int32_t graphs;        /* 1: the Schur-reduced KKT solve (up to 6 launches) is captured into a
                               CUDA graph on the engine's stream at its second use with a
                               given set of vectors and replayed from then on */
     int32_t factor_tile;   /* FP32 factor launches only: 0 shape from autotune; 1, 2, 4, 8:
