@@ -128,14 +128,24 @@ def minimum_diameter(P, F, Z):
     return math.sqrt(4.0 * float(vol.max()) / (math.pi * P["u_max"])), vol
 
 
-def kkt_error(P, F, d, Z, lam, zL, zU, zLd, zUd, s_max=100.0):
+def kkt_error(P, F, d, Z, lam, zL, zU, zLd, zUd, s_max=100.0, chunk=None):
     """E_0 (Wachter & Biegler 2006, Eq. (5) at mu = 0) from the definitions, with the
-    constraint Jacobian by complex step."""
-    lo, hi, dlo, dhi = model.bounds(P, Z.shape[0])
-    J, Jd = jacobian_complex_step(P, F, Z, d)
+    constraint Jacobian by complex step.  chunk: scenarios per complex-step Jacobian
+    (the Jacobian is block diagonal by scenario; chunking bounds the memory of the
+    (S, 220, 220) array and changes no arithmetic)."""
+    S = Z.shape[0]
+    lo, hi, dlo, dhi = model.bounds(P, S)
+    step = S if chunk is None else int(chunk)
+    rz = np.zeros_like(Z)
+    jdl = 0.0
+    for a in range(0, S, step):
+        b = min(S, a + step)
+        J, Jd = jacobian_complex_step(P, F[:, a:b], Z[a:b], d)
+        rz[a:b] = np.einsum("sr,src->sc", lam[a:b], J)
+        jdl += float(np.sum(Jd * lam[a:b]))
     C = model.residuals(P, F, Z, d)
-    rz = np.einsum("sr,src->sc", lam, J) - zL + zU
-    rd = 1.0 + float(np.sum(Jd * lam)) - zLd + zUd
+    rz = rz - zL + zU
+    rd = 1.0 + jdl - zLd + zUd
     hasL, hasU = np.isfinite(lo), np.isfinite(hi)
     cl = np.where(hasL, zL * (Z - np.where(hasL, lo, 0)), 0.0)
     cu = np.where(hasU, zU * (np.where(hasU, hi, 0) - Z), 0.0)
