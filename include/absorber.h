@@ -328,6 +328,20 @@ abs_status ipm_solve(abs_problem* h, const abs_options* opt, const double* warm_
                      const double* warm_y, abs_result* res, double* x_out, double* y_out,
                      abs_stream_t stream);
 
+/* Bound multipliers z_L, z_U of the bounds (10c-d) at the point the last ipm_solve,
+ * ipm_solve_batch or ipm_solve_learned on this handle returned (the primal-dual iterate
+ * of the interior-point method, Wachter & Biegler 2006, Eq. (4); the KKT point of the
+ * paper's Section "GPU-resident solution with MadNLP.jl"), for the unscaled problem
+ * min d (the solver's scaled multipliers divided by each problem's obj_scaling), so that
+ * with x_out and y_out of the same solve they give every term of the optimality error
+ * E_0.  Unknowns without a lower (upper) bound carry 0.
+ *   zl_out, zu_out  device primal vectors in the handle's layout (the d slot(s) receive
+ *                   each problem's multiplier of d >= d_lo / d <= d_hi), or NULL.
+ *   zd_out          host, 2 P doubles (z_L of each problem's d, then z_U), or NULL.
+ * Errors: ABS_ERR_ARG (no finished solve on the handle), ABS_ERR_CUDA.  Synchronous. */
+abs_status absorber_bound_multipliers(abs_problem* h, double* zl_out, double* zu_out, double* zd_out,
+                                      abs_stream_t stream);
+
 /* A handle holding P independent design problems side by side: problem q has sizes[q]
  * scenarios, and its feeds are columns [off_q, off_q + sizes[q]) of feeds (off_q = the
  * sum of the earlier sizes).
@@ -507,10 +521,13 @@ abs_status ipm_solve_learned(abs_problem* h, abs_mlp* net, const abs_options* op
  * Errors: ABS_ERR_ARG, ABS_ERR_NUMERIC (singular stage block), ABS_ERR_INERTIA (Schur
  * complement not positive: increase delta_w), ABS_ERR_CUDA.
  * The first call on each device looks up the array's device address and uploads the
- * pattern tables: make that first call before any stream capture.  All calls share
- * the one array, which keeps the last call's contents: calls that overlap on the GPU
- * (other streams, other host threads) race and must be serialised by the caller.
- * Synchronises the stream before returning. */
+ * pattern tables.  All calls share the one array, which keeps the last call's contents;
+ * the library serialises every call of this entry point in the process (a lock held
+ * until the call's stream has drained), so two calls never overlap on the GPU -- but
+ * other work the caller queues on other streams must not touch the same output buffers
+ * meanwhile.  The call copies a few scalars through pageable host memory and
+ * synchronises the stream before returning, so it cannot be recorded into a CUDA graph;
+ * it makes no allocation at any point. */
 #define ABS_NOALLOC_MAX_SCENARIOS 128
 abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t ld, const double* x,
                               const double* jac_vals, const double* hess_vals,

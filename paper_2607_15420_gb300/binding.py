@@ -123,6 +123,7 @@ EXPORTS = {
                                      C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
     "ipm_solve": (C.c_int, [C.c_void_p, C.POINTER(AbsOptions), C.c_void_p, C.c_void_p, C.POINTER(AbsResult),
                             C.c_void_p, C.c_void_p, C.c_void_p]),
+    "absorber_bound_multipliers": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ipm_solve_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(AbsOptions), C.POINTER(AbsResult),
                                     C.POINTER(C.c_void_p), C.c_void_p]),
     "absorber_create_batched": (C.c_int, [C.POINTER(AbsParams), C.c_void_p, C.POINTER(C.c_int64), C.c_int32,
@@ -341,6 +342,16 @@ class Problem:
         if check:
             self._check(st)
         return res
+
+    def bound_multipliers(self, zl_out=None, zu_out=None, stream=None):
+        """Bound multipliers of the last solve (unscaled problem min d) into the device
+        vectors zl_out, zu_out; returns the host array [z_L(d) per problem, z_U(d) per
+        problem]."""
+        nprob = int(lib().absorber_num_problems(self.h))
+        zd = np.zeros(2 * nprob)
+        self._check(lib().absorber_bound_multipliers(self.h, _ptr(zl_out), _ptr(zu_out), zd.ctypes.data,
+                                                     _stream(stream)))
+        return zd
 
     def last_error(self):
         msg = lib().abs_last_error(self.h)

@@ -285,9 +285,11 @@ PatternTables& pattern() {
 }
 
 bool g_uploaded[64] = {false};
+std::mutex g_upload_mu;   // handles may be created from several host threads
 
 cudaError_t upload_tables(int dev) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_upload_mu);
     if (g_uploaded[dev]) return cudaSuccess;
     PatternTables& T = pattern();
     cudaError_t e;
@@ -422,6 +424,10 @@ struct abs_problem {
     int64_t nlaunch = 0;         // kernels launched (every launch is followed by launch_check)
     float* mlp_x = nullptr;          // learned warm start: network inputs [ld][3] and outputs [ld][440]
     float* mlp_y = nullptr;
+    // bound multipliers of d at the end of the last engine run, per problem, of the scaled
+    // problem, and each problem's objective scaling w (absorber_bound_multipliers)
+    std::vector<double> zLd_last, zUd_last, w_last;
+    bool sol_valid = false;
     abs_problem* base = nullptr;     // expected-value sub-problem(s) for the starting point
     abs_problem* batch = nullptr;    // cached batch handle of ipm_solve_batched (on probs[0])
     std::vector<int64_t> batch_key;  // the sizes it was built for
@@ -1042,22 +1048,30 @@ abs_status upload_feeds(abs_problem* h, const double* feeds, cudaStream_t st) {
     return ABS_OK;
 }
 
+// the device parameter block of a parameter table: the table itself plus the derived
+// fields (logarithms of the liquid scales, enthalpy offsets, scaled temperature bounds);
+// false if a liquid scale is not positive
+bool make_params(const abs_params* p, Params* P) {
+    std::memset(P, 0, sizeof(*P));
+    std::memcpy(P, p, sizeof(abs_params));
+    for (int l = 0; l < 9; ++l) {
+        if (!(p->sx[l] > 0.0)) return false;
+        P->lnsx[l] = std::log(p->sx[l]);
+        P->hL0[l] = p->hL_ref[l] + p->hL_dh[l];
+    }
+    for (int j = 0; j < 4; ++j) P->hV0[j] = p->hV_ref[j] + p->hV_dh[j];
+    P->Tlo_s = p->T_lo / p->sT;
+    P->Thi_s = p->T_hi / p->sT;
+    return true;
+}
+
 abs_status init_handle(abs_problem* h, const abs_params* p, int64_t S) {
     CK(cudaGetDevice(&h->dev));
     CK(upload_tables(h->dev));
     h->S = S;
     h->ld = (S + 31) / 32 * 32;
-    std::memset(&h->P, 0, sizeof(h->P));
-    std::memcpy(&h->P, p, sizeof(abs_params));
     h->aparams = *p;
-    for (int l = 0; l < 9; ++l) {
-        if (!(p->sx[l] > 0.0)) return fail(h, ABS_ERR_ARG, "scales must be positive");
-        h->P.lnsx[l] = std::log(p->sx[l]);
-        h->P.hL0[l] = p->hL_ref[l] + p->hL_dh[l];
-    }
-    for (int j = 0; j < 4; ++j) h->P.hV0[j] = p->hV_ref[j] + p->hV_dh[j];
-    h->P.Tlo_s = p->T_lo / p->sT;
-    h->P.Thi_s = p->T_hi / p->sT;
+    if (!make_params(p, &h->P)) return fail(h, ABS_ERR_ARG, "scales must be positive");
     const PatternTables& T = pattern();
     h->nnzJ = (int)T.jrow.size();
     h->nnzH = (int)T.hrow.size();
@@ -1474,6 +1488,9 @@ static __device__ __align__(256) double g_noalloc_scratch[NA_TOTAL];
 double* g_na_base[64] = {nullptr};
 double g_na_host_part[NA_PART];   // host copy of the partial sums (static, not allocated)
 double g_na_host_ps[NA_PS];       // host source of the per-problem scalars
+// one call at a time in the process: the host arrays above and the device scratch are
+// shared by every call (the lock is held until the call's stream has drained)
+std::mutex g_na_mu;
 
 }  // namespace
 
@@ -1490,6 +1507,7 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
     if (ld != (S + 31) / 32 * 32) return fail(nullptr, ABS_ERR_ARG, "kkt_newton_noalloc: ld must be S rounded up to 32");
     if (!(delta_w >= 0.0)) return fail(nullptr, ABS_ERR_ARG, "kkt_newton_noalloc: delta_w must be >= 0");
     cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(g_na_mu);
     int dev = 0;
     CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(nullptr, ABS_ERR_ARG, "kkt_newton_noalloc: device index out of range");
@@ -1511,16 +1529,7 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
     double* psd = (double*)sing + NA_SING;
     // the problem's constants (derived fields as absorber_create computes them)
     Params P;
-    std::memset(&P, 0, sizeof(P));
-    std::memcpy(&P, p, sizeof(abs_params));
-    for (int l = 0; l < 9; ++l) {
-        if (!(p->sx[l] > 0.0)) return fail(nullptr, ABS_ERR_ARG, "kkt_newton_noalloc: scales must be positive");
-        P.lnsx[l] = std::log(p->sx[l]);
-        P.hL0[l] = p->hL_ref[l] + p->hL_dh[l];
-    }
-    for (int j = 0; j < 4; ++j) P.hV0[j] = p->hV_ref[j] + p->hV_dh[j];
-    P.Tlo_s = p->T_lo / p->sT;
-    P.Thi_s = p->T_hi / p->sT;
+    if (!make_params(p, &P)) return fail(nullptr, ABS_ERR_ARG, "kkt_newton_noalloc: scales must be positive");
     const dim3 g2((unsigned)((S + kThr - 1) / kThr), N_STAGES);
     const dim3 gq((unsigned)((S + QS_SCEN - 1) / QS_SCEN), N_STAGES);
     const int64_t od = (int64_t)NSC * ld;
@@ -1545,11 +1554,10 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
     schur_kernel<<<gq, kThr, 0, st>>>((int)S, ld, bv, hess_vals, sigma, true, pv, qv, rhs_x, sing, part,
                                       SCHUR_DD | SCHUR_RHS, nullptr, nullptr);
     NA_LAUNCHED();
-    double hx[3] = {0.0, 0.0, 0.0};
+    double hx[2] = {0.0, 0.0};   // Sigma_dd and r_d
     const int64_t plane = (int64_t)N_STAGES * ld;
-    CK(cudaMemcpyAsync(&hx[0], x + od, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&hx[1], sigma + od, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&hx[2], rhs_x + od, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hx[0], sigma + od, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hx[1], rhs_x + od, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(g_na_host_part, part, sizeof(double) * NA_K * (size_t)plane, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     double red[NA_K];
@@ -1561,12 +1569,12 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
     }
     if (red[5] != 0.0) return fail(nullptr, ABS_ERR_NUMERIC, "kkt_newton_noalloc: singular stage block");
     // S_d = K_dd + dw + sum q^T (W + Sigma) q + dw sum q^T q ;  dd = (r_d - beta) / S_d
-    const double Kdd = red[4] + hx[1];
+    const double Kdd = red[4] + hx[0];
     const double Sd = Kdd + delta_w + red[0] + delta_w * red[1];
     if (schur_d) *schur_d = Sd;
     if (!(Sd > 0.0)) return fail(nullptr, ABS_ERR_INERTIA, "kkt_newton_noalloc: Schur complement on d is not positive");
     const double beta = red[2] - delta_w * red[3];
-    const double dd = (hx[2] - beta) / Sd;
+    const double dd = (hx[1] - beta) / Sd;
     CK(cudaMemcpyAsync(sol_x + od, &dd, sizeof(double), cudaMemcpyHostToDevice, st));
     dz_kernel<<<gq, kThr, 0, st>>>((int)S, ld, bv, hess_vals, sigma, true, pv, qv, rhs_x, sol_x, gv);
     NA_LAUNCHED();

@@ -172,7 +172,8 @@ def test_learned_warm_start_beats_cold_start(B):
     o = B.default_options()
     cold = prob.ipm_solve(o)
     xw = torch.zeros(prob.n_primal, dtype=torch.float64, device="cuda")
-    warm = B.ipm_solve_learned(prob, net, o, x_out=xw)
+    yw = torch.zeros(prob.n_row, dtype=torch.float64, device="cuda")
+    warm = B.ipm_solve_learned(prob, net, o, x_out=xw, y_out=yw)
     assert cold.status == 0 and warm.status == 0
     assert warm.warm_status == 1, (warm.warm_E0, warm.cold_E0, warm.warm_theta, warm.cold_theta)
     assert warm.E0 <= 1e-8
@@ -188,6 +189,14 @@ def test_learned_warm_start_beats_cold_start(B):
     # the multipliers the solve returns are those of the same optimum
     dmin, _ = checks.minimum_diameter(P, F, prob.from_soa(_host(xw))[0])
     assert abs(warm.d - dmin) <= 1e-8 * dmin
+    # E_0 at the returned point, recomputed from the definitions by the oracle's check
+    zl, zu = torch.zeros_like(xw), torch.zeros_like(xw)
+    zd = prob.bound_multipliers(zl, zu)
+    Z, d = prob.from_soa(_host(xw))
+    lam, _ = prob.from_soa(_host(yw))
+    ZL, _ = prob.from_soa(_host(zl))
+    ZU, _ = prob.from_soa(_host(zu))
+    assert checks.kkt_error(P, F, d, Z, lam, ZL, ZU, zd[0], zd[1], chunk=100) <= 1e-8
 
 
 def test_learned_warm_start_rejects_a_bad_network(B):

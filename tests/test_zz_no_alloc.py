@@ -72,6 +72,45 @@ def test_noalloc_matches_factor_solve_two_calls(B):
         assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("S", [97, 128])
+def test_noalloc_ragged_and_maximum_size(B, S):
+    # a size that is not a multiple of 32 (ragged last warp and block) and the largest
+    # size the static scratch holds (every offset inside it at its limit)
+    import torch
+    prob, x, jac, hes, sig, rx, rc = _case(B, S, 2, 0.01)
+    inert = prob.kkt_factor(x, jac, hes, sig, delta_w=1e-6)
+    ref_x, ref_c = torch.zeros_like(rx), torch.zeros_like(rc)
+    prob.kkt_solve(rx, rc, ref_x, ref_c, max_refine=0)
+    out_x, out_c = torch.full_like(rx, np.nan), torch.full_like(rc, np.nan)
+    sd = B.kkt_newton_noalloc(P, prob.S, prob.ld, x, jac, hes, sig, rx, rc, out_x, out_c, delta_w=1e-6)
+    assert abs(sd - inert.schur_d) <= 1e-12 * abs(inert.schur_d)
+    a = np.concatenate([prob.from_soa(out_x.cpu().numpy())[0].ravel(), [out_x[-1].item()],
+                        prob.from_soa(out_c.cpu().numpy())[0].ravel()])
+    b = np.concatenate([prob.from_soa(ref_x.cpu().numpy())[0].ravel(), [ref_x[-1].item()],
+                        prob.from_soa(ref_c.cpu().numpy())[0].ravel()])
+    assert np.all(np.isfinite(a))
+    assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_noalloc_reports_singular_block_and_negative_schur(B):
+    import torch
+    prob, x, jac, hes, sig, rx, rc = _case(B, 10, 0, 0.0)
+    out_x, out_c = torch.zeros_like(rx), torch.zeros_like(rc)
+    # every Jacobian value of scenario 3 zeroed: its stage blocks are singular
+    js = jac.clone().view(prob.sizes.nnzJ_scen, prob.ld)
+    js[:, 3] = 0.0
+    with pytest.raises(B.AbsorberError) as e:
+        B.kkt_newton_noalloc(P, prob.S, prob.ld, x, js.view(-1), hes, sig, rx, rc, out_x, out_c)
+    assert e.value.status == -7
+    # a barrier diagonal far below zero makes the Schur complement on d negative
+    with pytest.raises(B.AbsorberError) as e:
+        B.kkt_newton_noalloc(P, prob.S, prob.ld, x, jac, hes, sig - 1e12, rx, rc, out_x, out_c)
+    assert e.value.status == -4
+    # the entry still works after both failures
+    sd = B.kkt_newton_noalloc(P, prob.S, prob.ld, x, jac, hes, sig, rx, rc, out_x, out_c, delta_w=1e-6)
+    assert np.isfinite(sd) and sd > 0
+
+
 def test_noalloc_rejects_oversized(B):
     import torch
     S = B.NOALLOC_MAX_SCENARIOS + 1
