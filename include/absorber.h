@@ -207,7 +207,10 @@ typedef struct abs_inertia {
  *              n_singular and by ABS_ERR_NUMERIC instead of regularised).
  *   precision  ABS_PREC_FP64 or ABS_PREC_FP32.
  *   inertia    host, receives the inertia (the call synchronises the stream).
- * The factorization stays in the handle for kkt_solve. */
+ * The factorization stays in the handle for kkt_solve, which reads jac_vals, hess_vals
+ * and diag->sigma again (its products with H and its FP64 refinement): those buffers
+ * are referenced, not copied, and must stay allocated and unchanged until the last
+ * kkt_solve of this factorization. */
 abs_status kkt_factor(abs_problem* h, const double* x, const double* jac_vals,
                       const double* hess_vals, const abs_kkt_diag* diag, int precision,
                       abs_inertia* inertia, abs_stream_t stream);

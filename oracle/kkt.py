@@ -127,6 +127,30 @@ class SchurKKT:
         return X[:, :n], dd, X[:, n:]
 
 
+def kkt_residual(W, sig, J, Jd, Kdd, dw, dc, dz, dd, dl, rz, rd, rc):
+    """r - K x of the bordered block-diagonal system above, by its block rows:
+    z rows (W + Sig + dw I) dz + J^T dl, the d row (K_dd + dw) dd + sum b^T dl and the
+    constraint rows J dz + b dd - dc dl."""
+    ez = rz - (np.einsum("sij,sj->si", W, dz) + (sig + dw) * dz + np.einsum("sri,sr->si", J, dl))
+    ed = rd - ((Kdd + dw) * dd + float(np.sum(Jd * dl)))
+    ec = rc - (np.einsum("sri,si->sr", J, dz) + Jd * dd - dc * dl)
+    return ez, ed, ec
+
+
+def solve_refined(fac, W, sig, J, Jd, Kdd, dw, dc, rz, rd, rc, steps=2):
+    """The Schur-reduced solve followed by `steps` rounds of FP64 iterative refinement
+    on the whole system (residual by kkt_residual, correction by the same factors): the
+    direction the GPU's refined solve is compared with when the KKT matrix is too
+    ill-conditioned for an unrefined backward-stable solve to agree with another to
+    1e-10."""
+    dz, dd, dl = fac.solve(rz, rd, rc)
+    for _ in range(steps):
+        ez, ed, ec = kkt_residual(W, sig, J, Jd, Kdd, dw, dc, dz, dd, dl, rz, rd, rc)
+        cz, cd, cl = fac.solve(ez, ed, ec)
+        dz, dd, dl = dz + cz, dd + cd, dl + cl
+    return dz, dd, dl
+
+
 def monolithic_matrix(W, sig, J, Jd, Kdd, dw, dc):
     """The whole KKT matrix, dense, unknowns ordered [d, (z_s, l_s) for each s]."""
     S, n, _ = W.shape

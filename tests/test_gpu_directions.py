@@ -7,12 +7,16 @@ path's FP64 escalation forced from the host.
 The GPU applies delta_w only to the Schur scalar and to the products with H (the block
 factors of J_s do not depend on it); the oracle factors the whole shifted KKT block by
 dense Bunch-Kaufman LDL^T.  Bound: relative error <= 1e-10 of the whole direction
-(dz, dd, dlambda) after FP64 refinement, the stated tolerance."""
+(dz, dd, dlambda) after FP64 refinement, the stated tolerance.  The oracle's direction is
+its Schur-reduced solve refined twice in FP64 on the whole system (oracle/kkt.py
+solve_refined): at these iterates cond(K) * eps is ~1e-10 to 1e-9, so two unrefined
+backward-stable solves (the oracle's Schur and monolithic ones) already differ by that
+much; refined, the oracle's direction is the system's solution to far below 1e-10."""
 import numpy as np
 import pytest
 
 import absorber_inputs as ai
-from oracle import ipm, model
+from oracle import ipm, kkt
 
 pytestmark = pytest.mark.gpu
 P = ai.PARAMS
@@ -69,11 +73,13 @@ def case600():
 def _check_direction(B, case, dw, prec):
     import torch
     F, solver, st, mu, (C, J, Jd, W, Wdd) = case
-    dZ, dd, dl, _, _, fac = solver.newton_direction(st, mu, C, J, Jd, W, Wdd, dw=dw, dc=0.0)
+    _, _, _, _, _, fac = solver.newton_direction(st, mu, C, J, Jd, W, Wdd, dw=dw, dc=0.0)
     sig, sigd = solver.sigma(st)
     gz, gd = solver.barrier_gradient(st, mu)
     rz = -(gz + np.einsum("src,sr->sc", J, st.lam))
     rd = -(gd + float(np.sum(Jd * st.lam)))
+    Kdd = float(np.sum(Wdd)) + sigd
+    dZ, dd, dl = kkt.solve_refined(fac, W, sig, J, Jd, Kdd, dw, 0.0, rz, rd, -C, steps=2)
     prob = B.Problem(P, F)
     ld = prob.ld
     x = dev(prob.to_soa(st.Z, st.d))
@@ -81,7 +87,9 @@ def _check_direction(B, case, dw, prec):
     jac = torch.zeros(prob.sizes.nnzJ_scen * ld, dtype=torch.float64, device="cuda")
     hes = torch.zeros(prob.sizes.nnzH_scen * ld, dtype=torch.float64, device="cuda")
     prob.eval_grad_jac_hess(x, lm, 1.0, jac=jac, hess=hes)
-    inert = prob.kkt_factor(x, jac, hes, dev(prob.to_soa(sig, sigd)), delta_w=dw, precision=prec)
+    # kkt_solve reads jac, hes and sigma again: they must outlive the factorization
+    sg = dev(prob.to_soa(sig, sigd))
+    inert = prob.kkt_factor(x, jac, hes, sg, delta_w=dw, precision=prec)
     assert inert.n_singular == 0
     assert (inert.n_pos, inert.n_neg, inert.n_zero) == fac.inertia()
     # the Schur scalar with the shift: FP64 to 1e-9; FP32 from FP32 block factors (the
