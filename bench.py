@@ -162,6 +162,49 @@ print(json.dumps(dict(iters=r.iters, seconds=el)))
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def visible_cores():
+    """(nproc as the OS reports it, CPUs this process may run on)."""
+    n = os.cpu_count() or 1
+    try:
+        a = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        a = n
+    return n, a
+
+
+def cpu_baseline_all_cores(workload, per_proc, iters, nproc, timeout=600):
+    """The oracle on every visible core: nproc single-threaded processes at once, process
+    k running `iters` interior-point iterations on its own block of `per_proc` scenarios
+    (scenarios k*per_proc ...) as an independent problem -- the scenario-parallel part
+    of an iteration; the scalar reductions that join the blocks are not timed."""
+    code = """
+import json, sys, time
+sys.path.insert(0, {root!r})
+import absorber_inputs as ai
+from oracle import ipm
+k = int(sys.argv[1])
+F = ai.workload_feeds({wl!r})[:, k * {pp}:(k + 1) * {pp}]
+opt = ipm.Options(max_iter={it}, init="inlet")
+t = time.perf_counter()
+r = ipm.solve(ai.PARAMS, F, opt)
+print(json.dumps(dict(iters=r.iters, seconds=time.perf_counter() - t)))
+""".format(root=ROOT, wl=workload, pp=per_proc, it=iters)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    t0 = time.perf_counter()
+    procs = [subprocess.Popen([sys.executable, "-c", code, str(k)], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                              text=True, env=env) for k in range(nproc)]
+    outs = []
+    for p in procs:
+        o, e = p.communicate(timeout=timeout)
+        if p.returncode != 0:
+            raise RuntimeError(e[-2000:])
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    wall = time.perf_counter() - t0
+    return {"iters": min(o["iters"] for o in outs), "wall_s": wall,
+            "per_process_s": [o["seconds"] for o in outs]}
+
+
 def run_reference(args, S_full):
     """Reference arm: the CPU oracle, timed on the host cores, one bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -184,6 +227,7 @@ def run_reference(args, S_full):
         "config": {"workload": args.workload, "scenarios": S_full, "tol": 1e-8,
                    "step": f"{iters} oracle IPM iterations on a {sample}-scenario sample, scaled by {sample}/{S_full}"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "visible_cores": dict(zip(("nproc", "affinity"), visible_cores())),
                          "sample": f"{iters} IPM iterations on the first {sample} scenarios per step, "
                                    f"per-iteration cost scaled linearly to {S_full} scenarios"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -476,10 +520,21 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample, its = 50, 6
+        nproc, naff = visible_cores()
         rb = cpu_baseline(args.workload, sample, its)
         cpu = {"value": rb["iters"] / rb["seconds"] * (sample / Sx), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "visible_cores": {"nproc": nproc, "affinity": naff},
                "sample": f"{rb['iters']} IPM iterations of the oracle on the first {sample} of the {Sx} "
-                         f"scenarios ({rb['seconds']:.1f} s), per-iteration cost scaled linearly to {Sx}"}
+                         f"scenarios ({rb['seconds']:.1f} s), one thread, per-iteration cost scaled linearly "
+                         f"to {Sx} (extrapolated)"}
+        per = 25
+        ra = cpu_baseline_all_cores(args.workload, per, its, naff)
+        cpu["all_cores"] = {
+            "value": ra["iters"] / ra["wall_s"] * (naff * per / Sx), "unit": UNIT, "cores": naff, "kind": "oracle",
+            "sample": f"{naff} single-threaded oracle processes at once, each {ra['iters']} IPM iterations on its "
+                      f"own block of {per} scenarios ({ra['wall_s']:.1f} s wall for {naff * per} scenarios), "
+                      f"per-iteration cost scaled linearly to {Sx} (extrapolated; the blocks' scalar "
+                      f"reductions are not timed)"}
 
     if rank == 0:
         r0 = results[0]
