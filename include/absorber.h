@@ -290,10 +290,12 @@ typedef struct abs_result {
     int64_t launches;            /* every kernel this library launched during the solve */
     int32_t base_iters;          /* iterations of the expected-value start solve */
     int32_t soc_steps;           /* second-order correction steps taken */
-    int32_t fp64_fallbacks;      /* FP32 iterations refactored in FP64 (refinement stalled) */
+    int32_t fp64_fallbacks;      /* FP32 factors: iterations in which the FP64 refinement
+                                    stalled and the scenarios behind it were refactored in FP64 */
     double base_ms;              /* host time of the expected-value start solve */
     int32_t warm_status;         /* ipm_solve_learned: 1 learned start used, 0 rejected */
-    int32_t reserved;
+    int32_t fp64_scenarios;      /* FP32 factors: scenario factorizations escalated to FP64 in
+                                    total (over the iterations; see fp64_fallbacks) */
     double warm_ms;              /* ipm_solve_learned: host time of prediction + acceptance test */
     double warm_E0, cold_E0;     /* E_0 at the learned start and at the inlet-copy start */
     double warm_theta, cold_theta;  /* constraint violation ||c||_1 at the same two starts */

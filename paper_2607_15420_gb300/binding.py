@@ -82,7 +82,7 @@ class AbsResult(C.Structure):
                 ("phase_ms", C.c_double * 6), ("kernel_ms", C.c_double * 5),
                 ("kernel_launches", C.c_int32 * 5), ("launches", C.c_int64),
                 ("base_iters", C.c_int32), ("soc_steps", C.c_int32), ("fp64_fallbacks", C.c_int32),
-                ("base_ms", C.c_double), ("warm_status", C.c_int32), ("reserved", C.c_int32),
+                ("base_ms", C.c_double), ("warm_status", C.c_int32), ("fp64_scenarios", C.c_int32),
                 ("warm_ms", C.c_double), ("warm_E0", C.c_double), ("cold_E0", C.c_double),
                 ("warm_theta", C.c_double), ("cold_theta", C.c_double), ("tiles", C.c_int32 * 4),
                 ("graph_replays", C.c_int32), ("reserved_res", C.c_int32)]

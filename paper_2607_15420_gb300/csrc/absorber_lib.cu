@@ -342,6 +342,38 @@ cudaError_t upload_tables(int dev) {
 
 }  // namespace
 
+// ---- state of the interior-point method on the device (engine.inc) -----------------------
+namespace {
+// the method's scalar options, passed by value to the control kernels
+struct DevOpt {
+    double tol, mu_init, kappa_eps, kappa_mu, theta_mu, tau_min, s_max, kappa_sigma, bound_push, bound_frac;
+    double gamma_theta, gamma_phi, delta, s_theta, s_phi, eta_phi, gamma_alpha, lam_init_max;
+    double dw0, dw_min, dw_max, kw_minus, kw_plus, kw_plus_bar, kappa_soc, obj_scaling, refine_tol;
+    double dlo, dhi, u_max;
+    int max_iter, max_refine, max_ls, soc_max;
+};
+
+// one problem's state of the method
+struct DState {
+    int status, iters, ls_trials, soc_steps, inertia_corr, refine_steps, fallbacks, esc_scen;
+    int have_theta0, tiny, ftype, soc_taken, ls, nls, nsoc, soc_new, nfilt, stepped;
+    double w, d, zLd, zUd, mu, tau, theta_max, theta_min, dw_last;
+    double E0, inf_pr, inf_du, theta, phi, jtl_d, sld, sud, dd;
+    double a_max, a_z, gphi, dzLd, dzUd, alpha, a_min, a0, th_old, a_soc, sd, ct_coef;
+    double Kdd, dw, Sd, rd, resid;
+};
+
+// state shared by the problems of a run
+struct DGlobal {
+    int k;              // iteration
+    int rk;             // refinement round of the current solve (shared, as the launches are)
+    int esc_any;        // an FP64 escalation took place in this iteration
+    int guard_iter, guard_ls;   // executions of the iteration / line-search loop bodies
+    int pad;
+    long long launches; // kernels of this library launched by graph execution
+};
+}  // namespace
+
 // kernel profiler (options.profile): event pairs around each hot-kernel launch
 struct Prof {
     bool on = false;
@@ -410,16 +442,26 @@ struct abs_problem {
     // that orders it after the caller's stream
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_in = nullptr;
-    int graphs = 1;                  // replay captured launch sequences (options.graphs)
-    struct GraphEntry {
-        const void* ptr[9];
-        int prec, use_w, have_p, autotune, tiles[4];
-        int runs;                    // eager runs so far (capture happens on the second)
-        cudaGraphExec_t exec;
-        int64_t nkern;
+    cudaEvent_t ev_b[2] = {nullptr, nullptr};   // around the expected-value start's run
+    // whole runs of the method captured into CUDA graphs (engine.inc), by configuration
+    struct RunGraph {
+        std::vector<char> key;
+        int eager_runs = 0;          // eager runs of this configuration (capture on the second)
+        cudaGraphExec_t exec = nullptr;
     };
-    std::vector<GraphEntry> gcache;
+    std::vector<RunGraph> rgraphs;
+    std::vector<cudaStream_t> cap;   // capture streams of conditional bodies, by depth
     int64_t graph_replays = 0;
+    // the method's state on the device
+    DState* dst = nullptr;           // [NP]
+    DGlobal* dglob = nullptr;
+    double* filt = nullptr;          // [NP][fcap][2]
+    int fcap = 0;
+    int* esc = nullptr;              // [ld] per-scenario FP64 escalation flags of the iteration
+    int* escn = nullptr;             // [NP] escalated scenarios per problem (reset by the control kernel)
+    int* doff = nullptr;             // [NP + 1] slot offsets of the problems
+    int* hcond = nullptr;            // mapped host memory: conditions of eager runs
+    int* hcond_dev = nullptr;
     int tile[4] = {4, 4, 4, 4};      // warps per block last used: factor, solve, solve x2, solve^T
     int64_t nlaunch = 0;         // kernels launched (every launch is followed by launch_check)
     float* mlp_x = nullptr;          // learned warm start: network inputs [ld][3] and outputs [ld][440]
@@ -554,6 +596,8 @@ abs_status ensure_stream(abs_problem* h) {
     if (h->stream) return ABS_OK;
     CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreate(&h->ev_b[0]));
+    CK(cudaEventCreate(&h->ev_b[1]));
     return ABS_OK;
 }
 
@@ -624,20 +668,22 @@ abs_status reduce(abs_problem* h, cudaStream_t st, int K, const RedOps& ops, int
 }
 
 double RED(const abs_problem* h, int k, int p) { return h->hmap[(size_t)k * h->NP + p]; }
-double DSLOT(const abs_problem* h, int p) { return h->hmap[(size_t)RED_KMAX * h->NP + p]; }
 
 // ---- the KKT machinery (every active problem at once) ----------------------------------
+// factor precision of a KKT system: ABS_PREC_FP64, ABS_PREC_FP32, or mixed -- the FP32
+// stage-block inverses of most scenarios with FP64 LU factors of the scenarios escalated
+// in this iteration (esc flags)
+constexpr int ABS_PREC_MIXED = 2;
+
 struct KKTSys {
-    const double* jac;
-    const double* hes;
-    const double* sig;
-    bool use_w;
-    int prec;
+    const double* jac = nullptr;
+    const double* hes = nullptr;
+    const double* sig = nullptr;
+    bool use_w = true;
+    int prec = ABS_PREC_FP64;
     // set before kkt_factor_core: p = J^-1 rc is solved together with q = J^-1 b (one
     // two-right-hand-side launch) and the first KKT solve with this rc reuses it
     const double* pre_rc = nullptr;
-    std::vector<double> Kdd, A0, Q2, Sd, dw, rd, wdd, d;   // per problem (host)
-    std::vector<int> nsing;
 };
 
 // ---- block-tile autotuner ----------------------------------------------------------------
@@ -716,26 +762,29 @@ abs_status tuned_launch(abs_problem* h, int kind, int es, std::initializer_list<
 }
 
 // factor launch shape: W warps per block.  FP32: stage-block inverses and G by
-// Gauss-Jordan (factor_gj_kernel); FP64: LU factors, row order and G (factor_warp_kernel)
+// Gauss-Jordan (factor_gj_kernel); FP64: LU factors, row order and G (factor_warp_kernel),
+// of the scenarios with mask[s] != 0 only when mask is given
 template <class T, int W>
-void factor_w(abs_problem* h, const double* jac, double pivtol, cudaStream_t st) {
+void factor_w(abs_problem* h, const double* jac, double pivtol, const int* mask, cudaStream_t st) {
     if constexpr (std::is_same<T, float>::value)
-        factor_gj_kernel<W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (float*)h->LU, h->piv,
-                                                            (float*)h->G, h->sing, pivtol);
+        factor_gj_kernel<W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (float*)h->LUp[ABS_PREC_FP32],
+                                                            h->piv, (float*)h->Gp[ABS_PREC_FP32], h->sing, pivtol);
     else if constexpr (factor_fits<T, W>())
-        factor_warp_kernel<T, W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (T*)h->LU, h->piv,
-                                                                (T*)h->G, h->sing, pivtol);
+        factor_warp_kernel<T, W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac,
+                                                                (T*)h->LUp[ABS_PREC_FP64], h->piv,
+                                                                (T*)h->Gp[ABS_PREC_FP64], h->sing, pivtol, mask);
 }
 
 template <class T>
-abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaStream_t st) {
+abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaStream_t st,
+                         const int* mask = nullptr) {
     prof_begin(h, K_FACTOR, st);
     auto go = [&](int w) {
         switch (w) {
-            case 1: factor_w<T, 1>(h, jac, pivtol, st); break;
-            case 2: factor_w<T, 2>(h, jac, pivtol, st); break;
-            case 8: factor_w<T, 8>(h, jac, pivtol, st); break;
-            default: factor_w<T, 4>(h, jac, pivtol, st); break;
+            case 1: factor_w<T, 1>(h, jac, pivtol, mask, st); break;
+            case 2: factor_w<T, 2>(h, jac, pivtol, mask, st); break;
+            case 8: factor_w<T, 8>(h, jac, pivtol, mask, st); break;
+            default: factor_w<T, 4>(h, jac, pivtol, mask, st); break;
         }
         return launch_check(h);
     };
@@ -745,6 +794,8 @@ abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaS
         r = go(h->factor_tile);
     } else if (std::is_same<T, float>::value)
         r = tuned_launch(h, TK_FACTOR, sizeof(T), {1, 2, 4, 8}, WPB_F, go, st);
+    else if (mask)
+        r = go(WPB_F);   // the escalation's masked factorization: the default shape
     else
         r = factor_fits<T, 8>() ? tuned_launch(h, TK_FACTOR, sizeof(T), {1, 2, 4, 8}, WPB_F, go, st)
                                 : tuned_launch(h, TK_FACTOR, sizeof(T), {1, 2, 4}, WPB_F, go, st);
@@ -755,9 +806,9 @@ abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaS
 template <class T, int NR_, int W>
 void solve_w(abs_problem* h, const double* jac, const double* x, const double* r0, const double* r1, double* o0,
              double* o1, cudaStream_t st) {
-    solve_warp_kernel<T, NR_, W, std::is_same<T, float>::value><<<gridw(h, W), 32 * W, 0, st>>>(h->P, (int)h->S, h->ld, view(h), jac,
-                                                                  (const T*)h->LU, h->piv, (const T*)h->G, x, r0, r1,
-                                                                  o0, o1);
+    const int pi = std::is_same<T, float>::value ? ABS_PREC_FP32 : ABS_PREC_FP64;
+    solve_warp_kernel<T, NR_, W, std::is_same<T, float>::value><<<gridw(h, W), 32 * W, 0, st>>>(
+        h->P, (int)h->S, h->ld, view(h), jac, (const T*)h->LUp[pi], h->piv, (const T*)h->Gp[pi], x, r0, r1, o0, o1);
 }
 
 template <class T, int NR_>
@@ -778,8 +829,21 @@ abs_status solve_launch(abs_problem* h, const double* jac, const double* x, cons
     return r;
 }
 
+// mixed factor precision (escalated scenarios FP64, the others FP32), default shape
+template <int NR_>
+abs_status solve_mixed(abs_problem* h, const double* jac, const double* x, const double* r0, const double* r1,
+                       double* o0, double* o1, cudaStream_t st) {
+    prof_begin(h, K_SOLVE, st);
+    solve_mixed_kernel<NR_, WPB_S><<<gridw(h, WPB_S), 32 * WPB_S, 0, st>>>(
+        h->P, (int)h->S, h->ld, view(h), jac, (const float*)h->LUp[ABS_PREC_FP32], (const double*)h->LUp[ABS_PREC_FP64],
+        h->piv, (const float*)h->Gp[ABS_PREC_FP32], (const double*)h->Gp[ABS_PREC_FP64], h->esc, x, r0, r1, o0, o1);
+    prof_end(h, st);
+    return launch_check(h);
+}
+
 abs_status solve_j(abs_problem* h, int prec, const double* jac, const double* x, const double* r0, double* o0,
                    cudaStream_t st) {
+    if (prec == ABS_PREC_MIXED) return solve_mixed<1>(h, jac, x, r0, nullptr, o0, nullptr, st);
     if (prec == ABS_PREC_FP32) return solve_launch<float, 1>(h, jac, x, r0, nullptr, o0, nullptr, st);
     return solve_launch<double, 1>(h, jac, x, r0, nullptr, o0, nullptr, st);
 }
@@ -787,14 +851,16 @@ abs_status solve_j(abs_problem* h, int prec, const double* jac, const double* x,
 // two right-hand sides in one launch (a null r means b = dc/dd)
 abs_status solve_j2(abs_problem* h, int prec, const double* jac, const double* x, const double* r0, const double* r1,
                     double* o0, double* o1, cudaStream_t st) {
+    if (prec == ABS_PREC_MIXED) return solve_mixed<2>(h, jac, x, r0, r1, o0, o1, st);
     if (prec == ABS_PREC_FP32) return solve_launch<float, 2>(h, jac, x, r0, r1, o0, o1, st);
     return solve_launch<double, 2>(h, jac, x, r0, r1, o0, o1, st);
 }
 
 template <class T, int W>
 void solve_t_w(abs_problem* h, const double* jac, const double* g, double* out, cudaStream_t st) {
-    solve_t_warp_kernel<T, W, std::is_same<T, float>::value><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (const T*)h->LU, h->piv,
-                                                               (const T*)h->G, g, out);
+    const int pi = std::is_same<T, float>::value ? ABS_PREC_FP32 : ABS_PREC_FP64;
+    solve_t_warp_kernel<T, W, std::is_same<T, float>::value><<<gridw(h, W), 32 * W, 0, st>>>(
+        (int)h->S, h->ld, view(h), jac, (const T*)h->LUp[pi], h->piv, (const T*)h->Gp[pi], g, out);
 }
 
 template <class T>
@@ -813,23 +879,38 @@ abs_status solve_jt_t(abs_problem* h, const double* jac, const double* g, double
 
 abs_status solve_jt(abs_problem* h, int prec, const double* jac, const double* g, double* out, cudaStream_t st) {
     prof_begin(h, K_SOLVE_T, st);
-    abs_status r = prec == ABS_PREC_FP32 ? solve_jt_t<float>(h, jac, g, out, st) : solve_jt_t<double>(h, jac, g, out, st);
+    abs_status r;
+    if (prec == ABS_PREC_MIXED) {
+        solve_t_mixed_kernel<WPB_S><<<gridw(h, WPB_S), 32 * WPB_S, 0, st>>>(
+            (int)h->S, h->ld, view(h), jac, (const float*)h->LUp[ABS_PREC_FP32], (const double*)h->LUp[ABS_PREC_FP64],
+            h->piv, (const float*)h->Gp[ABS_PREC_FP32], (const double*)h->Gp[ABS_PREC_FP64], h->esc, g, out);
+        r = launch_check(h);
+    } else {
+        r = prec == ABS_PREC_FP32 ? solve_jt_t<float>(h, jac, g, out, st) : solve_jt_t<double>(h, jac, g, out, st);
+    }
     prof_end(h, st);
     return r;
 }
 
-// factor every active problem's J_s, q = J^-1 b and the Schur sums: per problem A0 =
-// sum q^T (W + Sigma) q, Q2 = sum q^T q, wdd = sum of the d-d Hessian entries, nsing.
-// x: primal vector whose d slots hold the problems' d.
-abs_status kkt_factor_core(abs_problem* h, KKTSys& K, const double* x, cudaStream_t st) {
+// factor every active problem's J_s, q = J^-1 b (with p = J^-1 pre_rc when set) and the
+// Schur sums into h->red per problem: [0] A0 = sum q^T (W + Sigma) q, [1] Q2 = sum q^T q,
+// [4] the d-d Hessian entries, [5] singular stage blocks (fetch: also to the host, RED).
+// Mixed precision: FP64 factors of the escalated scenarios only (the others keep their
+// FP32 inverses).  x: primal vector whose d slots hold the problems' d.
+abs_status kkt_factor_core(abs_problem* h, const KKTSys& K, const double* x, cudaStream_t st, bool fetch) {
     abs_status r;
-    if ((r = ensure_factor(h, K.prec)) != ABS_OK) return r;
-    // FP64: a pivot below 1e-14 of the block's largest entry marks the stage block
-    // singular; FP32: only (numerically) zero pivots do -- accuracy is guarded by the FP64
-    // refinement instead, with an FP64 refactorization when it stalls
-    const double pivtol = K.prec == ABS_PREC_FP32 ? 1e-30 : 1e-14;
-    if (K.prec == ABS_PREC_FP32) r = factor_launch<float>(h, K.jac, pivtol, st);
-    else r = factor_launch<double>(h, K.jac, pivtol, st);
+    if (K.prec == ABS_PREC_MIXED) {
+        if ((r = ensure_factor(h, ABS_PREC_FP64)) != ABS_OK) return r;
+        if ((r = ensure_factor(h, ABS_PREC_FP32)) != ABS_OK) return r;
+        r = factor_launch<double>(h, K.jac, 1e-14, st, h->esc);
+    } else {
+        if ((r = ensure_factor(h, K.prec)) != ABS_OK) return r;
+        // FP64: a pivot below 1e-14 of the block's largest entry marks the stage block
+        // singular; FP32: only (numerically) zero pivots do -- accuracy is guarded by the
+        // FP64 refinement instead, with FP64 escalation where it stalls
+        if (K.prec == ABS_PREC_FP32) r = factor_launch<float>(h, K.jac, 1e-30, st);
+        else r = factor_launch<double>(h, K.jac, 1e-14, st);
+    }
     if (r != ABS_OK) return r;
     r = K.pre_rc ? solve_j2(h, K.prec, K.jac, x, K.pre_rc, nullptr, V(h, V_P), V(h, V_Q), st)
                  : solve_j(h, K.prec, K.jac, x, nullptr, V(h, V_Q), st);
@@ -837,22 +918,8 @@ abs_status kkt_factor_core(abs_problem* h, KKTSys& K, const double* x, cudaStrea
     schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, nullptr, V(h, V_Q),
                                              nullptr, h->sing, h->part, SCHUR_DD, V(h, V_HQ), nullptr);
     if ((r = launch_check(h)) != ABS_OK) return r;
-    if ((r = reduce(h, st, 6, make_ops({RSUM, RSUM, RSUM, RSUM, RSUM, RSUM}), PS_ACT, true)) != ABS_OK) return r;
-    const int NP = h->NP;
-    K.A0.assign(NP, 0.0);
-    K.Q2.assign(NP, 0.0);
-    K.wdd.assign(NP, 0.0);
-    K.nsing.assign(NP, 0);
-    for (int p = 0; p < NP; ++p) {
-        K.A0[p] = RED(h, 0, p);
-        K.Q2[p] = RED(h, 1, p);
-        K.wdd[p] = RED(h, 4, p);
-        K.nsing[p] = (int)RED(h, 5, p);
-    }
-    return ABS_OK;
+    return reduce(h, st, 6, make_ops({RSUM, RSUM, RSUM, RSUM, RSUM, RSUM}), PS_ACT, fetch);
 }
-
-double schur_value(const KKTSys& K, int p, double dw) { return K.Kdd[p] + dw + K.A0[p] + dw * K.Q2[p]; }
 
 // one Schur-reduced solve for every active problem: rz (z part), rc -> dz (d slots set),
 // dl.  PS_RD, PS_SD, PS_DW must be on the device.  No host round trip.  have_p: V_P
@@ -862,8 +929,7 @@ abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, 
     abs_status r;
     if (!have_p && (r = solve_j(h, K.prec, K.jac, x, rc, V(h, V_P), st)) != ABS_OK) return r;
     schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q),
-                                             rz, nullptr, h->part, SCHUR_RHS, nullptr,
-                                             V(h, V_T));
+                                             rz, nullptr, h->part, SCHUR_RHS, nullptr, V(h, V_T));
     if ((r = launch_check(h)) != ABS_OK) return r;
     if ((r = reduce(h, st, 4, make_ops({RSUM, RSUM, RSUM, RSUM}), PS_ACT, false)) != ABS_OK) return r;
     finalize_dd_kernel<<<(unsigned)((h->NP + 127) / 128), 128, 0, st>>>(h->ld, view(h), h->red, dz);
@@ -872,119 +938,6 @@ abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, 
                                               V(h, V_HQ), dz, V(h, V_G));
     if ((r = launch_check(h)) != ABS_OK) return r;
     return solve_jt(h, K.prec, K.jac, V(h, V_G), dl, st);
-}
-
-// the same, replayed from a CUDA graph on the engine's stream: the launch sequence
-// (up to 6 kernels, with the tile shapes the autotuner chose) is captured on its second use
-// with a given set of vectors and replayed from then on; the per-problem scalars it
-// depends on are read from device memory at replay time
-abs_status kkt_solve_once(abs_problem* h, const KKTSys& K, const double* x, const double* rz, const double* rc,
-                          double* dz, double* dl, cudaStream_t st, bool have_p = false) {
-    if (!h->graphs || h->prof.on || !h->stream || st != h->stream)
-        return kkt_solve_launches(h, K, x, rz, rc, dz, dl, st, have_p);
-    const void* key[9] = {K.jac, K.hes, K.sig, x, rz, rc, dz, dl, h->LU};
-    abs_problem::GraphEntry* ge = nullptr;
-    for (auto& g : h->gcache)
-        if (std::memcmp(g.ptr, key, sizeof(key)) == 0 && g.prec == K.prec && g.use_w == (int)K.use_w &&
-            g.have_p == (int)have_p && g.autotune == h->autotune &&
-            std::memcmp(g.tiles, h->tile, sizeof(g.tiles)) == 0) {
-            ge = &g;
-            break;
-        }
-    if (!ge) {
-        abs_problem::GraphEntry g{};
-        std::memcpy(g.ptr, key, sizeof(key));
-        g.prec = K.prec;
-        g.use_w = (int)K.use_w;
-        g.have_p = (int)have_p;
-        g.autotune = h->autotune;   // a first eager run under this tuner setting tunes the kinds used
-        std::memcpy(g.tiles, h->tile, sizeof(g.tiles));
-        h->gcache.push_back(g);
-        ge = &h->gcache.back();
-    }
-    if (!ge->exec && ge->runs < 1) {   // first use: eager (tunes the tile shapes if needed)
-        ge->runs++;
-        abs_status r = kkt_solve_launches(h, K, x, rz, rc, dz, dl, st, have_p);
-        std::memcpy(ge->tiles, h->tile, sizeof(ge->tiles));
-        return r;
-    }
-    if (!ge->exec) {
-        const int64_t n0 = h->nlaunch;
-        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        abs_status r = kkt_solve_launches(h, K, x, rz, rc, dz, dl, st, have_p);
-        cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamEndCapture(st, &graph);
-        if (r != ABS_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return r;
-        }
-        if (e != cudaSuccess) return fail(h, ABS_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
-        e = cudaGraphInstantiate(&ge->exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-            ge->exec = nullptr;
-            return fail(h, ABS_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
-        }
-        ge->nkern = h->nlaunch - n0;
-        h->nlaunch = n0;
-    }
-    CK(cudaGraphLaunch(ge->exec, st));
-    h->nlaunch += ge->nkern;
-    h->graph_replays++;
-    return ABS_OK;
-}
-
-// solve with FP64 iterative refinement on the full KKT residual of every active problem.
-// resid (if non-null) receives each problem's final scaled residual.
-abs_status kkt_solve_refined(abs_problem* h, KKTSys& K, const double* x, const double* rz, const double* rc,
-                             double* dz, double* dl, int max_refine, double tol, int* steps,
-                             std::vector<double>* resid, cudaStream_t st) {
-    abs_status r;
-    if ((r = kkt_solve_once(h, K, x, rz, rc, dz, dl, st, K.pre_rc == rc)) != ABS_OK) return r;
-    int k = 0;
-    const int NP = h->NP;
-    if (resid) resid->assign(NP, 0.0);
-    if (max_refine == 0 && !resid) {
-        if (steps) *steps = 0;
-        return ABS_OK;
-    }
-    std::vector<double> rhod(NP, 0.0);
-    // V_G holds r - H dz of the last block-elimination solve; dlast its dl
-    const double* dlast = dl;
-    for (;;) {
-        kkt_residual_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.jac, V(h, V_G), dlast, dz, dl,
-                                                        rz, rc, V(h, V_RHOZ), V(h, V_RHOC), h->part);
-        if ((r = launch_check(h)) != ABS_OK) return r;
-        if ((r = reduce(h, st, 5, make_ops({RMAX, RMAX, RSUM, RMAX, RMAX}), PS_ACT, true, dz + (int64_t)NSC * h->ld)) !=
-            ABS_OK)
-            return r;
-        // the previous correction has run: its right-hand sides may be restored
-        double worst = 0.0;
-        for (int p = 0; p < NP; ++p) {
-            PSV(h, PS_RD, p) = K.rd[p];
-            if (PSV(h, PS_ACT, p) == 0.0) continue;
-            const double dd = DSLOT(h, p);
-            const double b = -h->P.u_max * M_PI * 0.5 * K.d[p];
-            rhod[p] = K.rd[p] - ((K.Kdd[p] + K.dw[p]) * dd + b * RED(h, 2, p));
-            const double rn = std::max(std::max(RED(h, 0, p), RED(h, 1, p)), std::fabs(rhod[p]));
-            const double bn = std::max(std::max(RED(h, 3, p), RED(h, 4, p)), std::fabs(K.rd[p]));
-            const double sc = rn / (bn + 1e-300);
-            if (!(sc == sc)) return fail(h, ABS_ERR_NUMERIC, "NaN in the KKT solve");
-            if (resid) (*resid)[p] = sc;
-            worst = std::max(worst, sc);
-        }
-        if (worst <= tol || k >= max_refine) break;
-        for (int p = 0; p < NP; ++p) PSV(h, PS_RD, p) = rhod[p];
-        if ((r = upload_ps(h, st)) != ABS_OK) return r;
-        if ((r = kkt_solve_once(h, K, x, V(h, V_RHOZ), V(h, V_RHOC), V(h, V_CZ), V(h, V_CL), st)) != ABS_OK) return r;
-        axpy2_kernel<<<gride(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), V(h, V_CZ), dz, V(h, V_CL), dl);
-        if ((r = launch_check(h)) != ABS_OK) return r;
-        dlast = V(h, V_CL);
-        ++k;
-    }
-    if ((r = upload_ps(h, st)) != ABS_OK) return r;   // PS_RD restored
-    if (steps) *steps = k;
-    return ABS_OK;
 }
 
 // the paper's layout (Section "Numerical results"): [d, z_1 .. z_S], z_s = per stage x
@@ -1175,10 +1128,20 @@ void absorber_destroy(abs_problem* h) {
     absorber_destroy(h->base);
     absorber_destroy(h->batch);
     for (auto e : h->prof.pool) cudaEventDestroy(e);
-    for (auto& g : h->gcache)
+    for (auto& g : h->rgraphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto s : h->cap) cudaStreamDestroy(s);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
+    for (auto e : h->ev_b)
+        if (e) cudaEventDestroy(e);
     if (h->stream) cudaStreamDestroy(h->stream);
+    cudaFree(h->dst);
+    cudaFree(h->dglob);
+    cudaFree(h->filt);
+    cudaFree(h->esc);
+    cudaFree(h->escn);
+    cudaFree(h->doff);
+    if (h->hcond) cudaFreeHost(h->hcond);
     cudaFree(h->feed);
     cudaFree(h->pid);
     cudaFree(h->mlp_x);
@@ -1308,97 +1271,6 @@ abs_status absorber_paper_layout(abs_problem* h, const double* x, double* out, a
     cudaStream_t st = (cudaStream_t)stream;
     paper_layout_kernel<<<grid2(h), kThr, 0, st>>>(h->P, (int)h->S, h->ld, x, out);
     return launch_check(h);
-}
-
-abs_status kkt_factor(abs_problem* h, const double* x, const double* jac_vals, const double* hess_vals,
-                      const abs_kkt_diag* diag, int precision, abs_inertia* inertia, abs_stream_t stream) {
-    if (!h || !x || !jac_vals || !hess_vals || !diag || !diag->sigma || !inertia)
-        return fail(h, ABS_ERR_ARG, "bad argument");
-    if (precision != ABS_PREC_FP64 && precision != ABS_PREC_FP32) return fail(h, ABS_ERR_ARG, "bad precision");
-    if (diag->delta_c != 0.0) return fail(h, ABS_ERR_ARG, "delta_c must be 0: J_s is square");
-    if (h->NP != 1) return fail(h, ABS_ERR_ARG, "kkt_factor needs a single-problem handle");
-    cudaStream_t st = (cudaStream_t)stream;
-    abs_status r = ensure_buffers(h);
-    if (r != ABS_OK) return r;
-    PSV(h, PS_ACT, 0) = 1.0;
-    PSV(h, PS_DW, 0) = diag->delta_w;
-    if ((r = upload_ps(h, st)) != ABS_OK) return r;
-    KKTSys K;
-    K.jac = jac_vals;
-    K.hes = hess_vals;
-    K.sig = diag->sigma;
-    K.use_w = true;
-    K.prec = precision;
-    double hx[2] = {0.0, 0.0};
-    CK(cudaMemcpyAsync(&hx[0], x + (int64_t)NSC * h->ld, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&hx[1], diag->sigma + (int64_t)NSC * h->ld, sizeof(double), cudaMemcpyDeviceToHost, st));
-    if ((r = sync(h, st)) != ABS_OK) return r;
-    if ((r = kkt_factor_core(h, K, x, st)) != ABS_OK) return r;
-    const double Kdd = K.wdd[0] + hx[1];
-    const double Sd = Kdd + diag->delta_w + K.A0[0] + diag->delta_w * K.Q2[0];
-    const int64_t nb = (int64_t)NSC * h->S;
-    inertia->n_pos = nb + (Sd > 0 ? 1 : 0);
-    inertia->n_neg = nb + (Sd < 0 ? 1 : 0);
-    inertia->n_zero = (Sd == 0 ? 1 : 0);
-    inertia->schur_d = Sd;
-    inertia->n_singular = K.nsing[0];
-    h->fac.valid = K.nsing[0] == 0;
-    h->fac.prec = precision;
-    h->fac.jac = jac_vals;
-    h->fac.hes = hess_vals;
-    h->fac.sig = diag->sigma;
-    h->fac.d = hx[0];
-    h->fac.dw = diag->delta_w;
-    h->fac.Kdd = Kdd;
-    h->fac.A0 = K.A0[0];
-    h->fac.Q2 = K.Q2[0];
-    h->fac.Sd = Sd;
-    if (K.nsing[0]) return fail(h, ABS_ERR_NUMERIC, "singular stage block in the constraint Jacobian");
-    return ABS_OK;
-}
-
-abs_status kkt_solve(abs_problem* h, const double* rhs_x, const double* rhs_c, double* sol_x, double* sol_c,
-                     int max_refine, double refine_tol, abs_solve_info* info, abs_stream_t stream) {
-    if (!h || !rhs_x || !rhs_c || !sol_x || !sol_c || max_refine < 0) return fail(h, ABS_ERR_ARG, "bad argument");
-    if (!h->fac.valid) return fail(h, ABS_ERR_ARG, "no valid factorization (call kkt_factor)");
-    cudaStream_t st = (cudaStream_t)stream;
-    abs_status r;
-    KKTSys K;
-    K.jac = h->fac.jac;
-    K.hes = h->fac.hes;
-    K.sig = h->fac.sig;
-    K.use_w = true;
-    K.prec = h->fac.prec;
-    K.Kdd = {h->fac.Kdd};
-    K.A0 = {h->fac.A0};
-    K.Q2 = {h->fac.Q2};
-    K.Sd = {h->fac.Sd};
-    K.dw = {h->fac.dw};
-    K.d = {h->fac.d};
-    double rd = 0.0;
-    CK(cudaMemcpyAsync(&rd, rhs_x + (int64_t)NSC * h->ld, sizeof(double), cudaMemcpyDeviceToHost, st));
-    if ((r = sync(h, st)) != ABS_OK) return r;
-    K.rd = {rd};
-    ensure_factor(h, K.prec);
-    PSV(h, PS_ACT, 0) = 1.0;
-    PSV(h, PS_DW, 0) = K.dw[0];
-    PSV(h, PS_SD, 0) = K.Sd[0];
-    PSV(h, PS_RD, 0) = rd;
-    if ((r = upload_ps(h, st)) != ABS_OK) return r;
-    // the solves read b = dc/dd from a primal vector's d slot
-    double* xd = V(h, V_ONE);
-    CK(cudaMemcpyAsync(xd + (int64_t)NSC * h->ld, &K.d[0], sizeof(double), cudaMemcpyHostToDevice, st));
-    int steps = 0;
-    std::vector<double> resid;
-    r = kkt_solve_refined(h, K, xd, rhs_x, rhs_c, sol_x, sol_c, max_refine, refine_tol, &steps,
-                          (info || max_refine > 0) ? &resid : nullptr, st);
-    if (r != ABS_OK) return r;
-    CK(cudaStreamSynchronize(st));
-    if (info) {
-        info->refine_steps = steps;
-        info->residual = resid.empty() ? 0.0 : resid[0];
-    }
-    return ABS_OK;
 }
 
 }  // extern "C"

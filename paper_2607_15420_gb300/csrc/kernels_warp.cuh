@@ -226,11 +226,14 @@ __device__ inline T assemble_stage(int n, int64_t ld, int s, int lane, const dou
     return (T)pivtol * key_value(kmax, T(0));
 }
 
+// mask (optional): only scenarios s with mask[s] != 0 are factored (the FP64 escalation
+// of scenarios whose FP32 refinement stalled); the others keep their factors
 template <class T, int WPB = WPB_F>
 __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld, const BView b,
                                                                  const double* __restrict__ jac, T* __restrict__ LU,
                                                                  unsigned char* __restrict__ piv, T* __restrict__ G,
-                                                                 int* __restrict__ sing, double pivtol) {
+                                                                 int* __restrict__ sing, double pivtol,
+                                                                 const int* __restrict__ mask = nullptr) {
     __shared__ T sA[WPB][NV][PADA];
     __shared__ T sG[WPB][NV][NABV];
     __shared__ LaneTables lt;
@@ -239,6 +242,7 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
     const int s = blockIdx.x * WPB + warp;
     // whole warps leave together; no block-level barriers below
     if (live_prob(b, s, S, PS_ACT) < 0) return;
+    if (mask && mask[s] == 0) return;
     T(*A)[PADA] = sA[warp];
     T(*Gp)[NABV] = sG[warp];
     int singular = 0;
@@ -623,20 +627,15 @@ struct CouplingFetch {
 // J_s x = r (NRHS right-hand sides; a null r[k] means b = dc/dd), one warp per scenario.
 // INV (FP32 only): LU holds the stage-block inverses of factor_gj_kernel and each block
 // solve is a matrix-vector product; otherwise LU factors and row order.
-template <class T, int NRHS, int WPB = WPB_S, bool INV = false>
-__global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, int S, int64_t ld, const BView b,
-                                                                const double* __restrict__ jac, const T* __restrict__ LU,
-                                                                const unsigned char* __restrict__ piv,
-                                                                const T* __restrict__ G, const double* x,
-                                                                const double* r0, const double* r1, double* o0,
-                                                                double* o1) {
+// the block solves of scenario s (problem pr) by its warp; A: the warp's shared-memory
+// staging block for LU factors (unused with INV)
+template <class T, int NRHS, bool INV>
+__device__ __forceinline__ void solve_warp_body(const Params& P, int s, int pr, int lane, int64_t ld,
+                                                const double* __restrict__ jac, const T* __restrict__ LU,
+                                                const unsigned char* __restrict__ piv, const T* __restrict__ G,
+                                                const double* x, const double* r0, const double* r1, double* o0,
+                                                double* o1, T (*A)[PADL]) {
     static_assert(!INV || sizeof(T) == 4, "stage-block inverses are FP32");
-    __shared__ T sL[INV ? 1 : WPB][NV][PADL];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s = blockIdx.x * WPB + warp;
-    const int pr = live_prob(b, s, S, PS_ACT);
-    if (pr < 0) return;
-    T(*A)[PADL] = sL[INV ? 0 : warp];
     int perm = lane, ipos = lane;
     const double* rr[2] = {r0, r1};
     double* oo[2] = {o0, o1};
@@ -727,6 +726,43 @@ __global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, in
     }
 }
 
+template <class T, int NRHS, int WPB = WPB_S, bool INV = false>
+__global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, int S, int64_t ld, const BView b,
+                                                                const double* __restrict__ jac, const T* __restrict__ LU,
+                                                                const unsigned char* __restrict__ piv,
+                                                                const T* __restrict__ G, const double* x,
+                                                                const double* r0, const double* r1, double* o0,
+                                                                double* o1) {
+    __shared__ T sL[INV ? 1 : WPB][NV][PADL];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = blockIdx.x * WPB + warp;
+    const int pr = live_prob(b, s, S, PS_ACT);
+    if (pr < 0) return;
+    solve_warp_body<T, NRHS, INV>(P, s, pr, lane, ld, jac, LU, piv, G, x, r0, r1, o0, o1, sL[INV ? 0 : warp]);
+}
+
+// the same with factors of mixed precision: scenarios with esc[s] != 0 use their FP64 LU
+// factors (escalated), the others their FP32 stage-block inverses
+template <int NRHS, int WPB = WPB_S>
+__global__ void __launch_bounds__(32 * WPB) solve_mixed_kernel(const Params P, int S, int64_t ld, const BView b,
+                                                                 const double* __restrict__ jac,
+                                                                 const float* __restrict__ AI,
+                                                                 const double* __restrict__ LU,
+                                                                 const unsigned char* __restrict__ piv,
+                                                                 const float* __restrict__ G32,
+                                                                 const double* __restrict__ G64,
+                                                                 const int* __restrict__ esc, const double* x,
+                                                                 const double* r0, const double* r1, double* o0,
+                                                                 double* o1) {
+    __shared__ double sL[WPB][NV][PADL];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = blockIdx.x * WPB + warp;
+    const int pr = live_prob(b, s, S, PS_ACT);
+    if (pr < 0) return;
+    if (esc[s]) solve_warp_body<double, NRHS, false>(P, s, pr, lane, ld, jac, LU, piv, G64, x, r0, r1, o0, o1, sL[warp]);
+    else solve_warp_body<float, NRHS, true>(P, s, pr, lane, ld, jac, AI, piv, G32, x, r0, r1, o0, o1, nullptr);
+}
+
 // stage unknown j -> its index among the 11 stream-from-above unknowns (-1: none)
 __host__ __device__ constexpr int abv_index(int j) { return j < 9 ? j : (j == LL ? 9 : (j == LT ? 10 : -1)); }
 
@@ -738,19 +774,12 @@ __host__ __device__ constexpr int abv_index(int j) { return j < 9 ? j : (j == LL
 //   backward  v_9 = At_9^-T w_9,  v_n = At_n^-T (w_n - C_{n+1}^T v_{n+1})
 // one transposed block solve per stage.
 // INV (FP32 only): LU holds the stage-block inverses (see solve_warp_kernel).
-template <class T, int WPB = WPB_S, bool INV = false>
-__global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t ld, const BView b,
-                                                                const double* __restrict__ jac,
-                                                                const T* __restrict__ LU,
-                                                                const unsigned char* __restrict__ piv,
-                                                                const T* __restrict__ G,
-                                                                const double* __restrict__ g, double* out) {
+template <class T, bool INV>
+__device__ __forceinline__ void solve_t_warp_body(int s, int lane, int64_t ld, const double* __restrict__ jac,
+                                                  const T* __restrict__ LU, const unsigned char* __restrict__ piv,
+                                                  const T* __restrict__ G, const double* __restrict__ g, double* out,
+                                                  T (*A)[PADL]) {
     static_assert(!INV || sizeof(T) == 4, "stage-block inverses are FP32");
-    __shared__ T sL[INV ? 1 : WPB][NV][PADL];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s = blockIdx.x * WPB + warp;
-    if (live_prob(b, s, S, PS_ACT) < 0) return;
-    T(*A)[PADL] = sL[INV ? 0 : warp];
     int perm = lane, ipos = lane;
     const bool row = lane < NV;
     const int my_abv = abv_index(lane);   // lane j takes the product of column abv_index(j)
@@ -815,6 +844,39 @@ __global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t l
         if (row) out[(int64_t)(NR * n + lane) * ld + s] = (double)v;
         __syncwarp();
     }
+}
+
+template <class T, int WPB = WPB_S, bool INV = false>
+__global__ void __launch_bounds__(32 * WPB) solve_t_warp_kernel(int S, int64_t ld, const BView b,
+                                                                const double* __restrict__ jac,
+                                                                const T* __restrict__ LU,
+                                                                const unsigned char* __restrict__ piv,
+                                                                const T* __restrict__ G,
+                                                                const double* __restrict__ g, double* out) {
+    __shared__ T sL[INV ? 1 : WPB][NV][PADL];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = blockIdx.x * WPB + warp;
+    if (live_prob(b, s, S, PS_ACT) < 0) return;
+    solve_t_warp_body<T, INV>(s, lane, ld, jac, LU, piv, G, g, out, sL[INV ? 0 : warp]);
+}
+
+// mixed precision (see solve_mixed_kernel)
+template <int WPB = WPB_S>
+__global__ void __launch_bounds__(32 * WPB) solve_t_mixed_kernel(int S, int64_t ld, const BView b,
+                                                                   const double* __restrict__ jac,
+                                                                   const float* __restrict__ AI,
+                                                                   const double* __restrict__ LU,
+                                                                   const unsigned char* __restrict__ piv,
+                                                                   const float* __restrict__ G32,
+                                                                   const double* __restrict__ G64,
+                                                                   const int* __restrict__ esc,
+                                                                   const double* __restrict__ g, double* out) {
+    __shared__ double sL[WPB][NV][PADL];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int s = blockIdx.x * WPB + warp;
+    if (live_prob(b, s, S, PS_ACT) < 0) return;
+    if (esc[s]) solve_t_warp_body<double, false>(s, lane, ld, jac, LU, piv, G64, g, out, sL[warp]);
+    else solve_t_warp_body<float, true>(s, lane, ld, jac, AI, piv, G32, g, out, nullptr);
 }
 
 }  // namespace absorber

@@ -142,22 +142,34 @@ def test_autotuned_tiles_give_identical_results(B):
     assert outs[2][3][0] in (1, 2, 4, 8)
 
 
-def test_graph_replay_gives_identical_results(B):
-    # the Schur-reduced KKT solve replayed from a captured CUDA graph runs the same
-    # kernels with the same arguments: the solve is the same bit for bit
+@pytest.mark.parametrize("prec", [0, 1])
+def test_graph_replay_gives_identical_results(B, prec):
+    # a whole solve replayed from its captured CUDA graph (conditional nodes for the
+    # iteration, refinement and line-search loops; the decisions taken by the control
+    # kernels on the device) runs the same kernels with the same arguments as the eager
+    # run, whose conditions the host reads back: the same solve bit for bit, the same
+    # number of kernel launches, one graph launch per solve (the expected-value start's
+    # run is a second one)
     import torch
     F = ai.make_feeds(300, 1)
     prob = B.Problem(P, F)
     outs = []
-    for graphs in (0, 1):
+    for graphs in (0, 1, 1, 1):
         x = torch.zeros(prob.n_primal, dtype=torch.float64, device="cuda")
-        o = B.default_options(precision=1, max_refine=8, graphs=graphs)
+        o = B.default_options(precision=prec, max_refine=(8 if prec else 0), graphs=graphs)
         r = prob.ipm_solve(o, x_out=x)
         assert r.status == 0
-        outs.append((r.iters, r.d, _host(x), r.graph_replays))
-    assert outs[0][3] == 0 and outs[1][3] > outs[1][0]
-    assert outs[0][0] == outs[1][0] and outs[0][1] == outs[1][1]
-    assert np.array_equal(outs[0][2], outs[1][2])
+        outs.append((r.iters, r.d, _host(x), r.graph_replays, r.launches, r.base_iters))
+    eager = outs[0]
+    assert eager[3] == 0
+    assert outs[1][3] == 0                       # the first run of a configuration is eager
+    for o in outs[2:]:
+        assert o[3] == 2                         # expected-value start + the solve
+        assert o[0] == eager[0] and o[1] == eager[1] and o[5] == eager[5]
+        assert np.array_equal(o[2], eager[2])
+        # launches counted on the device equal the host's count of an eager run (the
+        # very first solve also times the tile candidates: compare with the second)
+        assert o[4] == outs[1][4], (o[4], outs[1][4])
 
 
 @pytest.mark.parametrize("S", [37, 600])
