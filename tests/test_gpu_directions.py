@@ -139,3 +139,22 @@ def test_forced_fp64_escalation_s10(B):
     assert abs(res.d - r64.d) <= 1e-6 * r64.d
     Z, d = prob.from_soa(host(x))
     assert np.all(np.isfinite(Z)) and d == res.d
+
+
+def test_partial_per_scenario_escalation_s600(B):
+    # FP32 factors with one refinement round and a 1e-9 target: in some iterations the
+    # round leaves a few scenarios' rows above the target; only those scenarios are
+    # refactored in FP64 (mixed-precision block solves for the rest of the iteration), and
+    # the solve reaches the FP64 path's optimum
+    F = ai.make_feeds(600, 1)
+    r64 = B.Problem(P, F).ipm_solve(B.default_options())
+    assert r64.status == 0
+    prob = B.Problem(P, F)
+    res = prob.ipm_solve(B.default_options(precision=1, max_refine=1, refine_tol=1e-9))
+    assert res.status == 0 and res.E0 <= 1e-8
+    assert res.fp64_fallbacks > 0
+    assert 0 < res.fp64_scenarios < 0.25 * prob.S * res.fp64_fallbacks, (res.fp64_scenarios, res.fp64_fallbacks)
+    assert abs(res.d - r64.d) <= 1e-6 * r64.d
+    # with the default refinement (8 rounds to 1e-10) nothing escalates on this workload
+    r8 = prob.ipm_solve(B.default_options(precision=1, max_refine=8))
+    assert r8.status == 0 and r8.fp64_scenarios == 0 and r8.fp64_fallbacks == 0
