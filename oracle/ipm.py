@@ -22,8 +22,12 @@ solver family the paper's MadNLP belongs to), with that paper's default constant
   * second-order corrections (their Section 2.4): when the first trial point is rejected
     and increases theta, up to p_max = 4 corrected steps from the same factorization with
     right-hand side c_soc = alpha c(x) + c(x + alpha dx), accepted by the same tests.
-Not included (as in the GPU path): the watchdog and the feasibility-restoration phase; a
-line search that falls below alpha_min stops with status "linesearch".
+  * feasibility restoration (their Section 3.3) when the line search falls below alpha_min:
+    the failed iterate's entry joins the filter, then damped Newton steps on the square
+    constraint system with d fixed (IPM.restoration) until the point is acceptable to the
+    filter with theta reduced by the factor 1 - gamma_theta; a restoration that fails
+    stops the solve with status "linesearch".
+Not included (as in the GPU path): the watchdog.
 
 Starting point (the paper says only that all configurations used the same one): for
 S > 1 the stage states of the expected-value problem's solution (one scenario with the
@@ -76,6 +80,7 @@ class Options:
     max_ls: int = 60
     soc_max: int = 4
     kappa_soc: float = 0.99
+    resto_max: int = 20                # feasibility restoration iterations (0: none)
     obj_scaling: float | None = None   # None: the number of scenarios S
     init: str = "basecase"             # "basecase" (S > 1) or "inlet"
     verbose: bool = False
@@ -290,6 +295,39 @@ class IPM:
             st.lam = lam
         return st
 
+    def restoration(self, st, mu, tau, filt, theta_k):
+        """Feasibility restoration (Wachter & Biegler 2006, Section 3.3) for the square
+        constraint system of problem (10): with d fixed, every scenario's c_s(z_s) = 0 is
+        220 equations in its 220 unknowns (J_s square), so the phase takes damped Newton
+        steps dz_s = -J_s^{-1} c_s, cut by the fraction to the boundary (tau) and halved
+        until ||c||_1 decreases (Armijo, 1e-4).  It returns the first point whose theta is
+        at most (1 - gamma_theta) theta_k and which the filter (augmented with the failed
+        iterate's entry before the phase) accepts; None after resto_max steps."""
+        pr, opt = self.pr, self.opt
+        Z = st.Z.copy()
+        d = st.d
+        C = model.residuals(pr.P, pr.F, Z, d)
+        theta = float(np.abs(C).sum())
+        for _ in range(opt.resto_max):
+            _, J, _, _, _ = model.derivatives(pr.P, pr.F, Z, d, np.zeros_like(Z), rows_only=True)
+            dZ = np.stack([-np.linalg.solve(J[s], C[s]) for s in range(pr.S)])
+            a = fraction_to_boundary(pr, Z, dZ, pr.hasL, pr.lo, pr.hasU, pr.hi, tau)
+            while True:
+                Zt = Z + a * dZ
+                Ct = model.residuals(pr.P, pr.F, Zt, d)
+                th_t = float(np.abs(Ct).sum())
+                if np.isfinite(th_t) and th_t <= (1.0 - 1e-4 * a) * theta:
+                    break
+                a *= 0.5
+                if a < 1e-10:
+                    return None
+            Z, C, theta = Zt, Ct, th_t
+            if theta <= (1.0 - opt.gamma_theta) * theta_k:
+                ph = barrier_phi(pr, Z, d, mu)
+                if all(not (theta >= tf and ph >= pf) for (tf, pf) in filt):
+                    return Z
+        return None
+
     def state_from_result(self, r):
         """The solver's internal iterate (multipliers of the scaled problem) for a Result."""
         w = self.pr.w
@@ -461,8 +499,20 @@ class IPM:
                     if alpha < a_min:
                         break
             if not accepted:
-                status = "linesearch"
-                break
+                # feasibility restoration: the filter keeps the failed iterate's entry
+                filt.append(((1 - opt.gamma_theta) * theta, phi - opt.gamma_phi * theta))
+                Zr = self.restoration(st, mu, tau, filt, theta) if opt.resto_max > 0 else None
+                if Zr is None:
+                    status = "linesearch"
+                    break
+                hist.append(dict(iter=k, mu=mu, E0=E0, theta=theta, alpha=0.0, alpha_z=0.0,
+                                 dw=dw, dc=dc, ls=n_ls, soc=n_soc, d=st.d, resto=True))
+                st.Z = Zr
+                sl, su = pr.sl(st.Z), pr.su(st.Z)
+                ks = opt.kappa_sigma
+                st.zL = np.where(pr.hasL, np.clip(st.zL, mu / (ks * sl), ks * mu / sl), 0.0)
+                st.zU = np.where(pr.hasU, np.clip(st.zU, mu / (ks * su), ks * mu / su), 0.0)
+                continue
             if not ftype and not tiny:
                 filt.append(((1 - opt.gamma_theta) * theta, phi - opt.gamma_phi * theta))
             hist.append(dict(iter=k, mu=mu, E0=E0, theta=theta, alpha=alpha, alpha_z=a_z,

@@ -102,3 +102,40 @@ def test_bruteforce_diameter_sweep(s10):
     assert feas[first:].all() and not feas[:first].any()
     # ... and the smallest feasible grid point brackets the optimum
     assert grid[first - 1] < r.d <= grid[first]
+
+
+def test_feasibility_restoration_rescues_a_stalled_line_search():
+    # single-scenario problems of the training distribution with the objective unscaled
+    # (w = 1) from the inlet-copy start: on this one the line search falls below alpha_min
+    # after 21 iterations; restoration (Newton on the square constraint system, d fixed)
+    # returns a point the filter accepts and the solve converges to the optimum that the
+    # definitions fix
+    F = ai.make_feeds(40, 7, stream=3)[:, 32:33]
+    r0 = ipm.solve(P, F, ipm.Options(obj_scaling=1.0, init="inlet", resto_max=0))
+    assert r0.status == "linesearch"
+    r = ipm.solve(P, F, ipm.Options(obj_scaling=1.0, init="inlet"))
+    assert sum(1 for h in r.history if h.get("resto")) >= 1
+    _check_solution(F, r)
+    # the restored point reduced the infeasibility of the failed iterate
+    k = next(i for i, h in enumerate(r.history) if h.get("resto"))
+    assert r.history[k + 1]["theta"] <= (1 - 1e-5) * r.history[k]["theta"]
+    # the optimum does not depend on the objective's scaling: w = 100 reaches it directly
+    rs = ipm.solve(P, F, ipm.Options(obj_scaling=100.0, init="inlet"))
+    assert rs.status == "ok" and abs(rs.d - r.d) <= 1e-7 * r.d
+
+
+def test_restoration_reduces_theta_inside_the_bounds():
+    # the restoration phase itself, from the failed iterate of the case above: the point
+    # it returns has a smaller ||c||_1 by the required factor and stays inside the bounds
+    F = ai.make_feeds(40, 7, stream=3)[:, 32:33]
+    solver = ipm.IPM(P, F, ipm.Options(obj_scaling=1.0, init="inlet", resto_max=0, max_iter=21))
+    r = solver.solve()
+    st = solver.state_from_result(r)
+    th0 = float(np.abs(model.residuals(P, F, st.Z, st.d)).sum())
+    Zr = ipm.IPM(P, F, ipm.Options(obj_scaling=1.0, init="inlet")).restoration(st, r.mu, max(0.99, 1 - r.mu), [],
+                                                                               th0)
+    assert Zr is not None
+    thr = float(np.abs(model.residuals(P, F, Zr, st.d)).sum())
+    assert thr <= (1 - 1e-5) * th0
+    lo, hi, _, _ = model.bounds(P, 1)
+    assert np.all(Zr[np.isfinite(lo)] > lo[np.isfinite(lo)]) and np.all(Zr[np.isfinite(hi)] < hi[np.isfinite(hi)])
