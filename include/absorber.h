@@ -58,7 +58,7 @@ typedef int abs_status;
 #define ABS_ERR_CUDA       -2   /* a CUDA runtime call failed */
 #define ABS_ERR_OOM        -3   /* device allocation failed */
 #define ABS_ERR_INERTIA    -4   /* inertia correction exceeded delta_w_max */
-#define ABS_ERR_LINESEARCH -5   /* step size fell below alpha_min (no restoration) */
+#define ABS_ERR_LINESEARCH -5   /* step size fell below alpha_min and restoration failed */
 #define ABS_ERR_MAXITER    -6   /* iteration limit reached */
 #define ABS_ERR_NUMERIC    -7   /* NaN/Inf, or a singular stage Jacobian block */
 #define ABS_ERR_TIMEOUT    -8   /* a device-side wait gave up */
@@ -267,6 +267,11 @@ typedef struct abs_options {
     int32_t factor_tile;   /* FP32 factor launches only: 0 shape from autotune; 1, 2, 4, 8:
                               that many warps (scenarios) per block (identical results);
                               other values are rejected with ABS_ERR_ARG */
+    int32_t resto_max;     /* feasibility restoration (Wachter & Biegler 2006, Section 3.3)
+                              when the line search fails: at most this many damped Newton
+                              steps on the square constraint system with d fixed, until the
+                              filter accepts a point with theta reduced by 1 - gamma_theta;
+                              0 disables it (the solve then stops with ABS_ERR_LINESEARCH) */
 } abs_options;
 
 void abs_default_options(abs_options* o);
@@ -302,8 +307,9 @@ typedef struct abs_result {
     int32_t tiles[4];            /* warps per block last used: factor (+16: the FP32
                                     register-resident variant), solve (1 and 2 right-hand
                                     sides), transposed solve */
-    int32_t graph_replays;       /* KKT solves replayed from captured graphs */
-    int32_t reserved_res;
+    int32_t graph_replays;       /* graph launches of the solve (whole runs replayed from
+                                    captured CUDA graphs) */
+    int32_t resto_phases;        /* feasibility restoration phases entered */
 } abs_result;
 
 /* Diagnostic: measured throughput of dependent-free fused multiply-adds on the current

@@ -71,7 +71,7 @@ class AbsOptions(C.Structure):
                 ("init", C.c_int32), ("soc_max", C.c_int32), ("kappa_soc", C.c_double),
                 ("obj_scaling", C.c_double), ("warm_mu_init", C.c_double), ("warm_bound_push", C.c_double),
                 ("warm_multipliers", C.c_int32), ("autotune", C.c_int32), ("graphs", C.c_int32),
-                ("factor_tile", C.c_int32)]
+                ("factor_tile", C.c_int32), ("resto_max", C.c_int32)]
 
 
 class AbsResult(C.Structure):
@@ -85,7 +85,7 @@ class AbsResult(C.Structure):
                 ("base_ms", C.c_double), ("warm_status", C.c_int32), ("fp64_scenarios", C.c_int32),
                 ("warm_ms", C.c_double), ("warm_E0", C.c_double), ("cold_E0", C.c_double),
                 ("warm_theta", C.c_double), ("cold_theta", C.c_double), ("tiles", C.c_int32 * 4),
-                ("graph_replays", C.c_int32), ("reserved_res", C.c_int32)]
+                ("graph_replays", C.c_int32), ("resto_phases", C.c_int32)]
 
 
 class AbsTrainOptions(C.Structure):

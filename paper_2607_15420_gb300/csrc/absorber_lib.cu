@@ -350,14 +350,16 @@ struct DevOpt {
     double gamma_theta, gamma_phi, delta, s_theta, s_phi, eta_phi, gamma_alpha, lam_init_max;
     double dw0, dw_min, dw_max, kw_minus, kw_plus, kw_plus_bar, kappa_soc, obj_scaling, refine_tol;
     double dlo, dhi, u_max;
-    int max_iter, max_refine, max_ls, soc_max;
+    int max_iter, max_refine, max_ls, soc_max, resto_max;
 };
 
 // one problem's state of the method
 struct DState {
     int status, iters, ls_trials, soc_steps, inertia_corr, refine_steps, fallbacks, esc_scen;
     int have_theta0, tiny, ftype, soc_taken, ls, nls, nsoc, soc_new, nfilt, stepped;
+    int resto, resto_it, resto_bt, resto_phases, resto_now;   // feasibility restoration state
     double w, d, zLd, zUd, mu, tau, theta_max, theta_min, dw_last;
+    double theta_k, ra, th_r, blog_r;              // restoration: entry theta, step, trial theta / logs
     double E0, inf_pr, inf_du, theta, phi, jtl_d, sld, sud, dd;
     double a_max, a_z, gphi, dzLd, dzUd, alpha, a_min, a0, th_old, a_soc, sd, ct_coef;
     double Kdd, dw, Sd, rd, resid;
@@ -1085,6 +1087,7 @@ void abs_default_options(abs_options* o) {
     o->warm_bound_push = 1e-8;
     o->autotune = 1;
     o->graphs = 1;
+    o->resto_max = 20;
 }
 
 abs_status absorber_create(const abs_params* p, const double* feeds, const double* prob, int64_t S,

@@ -164,11 +164,14 @@ def test_injected_inertia_failure(B):
 
 def test_injected_linesearch_failure(B):
     # from the inlet-copy start of this one-scenario problem the first full trial step of
-    # iteration 0 is rejected (the oracle backtracks there too); with one trial allowed and
-    # no second-order correction the line search fails: ABS_ERR_LINESEARCH
+    # iteration 0 is rejected (the oracle backtracks there too); with one trial allowed, no
+    # second-order correction and no restoration the line search fails: ABS_ERR_LINESEARCH
     F = ai.make_feeds(1, 0)
     prob = B.Problem(P, F)
-    r = prob.ipm_solve(B.default_options(init=1, max_ls=1, soc_max=0))
-    assert r.status == -5 and r.iters == 0, (r.status, r.iters)
+    r = prob.ipm_solve(B.default_options(init=1, max_ls=1, soc_max=0, resto_max=0))
+    assert r.status == -5 and r.iters == 0 and r.resto_phases == 0, (r.status, r.iters)
+    # with feasibility restoration the same crippled line search still reaches the optimum
+    rr = prob.ipm_solve(B.default_options(init=1, max_ls=1, soc_max=0))
     ok = prob.ipm_solve(B.default_options(init=1))
     assert ok.status == 0
+    assert rr.status == 0 and rr.resto_phases >= 1 and abs(rr.d - ok.d) <= 1e-6 * ok.d
