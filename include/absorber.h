@@ -277,6 +277,13 @@ typedef struct abs_options {
 void abs_default_options(abs_options* o);
 
 #define ABS_N_PHASES 6   /* eval, factor, solve, linesearch, step, other */
+#define ABS_N_KINDS 16   /* kernel kinds counted in abs_result.kind_launches: 0 evaluation with
+                            the Hessian, 1 line-search trial evaluation, 2 stage-block factor,
+                            3 block solve J x = r, 4 block solve J^T y = g, 5 KKT residual,
+                            6 Schur sums, 7 dual residual J^T lambda, 8 reduction planes (one
+                            count per plane reduced), 9 barrier diagonal and right-hand
+                            sides, 10 dz and g, 11 step sizes, 12 accept, 13 other vector
+                            kernels, 14 control kernels, 15 evaluation without the Hessian */
 #define ABS_N_KERNELS 5  /* eval (residual+Jacobian+Hessian), eval (line-search trial),
                             stage-block LU, block solve J x = r, block solve J^T y = g */
 
@@ -310,6 +317,8 @@ typedef struct abs_result {
     int32_t graph_replays;       /* graph launches of the solve (whole runs replayed from
                                     captured CUDA graphs) */
     int32_t resto_phases;        /* feasibility restoration phases entered */
+    int64_t kind_launches[ABS_N_KINDS];  /* launches per kernel kind issued by the host during
+                                    the solve (eager runs, captures; a replayed graph adds none) */
 } abs_result;
 
 /* Diagnostic: measured throughput of dependent-free fused multiply-adds on the current

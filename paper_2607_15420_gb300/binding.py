@@ -85,7 +85,8 @@ class AbsResult(C.Structure):
                 ("base_ms", C.c_double), ("warm_status", C.c_int32), ("fp64_scenarios", C.c_int32),
                 ("warm_ms", C.c_double), ("warm_E0", C.c_double), ("cold_E0", C.c_double),
                 ("warm_theta", C.c_double), ("cold_theta", C.c_double), ("tiles", C.c_int32 * 4),
-                ("graph_replays", C.c_int32), ("resto_phases", C.c_int32)]
+                ("graph_replays", C.c_int32), ("resto_phases", C.c_int32),
+                ("kind_launches", C.c_int64 * 16)]
 
 
 class AbsTrainOptions(C.Structure):
@@ -96,6 +97,8 @@ class AbsTrainOptions(C.Structure):
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 3, 256, 440, 245688
 
 KERNELS = ("eval", "eval_trial", "factor", "solve", "solve_t")
+KINDS = ("eval", "eval_trial", "factor", "solve", "solve_t", "residual", "schur", "dual", "reduce_planes", "rhs",
+         "dz", "step", "accept", "vector", "control", "eval_jac")
 PHASES = ("eval", "factor", "solve", "linesearch", "step", "other")
 
 

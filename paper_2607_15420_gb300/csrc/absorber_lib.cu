@@ -466,6 +466,7 @@ struct abs_problem {
     int* hcond_dev = nullptr;
     int tile[4] = {4, 4, 4, 4};      // warps per block last used: factor, solve, solve x2, solve^T
     int64_t nlaunch = 0;         // kernels launched (every launch is followed by launch_check)
+    int64_t kcount[ABS_N_KINDS] = {0};   // ... by kind
     float* mlp_x = nullptr;          // learned warm start: network inputs [ld][3] and outputs [ld][440]
     float* mlp_y = nullptr;
     // bound multipliers of d at the end of the last engine run, per problem, of the scaled
@@ -514,8 +515,18 @@ dim3 gridw(const abs_problem* h, int wpb) { return dim3((unsigned)((h->S + wpb -
 BView view(const abs_problem* h) { return BView{h->pid, h->ps, h->NP}; }
 double& PSV(abs_problem* h, int field, int p) { return h->hps[(size_t)field * h->NP + p]; }
 
-abs_status launch_check(abs_problem* h) {
-    if (h) h->nlaunch++;
+// kernel kinds of abs_result.kind_launches (include/absorber.h, ABS_N_KINDS)
+enum {
+    KD_EVAL = 0, KD_EVAL_TRIAL, KD_FACTOR, KD_SOLVE, KD_SOLVE_T, KD_RESIDUAL, KD_SCHUR, KD_DUAL, KD_REDUCE, KD_RHS,
+    KD_DZ, KD_STEP, KD_ACCEPT, KD_VEC, KD_CTL, KD_EVAL_JAC
+};
+
+// after every launch: count it (by kind; a reduction counts its planes) and check it
+abs_status launch_check(abs_problem* h, int kind = KD_VEC, int weight = 1) {
+    if (h) {
+        h->nlaunch++;
+        h->kcount[kind] += weight;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(h, ABS_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     return ABS_OK;
@@ -663,7 +674,7 @@ abs_status reduce(abs_problem* h, cudaStream_t st, int K, const RedOps& ops, int
 #undef RK
         default: return fail(h, ABS_ERR_ARG, "reduction with more than 9 planes");
     }
-    abs_status r = launch_check(h);
+    abs_status r = launch_check(h, KD_REDUCE, K);
     if (r != ABS_OK) return r;
     if (!fetch) return ABS_OK;
     return sync(h, st);
@@ -788,7 +799,7 @@ abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaS
             case 8: factor_w<T, 8>(h, jac, pivtol, mask, st); break;
             default: factor_w<T, 4>(h, jac, pivtol, mask, st); break;
         }
-        return launch_check(h);
+        return launch_check(h, KD_FACTOR);
     };
     abs_status r;
     if (std::is_same<T, float>::value && h->factor_tile != 0) {
@@ -824,7 +835,7 @@ abs_status solve_launch(abs_problem* h, const double* jac, const double* x, cons
             case 8: solve_w<T, NR_, 8>(h, jac, x, r0, r1, o0, o1, st); break;
             default: solve_w<T, NR_, 4>(h, jac, x, r0, r1, o0, o1, st); break;
         }
-        return launch_check(h);
+        return launch_check(h, KD_SOLVE);
     };
     abs_status r = tuned_launch(h, NR_ == 1 ? TK_SOLVE1 : TK_SOLVE2, sizeof(T), {1, 2, 4, 8}, WPB_S, go, st);
     prof_end(h, st);
@@ -840,7 +851,7 @@ abs_status solve_mixed(abs_problem* h, const double* jac, const double* x, const
         h->P, (int)h->S, h->ld, view(h), jac, (const float*)h->LUp[ABS_PREC_FP32], (const double*)h->LUp[ABS_PREC_FP64],
         h->piv, (const float*)h->Gp[ABS_PREC_FP32], (const double*)h->Gp[ABS_PREC_FP64], h->esc, x, r0, r1, o0, o1);
     prof_end(h, st);
-    return launch_check(h);
+    return launch_check(h, KD_SOLVE);
 }
 
 abs_status solve_j(abs_problem* h, int prec, const double* jac, const double* x, const double* r0, double* o0,
@@ -874,7 +885,7 @@ abs_status solve_jt_t(abs_problem* h, const double* jac, const double* g, double
             case 8: solve_t_w<T, 8>(h, jac, g, out, st); break;
             default: solve_t_w<T, 4>(h, jac, g, out, st); break;
         }
-        return launch_check(h);
+        return launch_check(h, KD_SOLVE_T);
     };
     return tuned_launch(h, TK_SOLVE_T, sizeof(T), {1, 2, 4, 8}, WPB_S, go, st);
 }
@@ -886,7 +897,7 @@ abs_status solve_jt(abs_problem* h, int prec, const double* jac, const double* g
         solve_t_mixed_kernel<WPB_S><<<gridw(h, WPB_S), 32 * WPB_S, 0, st>>>(
             (int)h->S, h->ld, view(h), jac, (const float*)h->LUp[ABS_PREC_FP32], (const double*)h->LUp[ABS_PREC_FP64],
             h->piv, (const float*)h->Gp[ABS_PREC_FP32], (const double*)h->Gp[ABS_PREC_FP64], h->esc, g, out);
-        r = launch_check(h);
+        r = launch_check(h, KD_SOLVE_T);
     } else {
         r = prec == ABS_PREC_FP32 ? solve_jt_t<float>(h, jac, g, out, st) : solve_jt_t<double>(h, jac, g, out, st);
     }
@@ -919,7 +930,7 @@ abs_status kkt_factor_core(abs_problem* h, const KKTSys& K, const double* x, cud
     if (r != ABS_OK) return r;
     schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, nullptr, V(h, V_Q),
                                              nullptr, h->sing, h->part, SCHUR_DD, V(h, V_HQ), nullptr);
-    if ((r = launch_check(h)) != ABS_OK) return r;
+    if ((r = launch_check(h, KD_SCHUR)) != ABS_OK) return r;
     return reduce(h, st, 6, make_ops({RSUM, RSUM, RSUM, RSUM, RSUM, RSUM}), PS_ACT, fetch);
 }
 
@@ -932,13 +943,13 @@ abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, 
     if (!have_p && (r = solve_j(h, K.prec, K.jac, x, rc, V(h, V_P), st)) != ABS_OK) return r;
     schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q),
                                              rz, nullptr, h->part, SCHUR_RHS, nullptr, V(h, V_T));
-    if ((r = launch_check(h)) != ABS_OK) return r;
+    if ((r = launch_check(h, KD_SCHUR)) != ABS_OK) return r;
     if ((r = reduce(h, st, 4, make_ops({RSUM, RSUM, RSUM, RSUM}), PS_ACT, false)) != ABS_OK) return r;
     finalize_dd_kernel<<<(unsigned)((h->NP + 127) / 128), 128, 0, st>>>(h->ld, view(h), h->red, dz);
-    if ((r = launch_check(h)) != ABS_OK) return r;
+    if ((r = launch_check(h, KD_VEC)) != ABS_OK) return r;
     dz_fast_kernel<<<gride(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), V(h, V_P), V(h, V_Q), V(h, V_T),
                                               V(h, V_HQ), dz, V(h, V_G));
-    if ((r = launch_check(h)) != ABS_OK) return r;
+    if ((r = launch_check(h, KD_DZ)) != ABS_OK) return r;
     return solve_jt(h, K.prec, K.jac, V(h, V_G), dl, st);
 }
 
@@ -988,7 +999,7 @@ abs_status upload_feeds(abs_problem* h, const double* feeds, cudaStream_t st) {
         CK(cudaMemcpyAsync(h->hfeed.data(), feeds, sizeof(double) * h->hfeed.size(), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         pad_feed_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((int)S, ld, feeds, h->feed);
-        return launch_check(h);
+        return launch_check(h, KD_VEC);
     }
     std::vector<double> hf((size_t)NFEED * ld, 0.0);
     for (int f = 0; f < NFEED; ++f)
@@ -1242,7 +1253,7 @@ abs_status eval_grad_jac_hess(abs_problem* h, const double* x, const double* lam
     else if (c)
         eval_kernel<true, false, false><<<g, kThr, 0, st>>>(h->P, (int)h->S, h->ld, b, false, x, nullptr, nullptr,
                                                             lambda, h->feed, c, nullptr, nullptr, nullptr);
-    abs_status r = launch_check(h);
+    abs_status r = launch_check(h, KD_EVAL);
     if (r != ABS_OK) return r;
     if (grad) {
         CK(cudaMemsetAsync(grad, 0, sizeof(double) * (size_t)((int64_t)NSC * h->ld + 1), st));
@@ -1273,7 +1284,7 @@ abs_status absorber_paper_layout(abs_problem* h, const double* x, double* out, a
     if (h->NP != 1) return fail(h, ABS_ERR_ARG, "absorber_paper_layout needs a single-problem handle");
     cudaStream_t st = (cudaStream_t)stream;
     paper_layout_kernel<<<grid2(h), kThr, 0, st>>>(h->P, (int)h->S, h->ld, x, out);
-    return launch_check(h);
+    return launch_check(h, KD_VEC);
 }
 
 }  // extern "C"
