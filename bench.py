@@ -381,6 +381,9 @@ def main():
     ap.add_argument("--capture-iters", type=int, default=0,
                     help="profiling case: only N interior-point iterations of the workload from the inlet "
                          "start (no expected-value solve), then exit without a JSON line")
+    ap.add_argument("--factor-kernel", type=int, default=0,
+                    help="FP32 factor kernel of the capture case: 0 Gauss-Jordan on the FP32 pipes, 1 tensor-core "
+                         "panels")
     ap.add_argument("--factor-tile", type=int, default=0,
                     help="fixed FP32 factor launch shape (1/2/4/8 warps per block; 0: autotuned) -- for "
                          "profiling one shape")
@@ -419,7 +422,8 @@ def main():
 
     if args.capture_iters > 0:
         r = prob.ipm_solve(B.default_options(precision=prec, max_refine=(8 if prec == B.PREC_FP32 else 0),
-                                             max_iter=args.capture_iters, init=1, factor_tile=FACTOR_TILE))
+                                             max_iter=args.capture_iters, init=1, factor_tile=FACTOR_TILE,
+                                             factor_kernel=args.factor_kernel, graphs=0))
         torch.cuda.synchronize()
         print(f"capture case: {r.iters} iterations, status {B.STATUS.get(r.status)}", flush=True)
         return

@@ -179,6 +179,8 @@ abs_status eval_grad_jac_hess(abs_problem* h, const double* x, const double* lam
 
 #define ABS_PREC_FP64 0   /* stage-block LU and solves in FP64 */
 #define ABS_PREC_FP32 1   /* stage-block LU and solves in FP32, FP64 refinement */
+#define ABS_PREC_FP32_TC 3 /* kkt_factor only: FP32 as ABS_PREC_FP32, the stage-block inverses
+                              by the tensor-core panel kernel (abs_options.factor_kernel = 1) */
 
 typedef struct abs_kkt_diag {
     const double* sigma;  /* device primal vector: barrier diagonal Sigma (d last) */
@@ -205,7 +207,7 @@ typedef struct abs_inertia {
  *   x, jac_vals, hess_vals  device, as produced by eval_grad_jac_hess at the iterate.
  *   diag       host struct; delta_c must be 0 (a singular J_s is reported in
  *              n_singular and by ABS_ERR_NUMERIC instead of regularised).
- *   precision  ABS_PREC_FP64 or ABS_PREC_FP32.
+ *   precision  ABS_PREC_FP64, ABS_PREC_FP32 or ABS_PREC_FP32_TC.
  *   inertia    host, receives the inertia (the call synchronises the stream).
  * The factorization stays in the handle for kkt_solve, which reads jac_vals, hess_vals
  * and diag->sigma again (its products with H and its FP64 refinement): those buffers
@@ -272,6 +274,11 @@ typedef struct abs_options {
                               steps on the square constraint system with d fixed, until the
                               filter accepts a point with theta reduced by 1 - gamma_theta;
                               0 disables it (the solve then stops with ABS_ERR_LINESEARCH) */
+    int32_t factor_kernel; /* FP32 stage-block inverses: 0 Gauss-Jordan exchanges on the FP32
+                              pipes; 1 blocked Gauss-Jordan (panels of 8 pivot columns) with
+                              the trailing updates on the tensor cores (mma.sync TF32, split
+                              in three products for FP32 accuracy).  Same outputs up to
+                              rounding; kkt_factor uses the last value an ipm_solve set */
 } abs_options;
 
 void abs_default_options(abs_options* o);

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libabsorber.so")
 ABS_OK = 0
 STATUS = {0: "ok", -1: "arg", -2: "cuda", -3: "oom", -4: "inertia", -5: "linesearch", -6: "maxiter",
           -7: "numeric", -8: "timeout", -9: "infeasible"}
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_FP32_TC = 0, 1, 3
 NSC = 220
 N_FEED = 18
 
@@ -71,7 +71,7 @@ class AbsOptions(C.Structure):
                 ("init", C.c_int32), ("soc_max", C.c_int32), ("kappa_soc", C.c_double),
                 ("obj_scaling", C.c_double), ("warm_mu_init", C.c_double), ("warm_bound_push", C.c_double),
                 ("warm_multipliers", C.c_int32), ("autotune", C.c_int32), ("graphs", C.c_int32),
-                ("factor_tile", C.c_int32), ("resto_max", C.c_int32)]
+                ("factor_tile", C.c_int32), ("resto_max", C.c_int32), ("factor_kernel", C.c_int32)]
 
 
 class AbsResult(C.Structure):

@@ -20,6 +20,7 @@
 #include "absorber.h"
 #include "kernels.cuh"
 #include "kernels_warp.cuh"
+#include "kernels_tc.cuh"
 #include "vec_kernels.cuh"
 
 using namespace absorber;
@@ -440,6 +441,7 @@ struct abs_problem {
     Prof prof;
     int autotune = 1;                // tile autotuner on (options.autotune)
     int factor_tile = 0;             // forced FP32 factor shape (options.factor_tile; 0: none)
+    int factor_kernel = 0;           // FP32 factor: 0 Gauss-Jordan on the FP32 pipes, 1 tensor-core panels
     // the engine's own stream (stream capture needs a non-default stream) and the event
     // that orders it after the caller's stream
     cudaStream_t stream = nullptr;
@@ -779,9 +781,16 @@ abs_status tuned_launch(abs_problem* h, int kind, int es, std::initializer_list<
 // of the scenarios with mask[s] != 0 only when mask is given
 template <class T, int W>
 void factor_w(abs_problem* h, const double* jac, double pivtol, const int* mask, cudaStream_t st) {
-    if constexpr (std::is_same<T, float>::value)
-        factor_gj_kernel<W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac, (float*)h->LUp[ABS_PREC_FP32],
-                                                            h->piv, (float*)h->Gp[ABS_PREC_FP32], h->sing, pivtol);
+    if constexpr (std::is_same<T, float>::value) {
+        if (h->factor_kernel == 1)
+            factor_gj_tc_kernel<W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac,
+                                                                   (float*)h->LUp[ABS_PREC_FP32], h->piv,
+                                                                   (float*)h->Gp[ABS_PREC_FP32], h->sing, pivtol);
+        else
+            factor_gj_kernel<W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac,
+                                                                (float*)h->LUp[ABS_PREC_FP32], h->piv,
+                                                                (float*)h->Gp[ABS_PREC_FP32], h->sing, pivtol);
+    }
     else if constexpr (factor_fits<T, W>())
         factor_warp_kernel<T, W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac,
                                                                 (T*)h->LUp[ABS_PREC_FP64], h->piv,
@@ -806,7 +815,7 @@ abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaS
         h->tile[TK_FACTOR] = h->factor_tile;
         r = go(h->factor_tile);
     } else if (std::is_same<T, float>::value)
-        r = tuned_launch(h, TK_FACTOR, sizeof(T), {1, 2, 4, 8}, WPB_F, go, st);
+        r = tuned_launch(h, TK_FACTOR, h->factor_kernel == 1 ? 5 : (int)sizeof(T), {1, 2, 4, 8}, WPB_F, go, st);
     else if (mask)
         r = go(WPB_F);   // the escalation's masked factorization: the default shape
     else

@@ -158,3 +158,29 @@ def test_partial_per_scenario_escalation_s600(B):
     # with the default refinement (8 rounds to 1e-10) nothing escalates on this workload
     r8 = prob.ipm_solve(B.default_options(precision=1, max_refine=8))
     assert r8.status == 0 and r8.fp64_scenarios == 0 and r8.fp64_fallbacks == 0
+
+
+@pytest.mark.parametrize("dw", [0.0, 1e-1])
+def test_tensor_core_factor_direction_s10(B, case10, dw):
+    # FP32 stage-block inverses by the blocked Gauss-Jordan with tensor-core trailing updates:
+    # after FP64 refinement the direction meets the same 1e-10 bound
+    _check_direction(B, case10, dw, 3)
+
+
+def test_tensor_core_factor_direction_s600(B, case600):
+    _check_direction(B, case600, 1e-4, 3)
+
+
+@pytest.mark.parametrize("S,seed", [(37, 2), (600, 1)])
+def test_tensor_core_factor_solve(B, S, seed):
+    # the interior-point solve with the tensor-core factor kernel reaches the same optimum as
+    # with the SIMT Gauss-Jordan kernel and the FP64 path
+    F = ai.make_feeds(S, seed)
+    prob = B.Problem(P, F)
+    r64 = prob.ipm_solve(B.default_options())
+    rs = prob.ipm_solve(B.default_options(precision=1, max_refine=8))
+    rt = prob.ipm_solve(B.default_options(precision=1, max_refine=8, factor_kernel=1))
+    assert r64.status == rs.status == rt.status == 0
+    assert rt.E0 <= 1e-8
+    assert abs(rt.d - r64.d) <= 1e-6 * r64.d and abs(rt.d - rs.d) <= 1e-6 * rs.d
+    assert abs(rt.iters - rs.iters) <= 2
