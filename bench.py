@@ -381,6 +381,9 @@ def main():
     ap.add_argument("--capture-iters", type=int, default=0,
                     help="profiling case: only N interior-point iterations of the workload from the inlet "
                          "start (no expected-value solve), then exit without a JSON line")
+    ap.add_argument("--graphs", type=int, default=1,
+                    help="1: each solve replays its captured CUDA graph; 0: eager launches (a profiler then sees "
+                         "every kernel launch of the timed solves)")
     ap.add_argument("--factor-kernel", type=int, default=0,
                     help="FP32 factor kernel of the capture case: 0 Gauss-Jordan on the FP32 pipes, 1 tensor-core "
                          "panels")
@@ -432,7 +435,7 @@ def main():
     if learned or not args.no_forms:
         net, train_info = train_network(B, ai)
 
-    def step(profile=0, graphs=1, x_out=None):
+    def step(profile=0, graphs=args.graphs, x_out=None):
         return solve_form(B, prob, net, args.form, profile, graphs, x_out)
 
     for _ in range(args.warmup):
