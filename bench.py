@@ -491,7 +491,7 @@ def main():
         "solve_t": (SOLVE_T_FLOPS_PER_SCEN * Sx, solve_t_bytes(es) * Sx),
     }
 
-    alu_peak = (fma32 if es == 4 else 1250.0)   # GFLOP/s: FP32 measured; FP64 nominal 1.25 TFLOP/s
+    alu_peak = fma32 if es == 4 else fma64     # GFLOP/s: the measured FMA throughput of the dtype
     kern = {}
     for k, name in enumerate(B.KERNELS):
         if kn[k] == 0:
@@ -515,7 +515,7 @@ def main():
         roof = {"bound": "alu", "achieved": dk["GFLOP_s"] / 1e3, "peak": alu_peak / 1e3, "unit": "TFLOP/s",
                 "frac": dk["GFLOP_s"] / alu_peak,
                 "peak_source": ("measured FP32 FMA throughput" if es == 4 else
-                                "nominal FP64 1.25 TFLOP/s of the GB300 table")}
+                                "measured FP64 FMA throughput") + " (abs_measure_fma_peak)"}
     else:
         roof = {"bound": "hbm", "achieved": dk["GB_s"], "peak": hbm, "unit": "GB/s", "frac": dk["GB_s"] / hbm,
                 "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json), of measured"}
