@@ -263,9 +263,12 @@ typedef struct abs_options {
                               size bucket (S rounded down to a power of two, S >= 256) times
                               every warps-per-block candidate and keeps the fastest
                               (results are identical); 0: 4 warps per block */
-    int32_t graphs;        /* 1: the Schur-reduced KKT solve (up to 6 launches) is captured into a
-                              CUDA graph on the engine's stream at its second use with a
-                              given set of vectors and replayed from then on */
+    int32_t graphs;        /* 1: the whole solve (every iteration, refinement round, line-search
+                              round and restoration step, with the device's decisions as
+                              conditional nodes) is captured into one CUDA graph on the second
+                              solve of a launch configuration and replayed from then on (the
+                              first runs eagerly and tunes the tile shapes); 0: every solve is
+                              launched eagerly, the host reading each decision */
     int32_t factor_tile;   /* FP32 factor launches only: 0 shape from autotune; 1, 2, 4, 8:
                               that many warps (scenarios) per block (identical results);
                               other values are rejected with ABS_ERR_ARG */
@@ -336,8 +339,11 @@ abs_status abs_measure_fma_peak(int kind, double* gflops);
  * solution, Section "GPU-resident solution with MadNLP.jl"): filter line-search
  * primal-dual method after Wachter & Biegler (2006) with second-order corrections and
  * the objective scaled by S, with the eval kernel, the block-LU + Schur KKT
- * factorization and solve, and every vector update running in this library's kernels;
- * the host only sequences launches and reads a few scalars per iteration.
+ * factorization and solve, every vector update and every scalar decision of the method
+ * (barrier update, Algorithm IC, refinement test, FP64 escalation, filter line search,
+ * feasibility restoration) running in this library's kernels; with options.graphs the
+ * solve is one replay of a captured CUDA graph whose loops and branches are conditional
+ * nodes set by those kernels.
  * Starting point (unless warm_x is given): for S > 1 and init = 0 the stage states of
  * the expected-value problem -- one scenario whose feed is the mean of the S feeds,
  * solved first by this same method from the inlet-copy start, always with FP64 factors
@@ -391,8 +397,8 @@ int32_t absorber_num_problems(const abs_problem* h);
  * studies of Section "Case study: absorber diameter minimization" side by side on one GPU).  Every kernel launch
  * covers the scenarios of all problems still iterating, laid out side by side in one
  * structure-of-arrays (problem p owns a contiguous run of scenario slots); per-problem
- * sums, maxima and minima come from segmented reductions; the host takes each
- * problem's scalar decisions from one fetch of those reductions per phase.  A problem
+ * sums, maxima and minima come from segmented reductions; the control kernels take each
+ * problem's scalar decisions on the device (one thread per problem).  A problem
  * that has converged or failed stops taking part.  The method and its starting point are
  * those of ipm_solve with warm_x = warm_y = NULL, applied to each problem: the
  * expected-value starts of all problems are themselves solved as one batch of P
