@@ -321,8 +321,7 @@ typedef struct abs_result {
     double warm_ms;              /* ipm_solve_learned: host time of prediction + acceptance test */
     double warm_E0, cold_E0;     /* E_0 at the learned start and at the inlet-copy start */
     double warm_theta, cold_theta;  /* constraint violation ||c||_1 at the same two starts */
-    int32_t tiles[4];            /* warps per block last used: factor (+16: the FP32
-                                    register-resident variant), solve (1 and 2 right-hand
+    int32_t tiles[4];            /* warps per block last used: factor, solve (1 and 2 right-hand
                                     sides), transposed solve */
     int32_t graph_replays;       /* graph launches of the solve (whole runs replayed from
                                     captured CUDA graphs) */
