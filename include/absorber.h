@@ -181,33 +181,43 @@ abs_status eval_grad_jac_hess(abs_problem* h, const double* x, const double* lam
 #define ABS_PREC_FP32 1   /* stage-block LU and solves in FP32, FP64 refinement */
 #define ABS_PREC_FP32_TC 3 /* kkt_factor only: FP32 as ABS_PREC_FP32, the stage-block inverses
                               by the tensor-core panel kernel (abs_options.factor_kernel = 1) */
+#define ABS_PREC_FP64_LDL 4 /* kkt_factor only: every scenario block K_s by the regularised
+                              block LDL^T in FP64 (taken whenever delta_c > 0) */
 
 typedef struct abs_kkt_diag {
     const double* sigma;  /* device primal vector: barrier diagonal Sigma (d last) */
-    double delta_w;       /* primal regularisation */
-    double delta_c;       /* dual regularisation; must be 0 (see kkt_factor) */
+    double delta_w;       /* primal regularisation, >= 0 */
+    double delta_c;       /* dual regularisation, >= 0 (> 0: the block LDL^T of kkt_factor) */
 } abs_kkt_diag;
 
 typedef struct abs_inertia {
     int64_t n_pos, n_neg, n_zero;   /* inertia of the whole KKT matrix */
     double schur_d;                 /* the scalar Schur complement on d */
-    int64_t n_singular;             /* scenarios whose stage-block LU met a tiny pivot */
+    int64_t n_singular;             /* scenarios whose factorization met a tiny pivot */
 } abs_inertia;
 
 /* Factor the primal-dual matrix of one interior-point iteration (Wachter & Biegler
- * 2006, Eq. (13); the paper's KKT step, Section "GPU-resident solution")
+ * 2006, Eq. (13) with the regularisations of their Section 3.1; the paper's KKT step,
+ * Section "GPU-resident solution")
  *     K = [ W + Sigma + dw I , J^T ; J , -dc I ]
- * for the bordered block-diagonal structure of (10): every scenario block's
- * constraint Jacobian J_s (220 x 220, block tridiagonal with 22 x 22 stage blocks) is
- * factored by a block LU with partial pivoting inside each stage block, and the
- * scenarios are eliminated onto d by a scalar Schur complement
- *     S_d = K_dd + sum_s q_s^T (W_s + Sigma_s + dw I) q_s,   q_s = J_s^{-1} b_s.
- * With J_s nonsingular each scenario block has inertia (220, 220, 0) whatever W_s is,
- * so the inertia of K is that plus the sign of S_d (Haynsworth).
+ * for the bordered block-diagonal structure of (10), the scenarios eliminated onto d by
+ * a scalar Schur complement S_d = K_dd + dw - sum_s bh_s^T K_s^{-1} bh_s (bh_s = [0; b_s],
+ * b_s = dc_s/dd); the inertia of K is that of the scenario blocks plus the sign of S_d
+ * (Haynsworth).  Two factorizations of the scenario blocks K_s:
+ *  - delta_c = 0 (ABS_PREC_FP64 / FP32 / FP32_TC): the constraint Jacobian J_s (220 x 220,
+ *    block tridiagonal with 22 x 22 stage blocks) by a block LU with partial pivoting
+ *    inside each stage block; then S_d = K_dd + sum_s q_s^T (W_s + Sigma_s + dw I) q_s,
+ *    q_s = J_s^{-1} b_s, and with J_s nonsingular every K_s has inertia (220, 220, 0)
+ *    whatever W_s is.  A singular stage block is reported in n_singular and by
+ *    ABS_ERR_NUMERIC;
+ *  - delta_c > 0 or ABS_PREC_FP64_LDL: K_s itself by a block LDL^T over its 44 x 44 stage
+ *    blocks (unknowns and rows of a stage together) with Bunch-Kaufman pivoting inside
+ *    each, in FP64; its inertia counted from the pivots.  A zero pivot is reported in
+ *    n_zero and n_singular and by ABS_ERR_NUMERIC.
  *   x, jac_vals, hess_vals  device, as produced by eval_grad_jac_hess at the iterate.
- *   diag       host struct; delta_c must be 0 (a singular J_s is reported in
- *              n_singular and by ABS_ERR_NUMERIC instead of regularised).
- *   precision  ABS_PREC_FP64, ABS_PREC_FP32 or ABS_PREC_FP32_TC.
+ *   diag       host struct (delta_w, delta_c >= 0, else ABS_ERR_ARG).
+ *   precision  ABS_PREC_FP64, ABS_PREC_FP32, ABS_PREC_FP32_TC or ABS_PREC_FP64_LDL;
+ *              delta_c > 0 needs ABS_PREC_FP64 or ABS_PREC_FP64_LDL (else ABS_ERR_ARG).
  *   inertia    host, receives the inertia (the call synchronises the stream).
  * The factorization stays in the handle for kkt_solve, which reads jac_vals, hess_vals
  * and diag->sigma again (its products with H and its FP64 refinement): those buffers

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libabsorber.so")
 ABS_OK = 0
 STATUS = {0: "ok", -1: "arg", -2: "cuda", -3: "oom", -4: "inertia", -5: "linesearch", -6: "maxiter",
           -7: "numeric", -8: "timeout", -9: "infeasible"}
-PREC_FP64, PREC_FP32, PREC_FP32_TC = 0, 1, 3
+PREC_FP64, PREC_FP32, PREC_FP32_TC, PREC_FP64_LDL = 0, 1, 3, 4
 NSC = 220
 N_FEED = 18
 

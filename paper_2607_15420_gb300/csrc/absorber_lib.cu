@@ -22,6 +22,7 @@
 #include "kernels_warp.cuh"
 #include "kernels_tc.cuh"
 #include "vec_kernels.cuh"
+#include "kernels_ldl.cuh"
 
 using namespace absorber;
 
@@ -436,8 +437,10 @@ struct abs_problem {
         const double* jac = nullptr;
         const double* hes = nullptr;
         const double* sig = nullptr;
-        double d = 0.0, dw = 0.0, Kdd = 0.0, A0 = 0.0, Q2 = 0.0, Sd = 0.0;
+        double d = 0.0, dw = 0.0, dc = 0.0, Kdd = 0.0, A0 = 0.0, Q2 = 0.0, Sd = 0.0;
+        bool ldl = false;            // factored by the block LDL^T (kernels_ldl.cuh)
     } fac;
+    double* ldl_inv = nullptr;       // [S][N_STAGES][44][44] inverses of the block LDL^T pivot blocks
     Prof prof;
     int autotune = 1;                // tile autotuner on (options.autotune)
     int factor_tile = 0;             // forced FP32 factor shape (options.factor_tile; 0: none)
@@ -485,7 +488,7 @@ namespace {
 // vector pool indices (each NSC * ld + ld doubles; the problems' d slots at NSC * ld + p)
 enum {
     V_X, V_LAM, V_ZL, V_ZU, V_C, V_JTL, V_SIG, V_RZ, V_RC, V_P, V_Q, V_DZ, V_DL, V_DZL, V_DZU,
-    V_G, V_RHOZ, V_RHOC, V_CZ, V_CL, V_ONE, V_CT, V_RCS, V_RCN, V_SZ, V_SL, V_HQ, V_T, V_IL, V_IU, V_COUNT
+    V_G, V_RHOZ, V_RHOC, V_CZ, V_CL, V_ONE, V_CT, V_RCS, V_RCN, V_SZ, V_SL, V_HQ, V_T, V_IL, V_IU, V_QL, V_COUNT
 };
 
 abs_status fail(abs_problem* h, abs_status st, const std::string& msg) {
@@ -627,6 +630,13 @@ abs_status ensure_factor(abs_problem* h, int prec) {
     return ABS_OK;
 }
 
+// the block LDL^T's inverses (allocated on first use) and its kernels' shared memory
+abs_status ensure_ldl(abs_problem* h) {
+    if (!h->ldl_inv) CK(cudaMalloc(&h->ldl_inv, sizeof(double) * (size_t)LDL_BLOCK * N_STAGES * h->S));
+    CK(cudaFuncSetAttribute(ldl_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LDL_FACTOR_SMEM));
+    return ABS_OK;
+}
+
 // host synchronisation point: every copy issued before it has completed
 abs_status sync(abs_problem* h, cudaStream_t st) {
     CK(cudaStreamSynchronize(st));
@@ -696,6 +706,9 @@ struct KKTSys {
     const double* sig = nullptr;
     bool use_w = true;
     int prec = ABS_PREC_FP64;
+    // block LDL^T of every scenario block (FP64, dw = PS_DW, dc = PS_DC) instead of the
+    // block LU of J_s
+    bool ldl = false;
     // set before kkt_factor_core: p = J^-1 rc is solved together with q = J^-1 b (one
     // two-right-hand-side launch) and the first KKT solve with this rc reuses it
     const double* pre_rc = nullptr;
@@ -921,6 +934,21 @@ abs_status solve_jt(abs_problem* h, int prec, const double* jac, const double* g
 // FP32 inverses).  x: primal vector whose d slots hold the problems' d.
 abs_status kkt_factor_core(abs_problem* h, const KKTSys& K, const double* x, cudaStream_t st, bool fetch) {
     abs_status r;
+    if (K.ldl) {
+        // block LDL^T: the pivot inverses and the inertia counts ([2] positive, [3] negative,
+        // [6] zero pivots, [5] scenarios with a zero pivot), then u = K_s^-1 [0; b] with
+        // [0] A0 = -sum b^T u_l (so that S_d = K_dd + dw + A0), [1] 0, [4] the d-d entries
+        if ((r = ensure_ldl(h)) != ABS_OK) return r;
+        ldl_factor_kernel<<<(unsigned)h->S, 32, LDL_FACTOR_SMEM, st>>>((int)h->S, h->ld, view(h), K.jac, K.hes, K.sig,
+                                                                       K.use_w, h->ldl_inv, h->part);
+        if ((r = launch_check(h, KD_FACTOR)) != ABS_OK) return r;
+        ldl_solve_kernel<<<(unsigned)h->S, 32, LDL_SOLVE_SMEM, st>>>((int)h->S, h->ld, view(h), K.jac, h->ldl_inv,
+                                                                     nullptr, nullptr, true, V(h, V_Q), V(h, V_QL),
+                                                                     h->part, 0, -1.0, true,
+                                                                     K.use_w ? K.hes : nullptr);
+        if ((r = launch_check(h, KD_SOLVE)) != ABS_OK) return r;
+        return reduce(h, st, 7, make_ops({RSUM, RSUM, RSUM, RSUM, RSUM, RSUM, RSUM}), PS_ACT, fetch);
+    }
     if (K.prec == ABS_PREC_MIXED) {
         if ((r = ensure_factor(h, ABS_PREC_FP64)) != ABS_OK) return r;
         if ((r = ensure_factor(h, ABS_PREC_FP32)) != ABS_OK) return r;
@@ -949,6 +977,19 @@ abs_status kkt_factor_core(abs_problem* h, const KKTSys& K, const double* x, cud
 abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, const double* rz, const double* rc,
                               double* dz, double* dl, cudaStream_t st, bool have_p = false) {
     abs_status r;
+    if (K.ldl) {
+        // v = K_s^-1 [rz; rc] into dz, dl with [2] b^T v_l ([3] zero), dd, then x = v - u dd
+        ldl_solve_kernel<<<(unsigned)h->S, 32, LDL_SOLVE_SMEM, st>>>((int)h->S, h->ld, view(h), K.jac, h->ldl_inv,
+                                                                     rz, rc, false, dz, dl, h->part, 2, 1.0, false,
+                                                                     nullptr);
+        if ((r = launch_check(h, KD_SOLVE)) != ABS_OK) return r;
+        if ((r = reduce(h, st, 4, make_ops({RSUM, RSUM, RSUM, RSUM}), PS_ACT, false)) != ABS_OK) return r;
+        finalize_dd_kernel<<<(unsigned)((h->NP + 127) / 128), 128, 0, st>>>(h->ld, view(h), h->red, dz);
+        if ((r = launch_check(h, KD_VEC)) != ABS_OK) return r;
+        ldl_back_kernel<<<dim3((unsigned)((h->S + 127) / 128), N_STAGES), 128, 0, st>>>((int)h->S, h->ld, view(h),
+                                                                                       V(h, V_Q), V(h, V_QL), dz, dl);
+        return launch_check(h, KD_DZ);
+    }
     if (!have_p && (r = solve_j(h, K.prec, K.jac, x, rc, V(h, V_P), st)) != ABS_OK) return r;
     schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q),
                                              rz, nullptr, h->part, SCHUR_RHS, nullptr, V(h, V_T));
@@ -1172,6 +1213,7 @@ void absorber_destroy(abs_problem* h) {
     cudaFree(h->jac);
     cudaFree(h->hes);
     cudaFree(h->vec);
+    cudaFree(h->ldl_inv);
     for (int k = 0; k < 2; ++k) {
         cudaFree(h->LUp[k]);
         cudaFree(h->Gp[k]);

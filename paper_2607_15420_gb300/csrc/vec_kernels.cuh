@@ -12,7 +12,7 @@
 namespace absorber {
 
 // Schur: r_d and S_d per problem; PS_BASE: 1 if the problem starts from the base states
-enum PsExtra { PS_RD = PS_COUNT, PS_SD, PS_BASE, PS_NFIELDS };
+enum PsExtra { PS_RD = PS_COUNT, PS_SD, PS_BASE, PS_DC, PS_NFIELDS };
 
 __device__ inline double lo_of(const Params& P, int j) { return j == LT ? P.Tlo_s : 0.0; }
 __device__ inline double hi_of(const Params& P, int /*j*/) { return P.Thi_s; }

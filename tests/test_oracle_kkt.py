@@ -113,3 +113,18 @@ def test_refined_schur_solve_matches_monolithic_and_reduces_the_residual():
         assert res2 <= res0
         xm = np.linalg.solve(K, r)
         assert np.linalg.norm(full(x2) - xm) <= np.linalg.norm(full(x0) - xm) + 1e-13 * np.linalg.norm(xm)
+
+
+def test_regularised_block_inertia_matches_eigenvalue_signs():
+    # the dual regularisation -dc I (Wachter & Biegler 2006, Section 3.1): the oracle's
+    # Bunch-Kaufman inertia of a scenario block against the signs of its eigenvalues, for
+    # dc small (the inertia of dc = 0) up to large (that of W + Sigma, indefinite here)
+    solver, st, C, J, Jd, W, Wdd, sig, sigd = _iterate(1, 3, 2)
+    seen = set()
+    for dc in (1e-8, 1e-2, 1.0, 1e6):
+        Ks = kkt.scenario_matrix(W[0], sig[0], J[0], 0.0, dc)
+        ev = np.linalg.eigvalsh(Ks)
+        expect = (int((ev > 0).sum()), int((ev < 0).sum()), 0)
+        assert kkt.BlockLDL(Ks).inertia() == expect, dc
+        seen.add(expect)
+    assert len(seen) > 1    # the range of dc crosses a change of inertia
