@@ -292,6 +292,12 @@ typedef struct abs_options {
                               the trailing updates on the tensor cores (mma.sync TF32, split
                               in three products for FP32 accuracy).  Same outputs up to
                               rounding; kkt_factor uses the last value an ipm_solve set */
+    int32_t kkt;           /* factorization of the scenario blocks: 0 block LU of J_s (inertia
+                              from the Schur scalar alone; a singular stage block ends the solve
+                              with ABS_ERR_NUMERIC); 1 the regularised block LDL^T of kkt_factor
+                              (FP64 only), with Algorithm IC complete: the inertia of every
+                              scenario block from its pivots, delta_c = 1e-8 mu^(1/4) when a
+                              pivot is zero, every delta_w trial refactored */
 } abs_options;
 
 void abs_default_options(abs_options* o);

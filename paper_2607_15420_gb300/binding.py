@@ -71,7 +71,8 @@ class AbsOptions(C.Structure):
                 ("init", C.c_int32), ("soc_max", C.c_int32), ("kappa_soc", C.c_double),
                 ("obj_scaling", C.c_double), ("warm_mu_init", C.c_double), ("warm_bound_push", C.c_double),
                 ("warm_multipliers", C.c_int32), ("autotune", C.c_int32), ("graphs", C.c_int32),
-                ("factor_tile", C.c_int32), ("resto_max", C.c_int32), ("factor_kernel", C.c_int32)]
+                ("factor_tile", C.c_int32), ("resto_max", C.c_int32), ("factor_kernel", C.c_int32),
+                ("kkt", C.c_int32)]
 
 
 class AbsResult(C.Structure):

@@ -352,7 +352,8 @@ struct DevOpt {
     double gamma_theta, gamma_phi, delta, s_theta, s_phi, eta_phi, gamma_alpha, lam_init_max;
     double dw0, dw_min, dw_max, kw_minus, kw_plus, kw_plus_bar, kappa_soc, obj_scaling, refine_tol;
     double dlo, dhi, u_max;
-    int max_iter, max_refine, max_ls, soc_max, resto_max;
+    double dc_bar, kappa_c;     // delta_c = dc_bar mu^kappa_c when a pivot is zero (block LDL^T)
+    int max_iter, max_refine, max_ls, soc_max, resto_max, kkt;
 };
 
 // one problem's state of the method
@@ -365,6 +366,8 @@ struct DState {
     double E0, inf_pr, inf_du, theta, phi, jtl_d, sld, sud, dd;
     double a_max, a_z, gphi, dzLd, dzUd, alpha, a_min, a0, th_old, a_soc, sd, ct_coef;
     double Kdd, dw, Sd, rd, resid;
+    int ic_trial;                                  // Algorithm IC trial of the block LDL^T path
+    double dc;                                     // its delta_c of the iteration
 };
 
 // state shared by the problems of a run
@@ -632,8 +635,11 @@ abs_status ensure_factor(abs_problem* h, int prec) {
 
 // the block LDL^T's inverses (allocated on first use) and its kernels' shared memory
 abs_status ensure_ldl(abs_problem* h) {
-    if (!h->ldl_inv) CK(cudaMalloc(&h->ldl_inv, sizeof(double) * (size_t)LDL_BLOCK * N_STAGES * h->S));
-    CK(cudaFuncSetAttribute(ldl_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LDL_FACTOR_SMEM));
+    if (!h->ldl_inv) {
+        CK(cudaMalloc(&h->ldl_inv, sizeof(double) * (size_t)LDL_BLOCK * N_STAGES * h->S));
+        CK(cudaFuncSetAttribute(ldl_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)LDL_FACTOR_SMEM));
+    }
     return ABS_OK;
 }
 
@@ -1149,6 +1155,7 @@ void abs_default_options(abs_options* o) {
     o->autotune = 1;
     o->graphs = 1;
     o->resto_max = 20;
+    o->kkt = 0;
 }
 
 abs_status absorber_create(const abs_params* p, const double* feeds, const double* prob, int64_t S,

@@ -145,3 +145,63 @@ def test_regularisation_arguments(B, case10):
         with pytest.raises(B.AbsorberError) as e:
             prob.kkt_factor(x, jac, hes, sg, **kw)
         assert e.value.status == -1, kw
+
+
+def _solve_point(B, prob, opt):
+    import torch
+    x = torch.zeros(prob.n_primal, dtype=torch.float64, device="cuda")
+    y = torch.zeros(prob.n_row, dtype=torch.float64, device="cuda")
+    res = prob.ipm_solve(opt, x_out=x, y_out=y)
+    zl = torch.zeros_like(x)
+    zu = torch.zeros_like(x)
+    zd = prob.bound_multipliers(zl, zu)
+    Z, d = prob.from_soa(host(x))
+    lam, _ = prob.from_soa(host(y))
+    ZL, _ = prob.from_soa(host(zl))
+    ZU, _ = prob.from_soa(host(zu))
+    return res, (Z, d, lam, ZL, ZU, zd[0], zd[1])
+
+
+@pytest.mark.parametrize("S,seed", [(10, 0), (37, 2)])
+def test_ipm_solve_through_the_block_ldlt(B, S, seed):
+    # the whole interior-point solve with every scenario block factored by the block LDL^T
+    # (Algorithm IC reading every block's inertia from its pivots, each delta_w trial
+    # refactored): the optimum of the block-LU path, E_0 <= 1e-8 recomputed by the oracle
+    # at the returned point (oracle/checks.kkt_error, complex-step Jacobian)
+    from oracle import checks
+    F = ai.make_feeds(S, seed)
+    prob = B.Problem(P, F)
+    r0 = prob.ipm_solve(B.default_options())
+    r1, pt = _solve_point(B, prob, B.default_options(kkt=1))
+    assert r0.status == 0 and r1.status == 0, (r0.status, r1.status)
+    assert abs(r1.d - r0.d) <= 1e-9 * r0.d, (r1.d, r0.d)
+    assert abs(r1.iters - r0.iters) <= 2, (r1.iters, r0.iters)
+    Z, d, lam, ZL, ZU, zld, zud = pt
+    assert checks.kkt_error(P, F, d, Z, lam, ZL, ZU, zld, zud) <= 1e-8
+    # graph replay of the same configuration: the eager result bit for bit
+    runs = [prob.ipm_solve(B.default_options(kkt=1, graphs=1)) for _ in range(2)]
+    assert runs[-1].graph_replays >= 1
+    for r in runs:
+        assert r.status == 0 and r.iters == r1.iters and r.d == r1.d
+
+
+def test_batched_block_ldlt_equals_single_solves(B):
+    # ragged problems (one of one scenario) side by side: each equals its own solve, and the
+    # optimum of the block-LU path wherever that one converges
+    feeds = ai.batched_feeds([7, 1, 33, 12], seed=21)
+    batch = B.Batch(P, feeds)
+    rb = batch.ipm_solve(B.default_options(kkt=1))
+    for F, r in zip(feeds, rb):
+        prob = B.Problem(P, F)
+        rs = prob.ipm_solve(B.default_options(kkt=1))
+        assert r.status == rs.status and r.iters == rs.iters and r.d == rs.d, (r.status, rs.status, r.iters, rs.iters)
+        rl = prob.ipm_solve(B.default_options())
+        if rl.status == 0:
+            assert rs.status == 0 and abs(rs.d - rl.d) <= 1e-9 * rl.d, (rs.status, rs.d, rl.d)
+
+
+def test_block_ldlt_option_checks(B):
+    prob = B.Problem(P, ai.make_feeds(2, 0))
+    for kw in (dict(kkt=2), dict(kkt=1, precision=1)):
+        r = prob.ipm_solve(B.default_options(**kw))
+        assert r.status == -1, kw
