@@ -17,14 +17,22 @@ H_CS = 1e-30
 
 
 def jacobian_complex_step(P, F, Z, d):
-    """dc/dz (S, 220, 220) and dc/dd (S, 220) by complex step, one column at a time."""
+    """dc/dz (S, 220, 220) and dc/dd (S, 220) by complex step, one column at a time
+    (for an array d of K section diameters dc/dd is (S, 220, K), one column per entry)."""
     S, n = Z.shape
     J = np.zeros((S, n, n))
     for j in range(n):
         Zc = Z.astype(complex)
         Zc[:, j] += 1j * H_CS
         J[:, :, j] = model.residuals(P, F, Zc, d).imag / H_CS
-    Jd = model.residuals(P, F, Z.astype(complex), d + 1j * H_CS).imag / H_CS
+    if np.ndim(d) == 0:
+        Jd = model.residuals(P, F, Z.astype(complex), d + 1j * H_CS).imag / H_CS
+    else:
+        Jd = np.zeros((S, n, np.size(d)))
+        for k in range(np.size(d)):
+            dc = np.asarray(d, dtype=complex).copy()
+            dc[k] += 1j * H_CS
+            Jd[:, :, k] = model.residuals(P, F, Z.astype(complex), dc).imag / H_CS
     return J, Jd
 
 
@@ -128,6 +136,16 @@ def minimum_diameter(P, F, Z):
     return math.sqrt(4.0 * float(vol.max()) / (math.pi * P["u_max"])), vol
 
 
+def section_diameters(P, F, Z, K):
+    """The smallest diameter of each of K column sections that satisfies the hydraulic
+    rows of its stages at the given states: max over scenarios and the section's stages
+    of sqrt(4 V R T / (pi u_max P^abs))."""
+    vol = model.hydraulic_volume(P, F, Z)
+    sec = model.stage_sections(K)
+    return np.array([math.sqrt(4.0 * float(vol[:, sec == k].max()) / (math.pi * P["u_max"]))
+                     for k in range(K)])
+
+
 def kkt_error(P, F, d, Z, lam, zL, zU, zLd, zUd, s_max=100.0, chunk=None):
     """E_0 (Wachter & Biegler 2006, Eq. (5) at mu = 0) from the definitions, with the
     constraint Jacobian by complex step.  chunk: scenarios per complex-step Jacobian
@@ -135,24 +153,27 @@ def kkt_error(P, F, d, Z, lam, zL, zU, zLd, zUd, s_max=100.0, chunk=None):
     (S, 220, 220) array and changes no arithmetic)."""
     S = Z.shape[0]
     lo, hi, dlo, dhi = model.bounds(P, S)
+    K = np.size(d)
+    dv, zLv, zUv = np.atleast_1d(d), np.atleast_1d(zLd), np.atleast_1d(zUd)
     step = S if chunk is None else int(chunk)
     rz = np.zeros_like(Z)
-    jdl = 0.0
+    jdl = np.zeros(K)
     for a in range(0, S, step):
         b = min(S, a + step)
         J, Jd = jacobian_complex_step(P, F[:, a:b], Z[a:b], d)
         rz[a:b] = np.einsum("sr,src->sc", lam[a:b], J)
-        jdl += float(np.sum(Jd * lam[a:b]))
+        jdl += np.atleast_1d(np.einsum("sr...,sr->...", Jd, lam[a:b]))
     C = model.residuals(P, F, Z, d)
     rz = rz - zL + zU
-    rd = 1.0 + jdl - zLd + zUd
+    # gradient of the objective sum_k w_k d_k (w = the sections' shares; 1 for K = 1)
+    rd = model.section_weights(K) + jdl - zLv + zUv
     hasL, hasU = np.isfinite(lo), np.isfinite(hi)
     cl = np.where(hasL, zL * (Z - np.where(hasL, lo, 0)), 0.0)
     cu = np.where(hasU, zU * (np.where(hasU, hi, 0) - Z), 0.0)
-    cd = max(abs(zLd * (d - dlo)), abs(zUd * (dhi - d)))
-    nz = hasL.sum() + hasU.sum() + 2
-    zs = np.abs(zL).sum() + np.abs(zU).sum() + abs(zLd) + abs(zUd)
+    cd = max(np.abs(zLv * (dv - dlo)).max(), np.abs(zUv * (dhi - dv)).max())
+    nz = hasL.sum() + hasU.sum() + 2 * K
+    zs = np.abs(zL).sum() + np.abs(zU).sum() + np.abs(zLv).sum() + np.abs(zUv).sum()
     sd = max(s_max, (np.abs(lam).sum() + zs) / (lam.size + nz)) / s_max
     sc = max(s_max, zs / nz) / s_max
-    return max(max(np.abs(rz).max(), abs(rd)) / sd, np.abs(C).max(),
+    return max(max(np.abs(rz).max(), np.abs(rd).max()) / sd, np.abs(C).max(),
                max(np.abs(cl).max(), np.abs(cu).max(), cd) / sc)

@@ -37,6 +37,11 @@ the inlet-copy start of model.initial_point.
 Unknowns: the diameter d (bounds (10c)) and the per-scenario z (S, 220) of model.py with
 bounds (10d).  The KKT systems are solved by kkt.SchurKKT (dense per-scenario
 Bunch-Kaufman LDL^T + scalar Schur complement on d).
+
+With P["n_sections"] = K > 1 the design vector is the K section diameters theta_k (model.py),
+each with the bounds of d, and the objective sum_k w_k theta_k with w_k the sections'
+shares of the stages; d, z_L(d), z_U(d) are then K-arrays (floats for K = 1) and the
+Schur complement is K x K.
 """
 from __future__ import annotations
 
@@ -122,12 +127,19 @@ class Problem:
         self.w = w                   # objective scaling: the solver minimises w * d
         self.S = F.shape[1]
         self.n = model.NS
+        self.K = model.n_sections(P)
+        self.wsec = model.section_weights(self.K)
         self.lo, self.hi, self.dlo, self.dhi = model.bounds(P, self.S)
         self.hasL = np.isfinite(self.lo)
         self.hasU = np.isfinite(self.hi)
-        self.nL = int(self.hasL.sum()) + 1   # + d
-        self.nU = int(self.hasU.sum()) + 1
+        self.nL = int(self.hasL.sum()) + self.K   # + the design entries
+        self.nU = int(self.hasU.sum()) + self.K
         self.m = self.S * self.n
+
+    def th(self, v):
+        """A design-vector quantity in the stored form: a float for K = 1, else an array."""
+        v = np.atleast_1d(np.asarray(v, dtype=float))
+        return float(v[0]) if self.K == 1 else v.copy()
 
     # slacks to the bounds (1 where there is no bound, never used)
     def sl(self, Z):
@@ -150,14 +162,20 @@ def push_into_bounds(pr, opt, Z, d):
     wd = pr.dhi - pr.dlo
     pdl = min(opt.bound_push * max(1.0, abs(pr.dlo)), opt.bound_frac * wd)
     pdu = min(opt.bound_push * max(1.0, abs(pr.dhi)), opt.bound_frac * wd)
-    d = min(max(d, pr.dlo + pdl), pr.dhi - pdu)
-    return Z, d
+    d = np.minimum(np.maximum(np.broadcast_to(np.atleast_1d(d), (pr.K,)), pr.dlo + pdl), pr.dhi - pdu)
+    return Z, pr.th(d)
+
+
+def jd_t(Jd, lam):
+    """sum_s b_s^T lam_s: a float for 2-D Jd (K = 1), a K-array for 3-D."""
+    v = np.einsum("sr...,sr->...", Jd, lam)
+    return float(v) if np.ndim(v) == 0 else v
 
 
 def dual_residual(pr, st, J, Jd):
-    """grad f + J^T lam - z_L + z_U for z (S, n) and for d (scalar)."""
+    """grad f + J^T lam - z_L + z_U for z (S, n) and for d (K-array)."""
     rz = np.einsum("src,sr->sc", J, st.lam) - st.zL + st.zU
-    rd = pr.w + float(np.sum(Jd * st.lam)) - st.zLd + st.zUd
+    rd = pr.w * pr.wsec + np.atleast_1d(jd_t(Jd, st.lam)) - np.atleast_1d(st.zLd) + np.atleast_1d(st.zUd)
     return rz, rd
 
 
@@ -167,23 +185,25 @@ def optimality_error(pr, opt, st, C, J, Jd, mu):
     sl, su = pr.sl(st.Z), pr.su(st.Z)
     cl = np.where(pr.hasL, st.zL * sl - mu, 0.0)
     cu = np.where(pr.hasU, st.zU * su - mu, 0.0)
-    cld = st.zLd * (st.d - pr.dlo) - mu
-    cud = st.zUd * (pr.dhi - st.d) - mu
-    zsum = float(np.abs(st.zL).sum() + np.abs(st.zU).sum() + abs(st.zLd) + abs(st.zUd))
+    dv, zLd, zUd = np.atleast_1d(st.d), np.atleast_1d(st.zLd), np.atleast_1d(st.zUd)
+    cld = zLd * (dv - pr.dlo) - mu
+    cud = zUd * (pr.dhi - dv) - mu
+    zsum = float(np.abs(st.zL).sum() + np.abs(st.zU).sum() + np.abs(zLd).sum() + np.abs(zUd).sum())
     s_d = max(opt.s_max, (float(np.abs(st.lam).sum()) + zsum) / (pr.m + pr.nL + pr.nU)) / opt.s_max
     s_c = max(opt.s_max, zsum / (pr.nL + pr.nU)) / opt.s_max
-    dual = max(float(np.abs(rz).max(initial=0.0)), abs(rd)) / s_d
+    dual = max(float(np.abs(rz).max(initial=0.0)), float(np.abs(rd).max())) / s_d
     primal = float(np.abs(C).max(initial=0.0))
     compl = max(float(np.abs(cl).max(initial=0.0)), float(np.abs(cu).max(initial=0.0)),
-                abs(cld), abs(cud)) / s_c
+                float(np.abs(cld).max()), float(np.abs(cud).max())) / s_c
     return max(dual, primal, compl), dual, primal, compl
 
 
 def barrier_phi(pr, Z, d, mu):
     sl, su = pr.sl(Z), pr.su(Z)
+    dv = np.atleast_1d(d)
     b = np.sum(np.log(sl[pr.hasL])) + np.sum(np.log(su[pr.hasU]))
-    b += math.log(d - pr.dlo) + math.log(pr.dhi - d)
-    return pr.w * d - mu * b
+    b += float(np.sum(np.log(dv - pr.dlo)) + np.sum(np.log(pr.dhi - dv)))
+    return pr.w * float(pr.wsec @ dv) - mu * b
 
 
 def fraction_to_boundary(pr, x, dx, lo_mask, lo, hi_mask, hi, tau):
@@ -215,15 +235,17 @@ class IPM:
         pr = self.pr
         sig = (np.where(pr.hasL, st.zL / pr.sl(st.Z), 0.0)
                + np.where(pr.hasU, st.zU / pr.su(st.Z), 0.0))
-        sigd = st.zLd / (st.d - pr.dlo) + st.zUd / (pr.dhi - st.d)
-        return sig, sigd
+        dv = np.atleast_1d(st.d)
+        sigd = np.atleast_1d(st.zLd) / (dv - pr.dlo) + np.atleast_1d(st.zUd) / (pr.dhi - dv)
+        return sig, pr.th(sigd)
 
     def barrier_gradient(self, st, mu):
         pr = self.pr
         gz = (np.where(pr.hasL, -mu / pr.sl(st.Z), 0.0)
               + np.where(pr.hasU, mu / pr.su(st.Z), 0.0))
-        gd = pr.w - mu / (st.d - pr.dlo) + mu / (pr.dhi - st.d)
-        return gz, gd
+        dv = np.atleast_1d(st.d)
+        gd = pr.w * pr.wsec - mu / (dv - pr.dlo) + mu / (pr.dhi - dv)
+        return gz, pr.th(gd)
 
     # ---- Newton direction with inertia correction -----------------------------------
     def newton_direction(self, st, mu, C, J, Jd, W, Wdd, dw=None, dc=None):
@@ -233,10 +255,10 @@ class IPM:
         sig, sigd = self.sigma(st)
         gz, gd = self.barrier_gradient(st, mu)
         rz = -(gz + np.einsum("src,sr->sc", J, st.lam))
-        rd = -(gd + float(np.sum(Jd * st.lam)))
+        rd = -(gd + jd_t(Jd, st.lam))
         rc = -C
-        Kdd = float(np.sum(Wdd)) + sigd
-        n_expect, m_expect = 1 + pr.S * pr.n, pr.S * pr.n
+        Kdd = (float(np.sum(Wdd)) + sigd) if pr.K == 1 else np.diag(Wdd.sum(axis=0) + sigd)
+        n_expect, m_expect = pr.K + pr.S * pr.n, pr.S * pr.n
 
         def factor(w, c):
             return kkt.SchurKKT(W, sig, J, Jd, Kdd, w, c)
@@ -267,10 +289,12 @@ class IPM:
         sl, su = pr.sl(st.Z), pr.su(st.Z)
         dzL = np.where(pr.hasL, mu / sl - st.zL - (st.zL / sl) * dZ, 0.0)
         dzU = np.where(pr.hasU, mu / su - st.zU + (st.zU / su) * dZ, 0.0)
-        sld, sud = st.d - pr.dlo, pr.dhi - st.d
-        dzLd = mu / sld - st.zLd - (st.zLd / sld) * dd
-        dzUd = mu / sud - st.zUd + (st.zUd / sud) * dd
-        return dzL, dzU, dzLd, dzUd
+        dv, ddv = np.atleast_1d(st.d), np.atleast_1d(dd)
+        zLd, zUd = np.atleast_1d(st.zLd), np.atleast_1d(st.zUd)
+        sld, sud = dv - pr.dlo, pr.dhi - dv
+        dzLd = mu / sld - zLd - (zLd / sld) * ddv
+        dzUd = mu / sud - zUd + (zUd / sud) * ddv
+        return dzL, dzU, pr.th(dzLd), pr.th(dzUd)
 
     # ---- initial point ------------------------------------------------------------
     def initial_state(self, Z0=None, d0=None, lam0=None):
@@ -281,7 +305,8 @@ class IPM:
         Z, d = push_into_bounds(pr, opt, Z, d)
         zL = np.where(pr.hasL, 1.0, 0.0)
         zU = np.where(pr.hasU, 1.0, 0.0)
-        st = State(d, Z, np.zeros((pr.S, pr.n)), zL, zU, 1.0, 1.0)
+        one = pr.th(np.ones(pr.K))
+        st = State(d, Z, np.zeros((pr.S, pr.n)), zL, zU, one, one)
         if lam0 is not None:
             st.lam = lam0.copy()
             return st
@@ -289,8 +314,9 @@ class IPM:
         C, J, Jd, _, _ = self.evaluate(st, rows_only=True)
         S, n = pr.S, pr.n
         Wid = np.broadcast_to(np.eye(n), (S, n, n))
-        fac = kkt.SchurKKT(Wid, np.zeros((S, n)), J, Jd, 1.0, 0.0, 0.0)
-        _, _, lam = fac.solve(-(-zL + zU), -(pr.w - st.zLd + st.zUd), np.zeros((S, n)))
+        fac = kkt.SchurKKT(Wid, np.zeros((S, n)), J, Jd, 1.0 if pr.K == 1 else np.eye(pr.K), 0.0, 0.0)
+        rd = pr.th(-(pr.w * pr.wsec - np.atleast_1d(st.zLd) + np.atleast_1d(st.zUd)))
+        _, _, lam = fac.solve(-(-zL + zU), rd, np.zeros((S, n)))
         if np.abs(lam).max() <= opt.lam_init_max:
             st.lam = lam
         return st
@@ -350,7 +376,7 @@ class IPM:
         d0 = 0.5 * (pr.dlo + pr.dhi)
         vol = model.hydraulic_volume(pr.P, pr.F, Z0.reshape(pr.S, -1))
         Z0[:, :, model.IS] = pr.P["u_max"] * math.pi * d0 * d0 / 4.0 - vol
-        return Z0.reshape(pr.S, -1), d0, r1.iters
+        return Z0.reshape(pr.S, -1), pr.th(np.full(pr.K, d0)), r1.iters
 
     # ---- main loop ----------------------------------------------------------------
     def solve(self, st=None):
@@ -399,25 +425,27 @@ class IPM:
                 break
             dzL, dzU, dzLd, dzUd = self.bound_dual_steps(st, mu, dZ, dd)
             # fraction to the boundary
+            allK = np.ones(pr.K, dtype=bool)
             a_max = min(fraction_to_boundary(pr, st.Z, dZ, pr.hasL, pr.lo, pr.hasU, pr.hi, tau),
-                        fraction_to_boundary(pr, np.array([st.d]), np.array([dd]),
-                                             np.array([True]), np.array([pr.dlo]),
-                                             np.array([True]), np.array([pr.dhi]), tau))
+                        fraction_to_boundary(pr, np.atleast_1d(st.d), np.atleast_1d(dd),
+                                             allK, np.full(pr.K, pr.dlo), allK, np.full(pr.K, pr.dhi), tau))
             zmask = pr.hasL
             a_z = min(fraction_to_boundary(pr, st.zL, dzL, pr.hasL, np.zeros_like(st.zL),
                                            np.zeros_like(pr.hasU), st.zL, tau),
                       fraction_to_boundary(pr, st.zU, dzU, pr.hasU, np.zeros_like(st.zU),
                                            np.zeros_like(pr.hasU), st.zU, tau),
-                      fraction_to_boundary(pr, np.array([st.zLd, st.zUd]), np.array([dzLd, dzUd]),
-                                           np.array([True, True]), np.zeros(2),
-                                           np.array([False, False]), np.zeros(2), tau))
+                      fraction_to_boundary(pr, np.concatenate([np.atleast_1d(st.zLd), np.atleast_1d(st.zUd)]),
+                                           np.concatenate([np.atleast_1d(dzLd), np.atleast_1d(dzUd)]),
+                                           np.ones(2 * pr.K, dtype=bool), np.zeros(2 * pr.K),
+                                           np.zeros(2 * pr.K, dtype=bool), np.zeros(2 * pr.K), tau))
             del zmask
             # filter line search
             phi = barrier_phi(pr, st.Z, st.d, mu)
             gz, gd = self.barrier_gradient(st, mu)
-            gphi = float(np.sum(gz * dZ)) + gd * dd
+            gphi = float(np.sum(gz * dZ)) + float(np.atleast_1d(gd) @ np.atleast_1d(dd))
             tiny = max(float(np.max(np.abs(dZ) / (1.0 + np.abs(st.Z)))),
-                       abs(dd) / (1.0 + abs(st.d))) < 10.0 * np.finfo(float).eps
+                       float(np.max(np.abs(np.atleast_1d(dd)) / (1.0 + np.abs(np.atleast_1d(st.d)))))
+                       ) < 10.0 * np.finfo(float).eps
             alpha = a_max
             accepted = False
             ftype = False
@@ -458,7 +486,8 @@ class IPM:
 
                 while n_ls < opt.max_ls:
                     n_ls += 1
-                    ok, ftype, th_t, Ct = acceptable(st.Z + alpha * dZ, st.d + alpha * dd, alpha)
+                    ok, ftype, th_t, Ct = acceptable(st.Z + alpha * dZ, pr.th(np.atleast_1d(st.d) + alpha * np.atleast_1d(dd)),
+                                                     alpha)
                     if ok:
                         accepted = True
                         break
@@ -469,12 +498,13 @@ class IPM:
                         th_old = theta
                         for p in range(opt.soc_max):
                             sZ, sd, sl = fac.solve(-(gz + np.einsum("src,sr->sc", J, st.lam)),
-                                                   -(gd + float(np.sum(Jd * st.lam))), -csoc)
+                                                   -(gd + jd_t(Jd, st.lam)), -csoc)
                             a_soc = min(fraction_to_boundary(pr, st.Z, sZ, pr.hasL, pr.lo, pr.hasU, pr.hi, tau),
-                                        fraction_to_boundary(pr, np.array([st.d]), np.array([sd]),
-                                                             np.array([True]), np.array([pr.dlo]),
-                                                             np.array([True]), np.array([pr.dhi]), tau))
-                            ok, ftype, th_s, Cs = acceptable(st.Z + a_soc * sZ, st.d + a_soc * sd, a0)
+                                        fraction_to_boundary(pr, np.atleast_1d(st.d), np.atleast_1d(sd),
+                                                             allK, np.full(pr.K, pr.dlo), allK,
+                                                             np.full(pr.K, pr.dhi), tau))
+                            ok, ftype, th_s, Cs = acceptable(
+                                st.Z + a_soc * sZ, pr.th(np.atleast_1d(st.d) + a_soc * np.atleast_1d(sd)), a0)
                             n_soc += 1
                             if ok:
                                 dZ, dd, dlam, alpha = sZ, sd, sl, a_soc
@@ -483,9 +513,12 @@ class IPM:
                                                                np.zeros_like(pr.hasU), st.zL, tau),
                                           fraction_to_boundary(pr, st.zU, dzU, pr.hasU, np.zeros_like(st.zU),
                                                                np.zeros_like(pr.hasU), st.zU, tau),
-                                          fraction_to_boundary(pr, np.array([st.zLd, st.zUd]),
-                                                               np.array([dzLd, dzUd]), np.array([True, True]),
-                                                               np.zeros(2), np.array([False, False]), np.zeros(2),
+                                          fraction_to_boundary(pr, np.concatenate([np.atleast_1d(st.zLd),
+                                                                                   np.atleast_1d(st.zUd)]),
+                                                               np.concatenate([np.atleast_1d(dzLd),
+                                                                               np.atleast_1d(dzUd)]),
+                                                               np.ones(2 * pr.K, dtype=bool), np.zeros(2 * pr.K),
+                                                               np.zeros(2 * pr.K, dtype=bool), np.zeros(2 * pr.K),
                                                                tau))
                                 accepted = True
                                 break
@@ -519,27 +552,28 @@ class IPM:
                              dw=dw, dc=dc, ls=n_ls, soc=n_soc, d=st.d))
             if opt.verbose:
                 print(f"{k:4d} E0={E0:.3e} th={theta:.3e} mu={mu:.2e} a={alpha:.3e} az={a_z:.3e} "
-                      f"dw={dw:.1e} ls={n_ls} soc={n_soc} d={st.d:.6f}")
+                      f"dw={dw:.1e} ls={n_ls} soc={n_soc} d={st.d}")
             # accept the step
             st.Z = st.Z + alpha * dZ
-            st.d = st.d + alpha * dd
+            st.d = pr.th(np.atleast_1d(st.d) + alpha * np.atleast_1d(dd))
             st.lam = st.lam + alpha * dlam
             st.zL = st.zL + a_z * dzL
             st.zU = st.zU + a_z * dzU
-            st.zLd = st.zLd + a_z * dzLd
-            st.zUd = st.zUd + a_z * dzUd
+            st.zLd = pr.th(np.atleast_1d(st.zLd) + a_z * np.atleast_1d(dzLd))
+            st.zUd = pr.th(np.atleast_1d(st.zUd) + a_z * np.atleast_1d(dzUd))
             # kappa_Sigma safeguard of the bound multipliers (Eq. (16))
             sl, su = pr.sl(st.Z), pr.su(st.Z)
             ks = opt.kappa_sigma
             st.zL = np.where(pr.hasL, np.clip(st.zL, mu / (ks * sl), ks * mu / sl), 0.0)
             st.zU = np.where(pr.hasU, np.clip(st.zU, mu / (ks * su), ks * mu / su), 0.0)
-            sld, sud = st.d - pr.dlo, pr.dhi - st.d
-            st.zLd = min(max(st.zLd, mu / (ks * sld)), ks * mu / sld)
-            st.zUd = min(max(st.zUd, mu / (ks * sud)), ks * mu / sud)
+            dv = np.atleast_1d(st.d)
+            sld, sud = dv - pr.dlo, pr.dhi - dv
+            st.zLd = pr.th(np.minimum(np.maximum(np.atleast_1d(st.zLd), mu / (ks * sld)), ks * mu / sld))
+            st.zUd = pr.th(np.minimum(np.maximum(np.atleast_1d(st.zUd), mu / (ks * sud)), ks * mu / sud))
         # report the multipliers of the unscaled problem (min d): those of min w d over w
         w = pr.w
-        return Result(status, k, st.d, st.Z, st.lam / w, st.zL / w, st.zU / w, st.zLd / w, st.zUd / w,
-                      E0, mu, hist, base_iters)
+        return Result(status, k, st.d, st.Z, st.lam / w, st.zL / w, st.zU / w,
+                      pr.th(np.atleast_1d(st.zLd) / w), pr.th(np.atleast_1d(st.zUd) / w), E0, mu, hist, base_iters)
 
 
 def solve(P, F, opt=None, **kw):

@@ -20,6 +20,12 @@ scenarios onto d with a scalar Schur complement
     S_d = K_dd - sum_s bh_s^T K_s^{-1} bh_s,    bh_s = [0; b_s]
 
 whose sign completes the inertia of the whole matrix (Haynsworth inertia additivity).
+
+With a design vector of K entries (the general Eq. (8), dim theta > 1) the border is
+b_s = dc_s/dtheta (220 x K), K_dd a K x K block, and the Schur complement the K x K
+matrix S_theta = K_dd + dw I - sum_s bh_s^T K_s^{-1} bh_s, whose eigenvalue signs complete
+the inertia; the solve takes dtheta from S_theta dtheta = r_theta - sum_s bh_s^T v_s.  A
+2-D Jd (K = 1) keeps the scalar shapes throughout.
 """
 from __future__ import annotations
 
@@ -85,56 +91,71 @@ def scenario_matrix(W, sig, J, dw, dc):
     return K
 
 
+def _border(Jd):
+    """b_s as (S, n, K) and whether the shapes are scalar (K = 1 given as (S, n))."""
+    return (Jd[:, :, None], True) if Jd.ndim == 2 else (Jd, False)
+
+
 class SchurKKT:
     """Factorization of the bordered block-diagonal KKT matrix by per-scenario dense
-    Bunch-Kaufman LDL^T plus the scalar Schur complement on d."""
+    Bunch-Kaufman LDL^T plus the Schur complement on the design vector (a scalar for d,
+    K x K for K sections)."""
 
     def __init__(self, W, sig, J, Jd, Kdd, dw, dc, zero_tol=0.0):
         S, n, _ = W.shape
         self.S, self.n = S, n
+        b3, self.scalar = _border(Jd)
+        K = b3.shape[2]
         self.facs = []
         self.inertia_blocks = [0, 0, 0]
-        self.U = np.zeros((S, 2 * n))
-        self.bh = np.zeros((S, 2 * n))
-        self.bh[:, n:] = Jd
+        self.U = np.zeros((S, 2 * n, K))
+        self.bh = np.zeros((S, 2 * n, K))
+        self.bh[:, n:, :] = b3
         for s in range(S):
             f = BlockLDL(scenario_matrix(W[s], sig[s], J[s], dw, dc))
             for k, v in enumerate(f.inertia(zero_tol)):
                 self.inertia_blocks[k] += v
             self.facs.append(f)
             self.U[s] = f.solve(self.bh[s])
-        # Schur complement of the scenario blocks in the full matrix: a scalar
-        self.Sd = (Kdd + dw) - float(np.sum(self.bh * self.U))
+        # Schur complement of the scenario blocks in the full matrix (K x K)
+        self.Smat = (np.atleast_2d(Kdd) + dw * np.eye(K)) - np.einsum("sik,sil->kl", self.bh, self.U)
+        self.Sd = float(self.Smat[0, 0]) if self.scalar else self.Smat
 
     def inertia(self):
         p, m, z = self.inertia_blocks
-        if self.Sd > 0:
-            p += 1
-        elif self.Sd < 0:
-            m += 1
-        else:
-            z += 1
+        for e in np.linalg.eigvalsh(0.5 * (self.Smat + self.Smat.T)):
+            if e > 0:
+                p += 1
+            elif e < 0:
+                m += 1
+            else:
+                z += 1
         return p, m, z
 
     def solve(self, rz, rd, rc):
-        """Solve for (dz (S,n), dd, dl (S,n)) given right-hand sides of the same shapes."""
+        """Solve for (dz (S,n), dd, dl (S,n)) given right-hand sides of the same shapes
+        (rd and dd scalars for K = 1, else K-vectors)."""
         S, n = self.S, self.n
         V = np.zeros((S, 2 * n))
         for s in range(S):
             V[s] = self.facs[s].solve(np.concatenate([rz[s], rc[s]]))
-        dd = (rd - float(np.sum(self.bh * V))) / self.Sd
-        X = V - self.U * dd
-        return X[:, :n], dd, X[:, n:]
+        t = np.einsum("sik,si->k", self.bh, V)
+        dd = np.linalg.solve(self.Smat, np.atleast_1d(rd) - t)
+        X = V - np.einsum("sik,k->si", self.U, dd)
+        return X[:, :n], (float(dd[0]) if self.scalar else dd), X[:, n:]
 
 
 def kkt_residual(W, sig, J, Jd, Kdd, dw, dc, dz, dd, dl, rz, rd, rc):
     """r - K x of the bordered block-diagonal system above, by its block rows:
-    z rows (W + Sig + dw I) dz + J^T dl, the d row (K_dd + dw) dd + sum b^T dl and the
-    constraint rows J dz + b dd - dc dl."""
+    z rows (W + Sig + dw I) dz + J^T dl, the design rows (K_dd + dw I) dd + sum b^T dl and
+    the constraint rows J dz + b dd - dc dl."""
+    b3, scalar = _border(Jd)
+    K = b3.shape[2]
+    ddv = np.atleast_1d(dd)
     ez = rz - (np.einsum("sij,sj->si", W, dz) + (sig + dw) * dz + np.einsum("sri,sr->si", J, dl))
-    ed = rd - ((Kdd + dw) * dd + float(np.sum(Jd * dl)))
-    ec = rc - (np.einsum("sri,si->sr", J, dz) + Jd * dd - dc * dl)
-    return ez, ed, ec
+    ed = np.atleast_1d(rd) - ((np.atleast_2d(Kdd) + dw * np.eye(K)) @ ddv + np.einsum("srk,sr->k", b3, dl))
+    ec = rc - (np.einsum("sri,si->sr", J, dz) + np.einsum("srk,k->sr", b3, ddv) - dc * dl)
+    return ez, (float(ed[0]) if scalar else ed), ec
 
 
 def solve_refined(fac, W, sig, J, Jd, Kdd, dw, dc, rz, rd, rc, steps=2):
@@ -152,16 +173,18 @@ def solve_refined(fac, W, sig, J, Jd, Kdd, dw, dc, rz, rd, rc, steps=2):
 
 
 def monolithic_matrix(W, sig, J, Jd, Kdd, dw, dc):
-    """The whole KKT matrix, dense, unknowns ordered [d, (z_s, l_s) for each s]."""
+    """The whole KKT matrix, dense, unknowns ordered [d (K entries), (z_s, l_s) for each s]."""
     S, n, _ = W.shape
-    N = 1 + 2 * n * S
+    b3, _ = _border(Jd)
+    nk = b3.shape[2]
+    N = nk + 2 * n * S
     K = np.zeros((N, N))
-    K[0, 0] = Kdd + dw
+    K[:nk, :nk] = np.atleast_2d(Kdd) + dw * np.eye(nk)
     for s in range(S):
-        o = 1 + 2 * n * s
+        o = nk + 2 * n * s
         K[o:o + 2 * n, o:o + 2 * n] = scenario_matrix(W[s], sig[s], J[s], dw, dc)
-        K[o + n:o + 2 * n, 0] = Jd[s]
-        K[0, o + n:o + 2 * n] = Jd[s]
+        K[o + n:o + 2 * n, :nk] = b3[s]
+        K[:nk, o + n:o + 2 * n] = b3[s].T
     return K
 
 
@@ -169,15 +192,17 @@ def monolithic_solve(W, sig, J, Jd, Kdd, dw, dc, rz, rd, rc):
     """Dense Bunch-Kaufman LDL^T of the whole matrix (no Schur step); for tiny S only.
     Returns (dz, dd, dl, inertia)."""
     S, n, _ = W.shape
+    b3, scalar = _border(Jd)
+    nk = b3.shape[2]
     K = monolithic_matrix(W, sig, J, Jd, Kdd, dw, dc)
     rhs = np.zeros(K.shape[0])
-    rhs[0] = rd
+    rhs[:nk] = np.atleast_1d(rd)
     for s in range(S):
-        o = 1 + 2 * n * s
+        o = nk + 2 * n * s
         rhs[o:o + n] = rz[s]
         rhs[o + n:o + 2 * n] = rc[s]
     f = BlockLDL(K)
     x = f.solve(rhs)
-    dz = np.stack([x[1 + 2 * n * s:1 + 2 * n * s + n] for s in range(S)])
-    dl = np.stack([x[1 + 2 * n * s + n:1 + 2 * n * (s + 1)] for s in range(S)])
-    return dz, x[0], dl, f.inertia()
+    dz = np.stack([x[nk + 2 * n * s:nk + 2 * n * s + n] for s in range(S)])
+    dl = np.stack([x[nk + 2 * n * s + n:nk + 2 * n * (s + 1)] for s in range(S)])
+    return dz, (float(x[0]) if scalar else x[:nk].copy()), dl, f.inertia()

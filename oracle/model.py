@@ -22,6 +22,12 @@ zero and are not unknowns.  Side feeds f, F and heat duty Q are zero and P_n = P
 The per-scenario unknowns are ordered stage-major (index 22 n + j), as are the rows.
 The shared design variable is the diameter d.  Derivatives come from ad.Jet, never from
 hand-derived formulas.
+
+Design vector with more than one entry (the general Eq. (8) with dim theta > 1): with
+P["n_sections"] = K > 1 the column is split into K sections of consecutive stages
+(stage n in section floor(n K / N)), each with its own diameter theta_k; the hydraulic
+row (10b) of a stage uses its section's diameter.  d is then an array of K entries and
+the d-derivatives gain a last axis of K; a scalar d (K = 1) keeps the scalar shapes.
 """
 from __future__ import annotations
 
@@ -76,6 +82,22 @@ def feed_rows():
 
 
 FEED = feed_rows()
+
+
+def n_sections(P):
+    """Number of column sections K, each with its own diameter (1: the case study)."""
+    return int(P.get("n_sections", 1))
+
+
+def stage_sections(K):
+    """Section of every stage: floor(n K / N) (consecutive stages, sizes within one)."""
+    return (np.arange(N) * K) // N
+
+
+def section_weights(K):
+    """Objective weight of each section's diameter: its share of the stages (its share
+    of the column height), so that K = 1 gives the objective d."""
+    return np.bincount(stage_sections(K), minlength=K) / float(N)
 
 
 def local_to_scenario(n):
@@ -190,7 +212,8 @@ def _local_values(P, F, Z, d):
     plus boolean masks of which 'above'/'below' entries are unknowns."""
     S = Z.shape[0]
     Zs = Z.reshape(S, N, NV)
-    vals = np.zeros((K_LOC, S, N), dtype=np.result_type(Z.dtype, np.asarray(d).dtype, np.float64))
+    dv = np.atleast_1d(np.asarray(d))
+    vals = np.zeros((K_LOC, S, N), dtype=np.result_type(Z.dtype, dv.dtype, np.float64))
     vals[:NV] = np.moveaxis(Zs, 2, 0)
     sx = np.asarray(P["sx"])
     sy = np.asarray(P["sy"])
@@ -208,7 +231,7 @@ def _local_values(P, F, Z, d):
     vals[B_Y:B_Y + 4, :, 0] = F[FEED["y0"]:FEED["y0"] + 4, :] / sy[:, None]
     vals[B_V, :, 0] = F[FEED["V0"], :]
     vals[B_T, :, 0] = F[FEED["T0"], :] / P["sT"]
-    vals[I_D] = d
+    vals[I_D] = dv[stage_sections(dv.size)][None, :]     # each stage its section's diameter
     active = np.ones((K_LOC, S, N), dtype=bool)
     active[A_X:B_Y, :, N - 1] = False
     active[B_Y:I_D, :, 0] = False
@@ -231,9 +254,10 @@ def derivatives(P, F, Z, d, lam, rows_only=False):
     Returns (C, J, Jd, W, Wdd):
       C   (S, 220)       residuals
       J   (S, 220, 220)  dc_s/dz_s (dense per scenario)
-      Jd  (S, 220)       dc_s/dd
+      Jd  (S, 220)       dc_s/dd                   ((S, 220, K) for an array d of K)
       W   (S, 220, 220)  Hessian of lam_s^T c_s with respect to z_s (symmetric)
-      Wdd (S,)           d^2 (lam_s^T c_s)/dd^2   (the objective d is linear)
+      Wdd (S,)           d^2 (lam_s^T c_s)/dd^2    ((S, K): diagonal in the sections)
+    (the objective is linear in d).
     """
     S = Z.shape[0]
     vals, active, pres = _local_values(P, F, Z, d)
@@ -255,19 +279,23 @@ def derivatives(P, F, Z, d, lam, rows_only=False):
     C = C.reshape(S, N, NR).reshape(S, NS)
     G = G.reshape(S, N, NR, K_LOC)
     Hl = Hl.reshape(S, N, K_LOC, K_LOC)
+    K = np.size(d)
+    sec = stage_sections(K)
     J = np.zeros((S, NS, NS))
-    Jd = np.zeros((S, NS))
+    Jd = np.zeros((S, NS, K))
     W = np.zeros((S, NS, NS))
-    Wdd = np.zeros(S)
+    Wdd = np.zeros((S, K))
     for n in range(N):
         m = local_to_scenario(n)
         rws = NR * n + np.arange(NR)
         loc = np.nonzero(m >= 0)[0]
         J[:, rws[:, None], m[loc][None, :]] += G[:, n][:, :, loc]
-        Jd[:, rws] = G[:, n, :, I_D]
+        Jd[:, rws, sec[n]] = G[:, n, :, I_D]
         if not rows_only:
             W[:, m[loc][:, None], m[loc][None, :]] += Hl[:, n][:, loc[:, None], loc[None, :]]
-            Wdd += Hl[:, n, I_D, I_D]
+            Wdd[:, sec[n]] += Hl[:, n, I_D, I_D]
+    if np.ndim(d) == 0:
+        return C, J, Jd[:, :, 0], W, Wdd[:, 0]
     return C, J, Jd, W, Wdd
 
 
