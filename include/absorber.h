@@ -84,6 +84,12 @@ typedef struct abs_params {
     double henry_a, henry_b, henry_m, henry_w, rho_L;
     double hL_ref[9], hL_cpa[9], hL_cpb[9], hL_dh[9];
     double hV_ref[4], hV_cpa[4], hV_cpb[4], hV_dh[4];
+    int32_t n_sections;   /* design vector (Eq. (8) with dim theta = n_sections): 1 the case
+                             study's single diameter d; 2 a column of two sections of 5
+                             stages (bottom, top), each with its own diameter theta_k in
+                             [d_lo, d_hi] used by its stages' hydraulic rows (10b), the
+                             objective (theta_0 + theta_1) / 2.  Design entries of a primal
+                             vector: problem q's theta_k at 220 ld + k P + q (P problems) */
 } abs_params;
 
 typedef struct abs_sizes {
@@ -344,6 +350,8 @@ typedef struct abs_result {
     int32_t resto_phases;        /* feasibility restoration phases entered */
     int64_t kind_launches[ABS_N_KINDS];  /* launches per kernel kind issued by the host during
                                     the solve (eager runs, captures; a replayed graph adds none) */
+    double d_sec[2];             /* the design entries (abs_params.n_sections of them; d_sec[0] =
+                                    d); obj = their stage-weighted sum */
 } abs_result;
 
 /* Diagnostic: measured throughput of dependent-free fused multiply-adds on the current
@@ -383,9 +391,10 @@ abs_status ipm_solve(abs_problem* h, const abs_options* opt, const double* warm_
  * min d (the solver's scaled multipliers divided by each problem's obj_scaling), so that
  * with x_out and y_out of the same solve they give every term of the optimality error
  * E_0.  Unknowns without a lower (upper) bound carry 0.
- *   zl_out, zu_out  device primal vectors in the handle's layout (the d slot(s) receive
- *                   each problem's multiplier of d >= d_lo / d <= d_hi), or NULL.
- *   zd_out          host, 2 P doubles (z_L of each problem's d, then z_U), or NULL.
+ *   zl_out, zu_out  device primal vectors in the handle's layout (the design slots receive
+ *                   each problem's multipliers of d >= d_lo / d <= d_hi), or NULL.
+ *   zd_out          host, 2 K P doubles (K = n_sections: z_L of the design entries, entry k
+ *                   of problem q at k P + q, then z_U likewise), or NULL.
  * Errors: ABS_ERR_ARG (no finished solve on the handle), ABS_ERR_CUDA.  Synchronous. */
 abs_status absorber_bound_multipliers(abs_problem* h, double* zl_out, double* zu_out, double* zd_out,
                                       abs_stream_t stream);

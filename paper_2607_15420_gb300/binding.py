@@ -34,7 +34,7 @@ class AbsParams(C.Structure):
                 ("hL_ref", C.c_double * 9), ("hL_cpa", C.c_double * 9), ("hL_cpb", C.c_double * 9),
                 ("hL_dh", C.c_double * 9),
                 ("hV_ref", C.c_double * 4), ("hV_cpa", C.c_double * 4), ("hV_cpb", C.c_double * 4),
-                ("hV_dh", C.c_double * 4)]
+                ("hV_dh", C.c_double * 4), ("n_sections", C.c_int32)]
 
 
 class AbsSizes(C.Structure):
@@ -87,7 +87,7 @@ class AbsResult(C.Structure):
                 ("warm_ms", C.c_double), ("warm_E0", C.c_double), ("cold_E0", C.c_double),
                 ("warm_theta", C.c_double), ("cold_theta", C.c_double), ("tiles", C.c_int32 * 4),
                 ("graph_replays", C.c_int32), ("resto_phases", C.c_int32),
-                ("kind_launches", C.c_int64 * 16)]
+                ("kind_launches", C.c_int64 * 16), ("d_sec", C.c_double * 2)]
 
 
 class AbsTrainOptions(C.Structure):
@@ -184,6 +184,9 @@ class AbsorberError(RuntimeError):
 def make_params(P: dict) -> AbsParams:
     p = AbsParams()
     for name, _ in AbsParams._fields_:
+        if name == "n_sections":
+            p.n_sections = int(P.get("n_sections", 1))
+            continue
         v = P[name]
         if isinstance(v, (tuple, list)):
             arr = getattr(p, name)
@@ -298,8 +301,13 @@ class Problem:
             pass
 
     @property
+    def K(self):
+        """Design entries (column sections with their own diameter)."""
+        return int(self.params.n_sections)
+
+    @property
     def n_primal(self):
-        return NSC * self.ld + 1
+        return NSC * self.ld + self.K
 
     @property
     def n_row(self):
@@ -352,7 +360,7 @@ class Problem:
         vectors zl_out, zu_out; returns the host array [z_L(d) per problem, z_U(d) per
         problem]."""
         nprob = int(lib().absorber_num_problems(self.h))
-        zd = np.zeros(2 * nprob)
+        zd = np.zeros(2 * self.K * nprob)
         self._check(lib().absorber_bound_multipliers(self.h, _ptr(zl_out), _ptr(zu_out), zd.ctypes.data,
                                                      _stream(stream)))
         return zd
@@ -386,14 +394,16 @@ class Problem:
         out = np.zeros(self.n_primal if d is not None else self.n_row)
         out[:NSC * self.ld].reshape(NSC, self.ld)[:, :S] = np.asarray(Z).T
         if d is not None:
-            out[NSC * self.ld] = d
+            out[NSC * self.ld:NSC * self.ld + self.K] = np.atleast_1d(d)
         return out
 
     def from_soa(self, v):
         """flat primal/row vector -> ((S, 220), d or None)."""
         v = np.asarray(v)
         Z = v[:NSC * self.ld].reshape(NSC, self.ld)[:, :self.S].T.copy()
-        d = float(v[NSC * self.ld]) if v.shape[0] > NSC * self.ld else None
+        d = None
+        if v.shape[0] > NSC * self.ld:
+            d = float(v[NSC * self.ld]) if self.K == 1 else v[NSC * self.ld:NSC * self.ld + self.K].copy()
         return Z, d
 
     def values_to_scen(self, vals, nnz):
@@ -426,7 +436,7 @@ class Batch(Problem):
 
     @property
     def n_primal(self):
-        return NSC * self.ld + self.ld
+        return NSC * self.ld + self.K * self.ld
 
     def ipm_solve(self, options=None, x_out=None, y_out=None, stream=None):
         res = (AbsResult * self.P)()
@@ -441,7 +451,10 @@ class Batch(Problem):
         out = []
         for q in range(self.P):
             Zq = Z[:, self.off[q]:self.off[q + 1]].T.copy()
-            dq = float(v[NSC * self.ld + q]) if v.shape[0] > NSC * self.ld else None
+            dq = None
+            if v.shape[0] > NSC * self.ld:
+                dv = v[NSC * self.ld + q + self.P * np.arange(self.K)]
+                dq = float(dv[0]) if self.K == 1 else dv.copy()
             out.append((Zq, dq))
         return out
 

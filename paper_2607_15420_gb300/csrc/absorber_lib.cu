@@ -353,7 +353,8 @@ struct DevOpt {
     double dw0, dw_min, dw_max, kw_minus, kw_plus, kw_plus_bar, kappa_soc, obj_scaling, refine_tol;
     double dlo, dhi, u_max;
     double dc_bar, kappa_c;     // delta_c = dc_bar mu^kappa_c when a pivot is zero (block LDL^T)
-    int max_iter, max_refine, max_ls, soc_max, resto_max, kkt;
+    double wsec[KSEC];          // objective weights of the design entries
+    int max_iter, max_refine, max_ls, soc_max, resto_max, kkt, nsec;
 };
 
 // one problem's state of the method
@@ -361,11 +362,15 @@ struct DState {
     int status, iters, ls_trials, soc_steps, inertia_corr, refine_steps, fallbacks, esc_scen;
     int have_theta0, tiny, ftype, soc_taken, ls, nls, nsoc, soc_new, nfilt, stepped;
     int resto, resto_it, resto_bt, resto_phases, resto_now;   // feasibility restoration state
-    double w, d, zLd, zUd, mu, tau, theta_max, theta_min, dw_last;
+    double w, mu, tau, theta_max, theta_min, dw_last;
+    // the design vector (section diameters; one entry for the single d) and its bound
+    // multipliers, slacks, steps
+    double d[KSEC], zLd[KSEC], zUd[KSEC], jtl_d[KSEC], sld[KSEC], sud[KSEC], dd[KSEC];
+    double dzLd[KSEC], dzUd[KSEC], sd[KSEC], Kdd[KSEC], rd[KSEC];
     double theta_k, ra, th_r, blog_r;              // restoration: entry theta, step, trial theta / logs
-    double E0, inf_pr, inf_du, theta, phi, jtl_d, sld, sud, dd;
-    double a_max, a_z, gphi, dzLd, dzUd, alpha, a_min, a0, th_old, a_soc, sd, ct_coef;
-    double Kdd, dw, Sd, rd, resid;
+    double E0, inf_pr, inf_du, theta, phi;
+    double a_max, a_z, gphi, alpha, a_min, a0, th_old, a_soc, ct_coef;
+    double dw, Sd, S01, S11, resid;                // Sd (and S01, S11): the design Schur complement
     int ic_trial;                                  // Algorithm IC trial of the block LDL^T path
     double dc;                                     // its delta_c of the iteration
 };
@@ -389,7 +394,7 @@ struct Prof {
     size_t used = 0;
 };
 
-constexpr int KMAX = 9;          // partial values per (scenario, stage) thread, at most
+constexpr int KMAX = 10;         // partial values per (scenario, stage) thread, at most
 constexpr int PS_RING = 16;      // pinned staging buffers for per-problem scalar uploads
 constexpr int CHUNK = RED_CHUNK;  // reduction elements per chunk
 
@@ -491,7 +496,8 @@ namespace {
 // vector pool indices (each NSC * ld + ld doubles; the problems' d slots at NSC * ld + p)
 enum {
     V_X, V_LAM, V_ZL, V_ZU, V_C, V_JTL, V_SIG, V_RZ, V_RC, V_P, V_Q, V_DZ, V_DL, V_DZL, V_DZU,
-    V_G, V_RHOZ, V_RHOC, V_CZ, V_CL, V_ONE, V_CT, V_RCS, V_RCN, V_SZ, V_SL, V_HQ, V_T, V_IL, V_IU, V_QL, V_COUNT
+    V_G, V_RHOZ, V_RHOC, V_CZ, V_CL, V_ONE, V_CT, V_RCS, V_RCN, V_SZ, V_SL, V_HQ, V_T, V_IL, V_IU, V_QL, V_Q1, V_HQ1,
+    V_COUNT
 };
 
 abs_status fail(abs_problem* h, abs_status st, const std::string& msg) {
@@ -508,7 +514,9 @@ abs_status fail(abs_problem* h, abs_status st, const std::string& msg) {
                         std::string(#call) + ": " + cudaGetErrorString(e_));             \
     } while (0)
 
-int64_t vsize(const abs_problem* h) { return (int64_t)NSC * h->ld + h->ld; }
+// vector length: the scenario entries, then room for every problem's design entries
+// (problem p's section k at NSC ld + k NP + p)
+int64_t vsize(const abs_problem* h) { return (int64_t)NSC * h->ld + (int64_t)h->P.nsec * h->ld; }
 double* V(abs_problem* h, int k) { return h->vec + (int64_t)k * vsize(h); }
 dim3 grid2(const abs_problem* h) { return dim3((unsigned)((h->S + kThr - 1) / kThr), N_STAGES); }
 // the trial evaluation (FP64-pipe-bound, limited by registers) in 32-thread blocks: the
@@ -688,9 +696,9 @@ abs_status reduce(abs_problem* h, cudaStream_t st, int K, const RedOps& ops, int
         reduce_kernel<k><<<(unsigned)h->nchunk, RED_T, 0, st>>>(h->part, h->ld, ops, h->chunks, h->nchunk, h->pchunk, \
                                                                  h->ps, h->NP, flag, h->cred, h->rcnt, h->red, hout, ds); \
         break;
-        RK(1) RK(2) RK(3) RK(4) RK(5) RK(6) RK(7) RK(8) RK(9)
+        RK(1) RK(2) RK(3) RK(4) RK(5) RK(6) RK(7) RK(8) RK(9) RK(10)
 #undef RK
-        default: return fail(h, ABS_ERR_ARG, "reduction with more than 9 planes");
+        default: return fail(h, ABS_ERR_ARG, "reduction with more than 10 planes");
     }
     abs_status r = launch_check(h, KD_REDUCE, K);
     if (r != ABS_OK) return r;
@@ -846,22 +854,24 @@ abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaS
 
 template <class T, int NR_, int W>
 void solve_w(abs_problem* h, const double* jac, const double* x, const double* r0, const double* r1, double* o0,
-             double* o1, cudaStream_t st) {
+             double* o1, cudaStream_t st, int bsec) {
     const int pi = std::is_same<T, float>::value ? ABS_PREC_FP32 : ABS_PREC_FP64;
     solve_warp_kernel<T, NR_, W, std::is_same<T, float>::value><<<gridw(h, W), 32 * W, 0, st>>>(
-        h->P, (int)h->S, h->ld, view(h), jac, (const T*)h->LUp[pi], h->piv, (const T*)h->Gp[pi], x, r0, r1, o0, o1);
+        h->P, (int)h->S, h->ld, view(h), jac, (const T*)h->LUp[pi], h->piv, (const T*)h->Gp[pi], x, r0, r1, o0, o1,
+        bsec);
 }
 
+// bsec: the design entry whose border column a null right-hand side stands for
 template <class T, int NR_>
 abs_status solve_launch(abs_problem* h, const double* jac, const double* x, const double* r0, const double* r1,
-                        double* o0, double* o1, cudaStream_t st) {
+                        double* o0, double* o1, cudaStream_t st, int bsec = 0) {
     prof_begin(h, K_SOLVE, st);
     auto go = [&](int w) {
         switch (w) {
-            case 1: solve_w<T, NR_, 1>(h, jac, x, r0, r1, o0, o1, st); break;
-            case 2: solve_w<T, NR_, 2>(h, jac, x, r0, r1, o0, o1, st); break;
-            case 8: solve_w<T, NR_, 8>(h, jac, x, r0, r1, o0, o1, st); break;
-            default: solve_w<T, NR_, 4>(h, jac, x, r0, r1, o0, o1, st); break;
+            case 1: solve_w<T, NR_, 1>(h, jac, x, r0, r1, o0, o1, st, bsec); break;
+            case 2: solve_w<T, NR_, 2>(h, jac, x, r0, r1, o0, o1, st, bsec); break;
+            case 8: solve_w<T, NR_, 8>(h, jac, x, r0, r1, o0, o1, st, bsec); break;
+            default: solve_w<T, NR_, 4>(h, jac, x, r0, r1, o0, o1, st, bsec); break;
         }
         return launch_check(h, KD_SOLVE);
     };
@@ -873,20 +883,21 @@ abs_status solve_launch(abs_problem* h, const double* jac, const double* x, cons
 // mixed factor precision (escalated scenarios FP64, the others FP32), default shape
 template <int NR_>
 abs_status solve_mixed(abs_problem* h, const double* jac, const double* x, const double* r0, const double* r1,
-                       double* o0, double* o1, cudaStream_t st) {
+                       double* o0, double* o1, cudaStream_t st, int bsec = 0) {
     prof_begin(h, K_SOLVE, st);
     solve_mixed_kernel<NR_, WPB_S><<<gridw(h, WPB_S), 32 * WPB_S, 0, st>>>(
         h->P, (int)h->S, h->ld, view(h), jac, (const float*)h->LUp[ABS_PREC_FP32], (const double*)h->LUp[ABS_PREC_FP64],
-        h->piv, (const float*)h->Gp[ABS_PREC_FP32], (const double*)h->Gp[ABS_PREC_FP64], h->esc, x, r0, r1, o0, o1);
+        h->piv, (const float*)h->Gp[ABS_PREC_FP32], (const double*)h->Gp[ABS_PREC_FP64], h->esc, x, r0, r1, o0, o1,
+        bsec);
     prof_end(h, st);
     return launch_check(h, KD_SOLVE);
 }
 
 abs_status solve_j(abs_problem* h, int prec, const double* jac, const double* x, const double* r0, double* o0,
-                   cudaStream_t st) {
-    if (prec == ABS_PREC_MIXED) return solve_mixed<1>(h, jac, x, r0, nullptr, o0, nullptr, st);
-    if (prec == ABS_PREC_FP32) return solve_launch<float, 1>(h, jac, x, r0, nullptr, o0, nullptr, st);
-    return solve_launch<double, 1>(h, jac, x, r0, nullptr, o0, nullptr, st);
+                   cudaStream_t st, int bsec = 0) {
+    if (prec == ABS_PREC_MIXED) return solve_mixed<1>(h, jac, x, r0, nullptr, o0, nullptr, st, bsec);
+    if (prec == ABS_PREC_FP32) return solve_launch<float, 1>(h, jac, x, r0, nullptr, o0, nullptr, st, bsec);
+    return solve_launch<double, 1>(h, jac, x, r0, nullptr, o0, nullptr, st, bsec);
 }
 
 // two right-hand sides in one launch (a null r means b = dc/dd)
@@ -971,9 +982,14 @@ abs_status kkt_factor_core(abs_problem* h, const KKTSys& K, const double* x, cud
     r = K.pre_rc ? solve_j2(h, K.prec, K.jac, x, K.pre_rc, nullptr, V(h, V_P), V(h, V_Q), st)
                  : solve_j(h, K.prec, K.jac, x, nullptr, V(h, V_Q), st);
     if (r != ABS_OK) return r;
+    // a second design entry: q1 = J^-1 b1, b1 the border column of the second section
+    const bool two = h->P.nsec == 2;
+    if (two && (r = solve_j(h, K.prec, K.jac, x, nullptr, V(h, V_Q1), st, 1)) != ABS_OK) return r;
     schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, nullptr, V(h, V_Q),
-                                             nullptr, h->sing, h->part, SCHUR_DD, V(h, V_HQ), nullptr);
+                                             nullptr, h->sing, h->part, SCHUR_DD, V(h, V_HQ), nullptr,
+                                             two ? V(h, V_Q1) : nullptr, two ? V(h, V_HQ1) : nullptr);
     if ((r = launch_check(h, KD_SCHUR)) != ABS_OK) return r;
+    if (two) return reduce(h, st, 9, make_ops({RSUM, RSUM, RSUM, RSUM, RSUM, RSUM, RSUM, RSUM, RSUM}), PS_ACT, fetch);
     return reduce(h, st, 6, make_ops({RSUM, RSUM, RSUM, RSUM, RSUM, RSUM}), PS_ACT, fetch);
 }
 
@@ -997,14 +1013,17 @@ abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, 
         return launch_check(h, KD_DZ);
     }
     if (!have_p && (r = solve_j(h, K.prec, K.jac, x, rc, V(h, V_P), st)) != ABS_OK) return r;
+    const bool two = h->P.nsec == 2;
     schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q),
-                                             rz, nullptr, h->part, SCHUR_RHS, nullptr, V(h, V_T));
+                                             rz, nullptr, h->part, SCHUR_RHS, nullptr, V(h, V_T),
+                                             two ? V(h, V_Q1) : nullptr, nullptr);
     if ((r = launch_check(h, KD_SCHUR)) != ABS_OK) return r;
     if ((r = reduce(h, st, 4, make_ops({RSUM, RSUM, RSUM, RSUM}), PS_ACT, false)) != ABS_OK) return r;
-    finalize_dd_kernel<<<(unsigned)((h->NP + 127) / 128), 128, 0, st>>>(h->ld, view(h), h->red, dz);
+    finalize_dd_kernel<<<(unsigned)((h->NP + 127) / 128), 128, 0, st>>>(h->ld, view(h), h->red, dz, h->P.nsec);
     if ((r = launch_check(h, KD_VEC)) != ABS_OK) return r;
     dz_fast_kernel<<<gride(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), V(h, V_P), V(h, V_Q), V(h, V_T),
-                                              V(h, V_HQ), dz, V(h, V_G));
+                                              V(h, V_HQ), dz, V(h, V_G), two ? V(h, V_Q1) : nullptr,
+                                              two ? V(h, V_HQ1) : nullptr);
     if ((r = launch_check(h, KD_DZ)) != ABS_OK) return r;
     return solve_jt(h, K.prec, K.jac, V(h, V_G), dl, st);
 }
@@ -1084,7 +1103,7 @@ bool make_params(const abs_params* p, Params* P) {
     for (int j = 0; j < 4; ++j) P->hV0[j] = p->hV_ref[j] + p->hV_dh[j];
     P->Tlo_s = p->T_lo / p->sT;
     P->Thi_s = p->T_hi / p->sT;
-    return true;
+    return p->n_sections >= 1 && p->n_sections <= KSEC;
 }
 
 abs_status init_handle(abs_problem* h, const abs_params* p, int64_t S) {
@@ -1093,10 +1112,10 @@ abs_status init_handle(abs_problem* h, const abs_params* p, int64_t S) {
     h->S = S;
     h->ld = (S + 31) / 32 * 32;
     h->aparams = *p;
-    if (!make_params(p, &h->P)) return fail(h, ABS_ERR_ARG, "scales must be positive");
+    if (!make_params(p, &h->P)) return fail(h, ABS_ERR_ARG, "scales must be positive, n_sections 1 or 2");
     const PatternTables& T = pattern();
     h->nnzJ = (int)T.jrow.size();
-    h->nnzH = (int)T.hrow.size();
+    h->nnzH = (int)T.hrow.size() + h->P.nsec - 1;   // one d-d entry per section
     h->NP = 1;
     h->off = {0, (int)S};
     CK(cudaMalloc(&h->feed, sizeof(double) * (size_t)NFEED * h->ld));
@@ -1290,6 +1309,7 @@ int64_t abs_struct_size(int which) {
 
 abs_status absorber_pattern(const abs_problem* h, int32_t* jrow, int32_t* jcol, int32_t* hrow, int32_t* hcol) {
     if (!h) return fail(nullptr, ABS_ERR_ARG, "bad argument");
+    if (h->P.nsec != 1) return fail(const_cast<abs_problem*>(h), ABS_ERR_ARG, "absorber_pattern: one section only");
     return abs_scenario_pattern(nullptr, nullptr, jrow, jcol, hrow, hcol);
 }
 
@@ -1313,17 +1333,27 @@ abs_status eval_grad_jac_hess(abs_problem* h, const double* x, const double* lam
                                                             lambda, h->feed, c, nullptr, nullptr, nullptr);
     abs_status r = launch_check(h, KD_EVAL);
     if (r != ABS_OK) return r;
+    // the objective sum_k w_k theta_k (w = 1, the single d, for one section)
+    const int K = h->P.nsec;
+    double gk[KSEC];
+    for (int k = 0; k < K; ++k) gk[k] = obj_factor * sec_weight(k, K);
     if (grad) {
-        CK(cudaMemsetAsync(grad, 0, sizeof(double) * (size_t)((int64_t)NSC * h->ld + 1), st));
-        CK(cudaMemcpyAsync(grad + (int64_t)NSC * h->ld, &obj_factor, sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(grad, 0, sizeof(double) * (size_t)((int64_t)NSC * h->ld + (K - 1) * h->NP + 1), st));
+        for (int k = 0; k < K; ++k)
+            CK(cudaMemcpyAsync(grad + (int64_t)NSC * h->ld + (int64_t)k * h->NP, &gk[k], sizeof(double),
+                               cudaMemcpyHostToDevice, st));
     }
     if (f) {
-        double d = 0.0;
-        CK(cudaMemcpyAsync(&d, x + (int64_t)NSC * h->ld, sizeof(double), cudaMemcpyDeviceToHost, st));
+        double d[KSEC] = {0.0, 0.0};
+        for (int k = 0; k < K; ++k)
+            CK(cudaMemcpyAsync(&d[k], x + (int64_t)NSC * h->ld + (int64_t)k * h->NP, sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        *f = obj_factor * d;
+        double fv = 0.0;
+        for (int k = 0; k < K; ++k) fv += gk[k] * d[k];
+        *f = fv;
     } else if (grad) {
-        CK(cudaStreamSynchronize(st));   // obj_factor lives on this stack frame
+        CK(cudaStreamSynchronize(st));   // gk lives on this stack frame
     }
     return ABS_OK;
 }
@@ -1339,7 +1369,8 @@ abs_status absorber_scenario_status(const abs_problem* ch, int32_t* status) {
 
 abs_status absorber_paper_layout(abs_problem* h, const double* x, double* out, abs_stream_t stream) {
     if (!h || !x || !out) return fail(h, ABS_ERR_ARG, "bad argument");
-    if (h->NP != 1) return fail(h, ABS_ERR_ARG, "absorber_paper_layout needs a single-problem handle");
+    if (h->NP != 1 || h->P.nsec != 1)
+        return fail(h, ABS_ERR_ARG, "absorber_paper_layout needs a single-problem, single-diameter handle");
     cudaStream_t st = (cudaStream_t)stream;
     paper_layout_kernel<<<grid2(h), kThr, 0, st>>>(h->P, (int)h->S, h->ld, x, out);
     return launch_check(h, KD_VEC);
@@ -1473,7 +1504,8 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
     double* psd = (double*)sing + NA_SING;
     // the problem's constants (derived fields as absorber_create computes them)
     Params P;
-    if (!make_params(p, &P)) return fail(nullptr, ABS_ERR_ARG, "kkt_newton_noalloc: scales must be positive");
+    if (!make_params(p, &P) || P.nsec != 1)
+        return fail(nullptr, ABS_ERR_ARG, "kkt_newton_noalloc: scales must be positive, one section");
     const dim3 g2((unsigned)((S + kThr - 1) / kThr), N_STAGES);
     const dim3 gq((unsigned)((S + QS_SCEN - 1) / QS_SCEN), N_STAGES);
     const int64_t od = (int64_t)NSC * ld;

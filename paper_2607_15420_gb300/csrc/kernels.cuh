@@ -153,7 +153,7 @@ struct DevEmit {
 
 __device__ inline void load_stage(const Params& P, int S, int64_t ld, const double* __restrict__ x,
                                   const double* __restrict__ dx, double alpha, const double* __restrict__ feed,
-                                  int s, int n, int p, StageIn& in) {
+                                  int s, int n, int p, int NP, StageIn& in) {
     const double* xs = x + s;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
@@ -191,7 +191,7 @@ __device__ inline void load_stage(const Params& P, int S, int64_t ld, const doub
         in.qb[4] = feed[(int64_t)F_V0 * ld + s];
         in.qb[5] = feed[(int64_t)F_T0 * ld + s] / P.sT;
     }
-    const int64_t od = (int64_t)NSC * ld + p;   // the problem's d slot
+    const int64_t od = (int64_t)NSC * ld + (int64_t)stage_sec(n, P.nsec) * NP + p;   // its section's diameter
     in.d = x[od] + (dx ? alpha * dx[od] : 0.0);
     in.P = feed[(int64_t)F_P * ld + s];
 }
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(128) eval_kernel(const Params P, int S, int64_
         dx = (b.ps && psv(b, PS_SOC, p) != 0.0) ? dxB : dxA;
         alpha = psv(b, PS_ALPHA, p);
     }
-    load_stage(P, S, ld, x, dx, alpha, feed, s, n, p, in);
+    load_stage(P, S, ld, x, dx, alpha, feed, s, n, p, b.NP, in);
     StageLam L;
     if (WH) {
 #pragma unroll
@@ -246,11 +246,15 @@ __global__ void __launch_bounds__(128) eval_kernel(const Params P, int S, int64_
     }
     stage_eval(P, in, WH ? &L : nullptr, em);
     if (WH && n == 0) {
-        // the scenario's share of d-d: -u_max pi / 2 * sum_n lambda_hydraulic
-        double sl = 0.0;
+        // the scenario's share of d-d: -u_max pi / 2 * sum_n lambda_hydraulic, one entry per
+        // section (its stages' rows)
+        for (int k = 0; k < P.nsec; ++k) {
+            double sl = 0.0;
 #pragma unroll
-        for (int m = 0; m < N_STAGES; ++m) sl += lam[(int64_t)(NR * m + R_H) * ld + s];
-        hes[(int64_t)(NHS * N_STAGES) * ld + s] = -P.u_max * M_PI * 0.5 * sl;
+            for (int m = 0; m < N_STAGES; ++m)
+                if (stage_sec(m, P.nsec) == k) sl += lam[(int64_t)(NR * m + R_H) * ld + s];
+            hes[(int64_t)(NHS * N_STAGES + k) * ld + s] = -P.u_max * M_PI * 0.5 * sl;
+        }
     }
     if (part) {
         // sum of ln(slack) over the stage's 18 bounds as the logarithm of their product: the
@@ -314,8 +318,8 @@ __device__ __forceinline__ double jt_one(int64_t ld, const double* __restrict__ 
     return a;
 }
 
-// (J v)_r for row r of stage n; v a primal vector, vd the d step (the hydraulic row's d
-// column)
+// (J v)_r for row r of stage n; v a primal vector, vd the step of the stage's section
+// diameter (the hydraulic row's d column)
 __device__ __forceinline__ double jv_one(int64_t ld, const double* __restrict__ jac, const double* __restrict__ v, double vd,
                                 int s, int n, int r) {
     const int t = stage_type(n);

@@ -624,7 +624,9 @@ struct CouplingFetch {
     }
 };
 
-// J_s x = r (NRHS right-hand sides; a null r[k] means b = dc/dd), one warp per scenario.
+// J_s x = r (NRHS right-hand sides; a null r[k] means b = dc/dtheta_bsec, the border
+// column of design entry bsec: nonzero in the hydraulic rows of that section's stages),
+// one warp per scenario.
 // INV (FP32 only): LU holds the stage-block inverses of factor_gj_kernel and each block
 // solve is a matrix-vector product; otherwise LU factors and row order.
 // the block solves of scenario s (problem pr) by its warp; A: the warp's shared-memory
@@ -634,12 +636,13 @@ __device__ __forceinline__ void solve_warp_body(const Params& P, int s, int pr, 
                                                 const double* __restrict__ jac, const T* __restrict__ LU,
                                                 const unsigned char* __restrict__ piv, const T* __restrict__ G,
                                                 const double* x, const double* r0, const double* r1, double* o0,
-                                                double* o1, T (*A)[PADL]) {
+                                                double* o1, T (*A)[PADL], int NP, int bsec) {
     static_assert(!INV || sizeof(T) == 4, "stage-block inverses are FP32");
     int perm = lane, ipos = lane;
     const double* rr[2] = {r0, r1};
     double* oo[2] = {o0, o1};
-    const T bval = (T)(-P.u_max * M_PI * 0.5 * x[(int64_t)NSC * ld + pr]);   // b = dc/dd of the problem
+    // b = dc/dtheta of the problem's design entry bsec
+    const T bval = (T)(-P.u_max * M_PI * 0.5 * x[(int64_t)NSC * ld + (int64_t)bsec * NP + pr]);
     const bool row = lane < NV;
     T y[NRHS];
 #pragma unroll
@@ -661,7 +664,8 @@ __device__ __forceinline__ void solve_warp_body(const Params& P, int s, int pr, 
         const CouplingFetch cc = cnext;
         T w[NRHS];
 #pragma unroll
-        for (int k = 0; k < NRHS; ++k) w[k] = rr[k] ? (T)rnext[k] : ((lane == R_H) ? bval : T(0));
+        for (int k = 0; k < NRHS; ++k)
+            w[k] = rr[k] ? (T)rnext[k] : ((lane == R_H && stage_sec(n, P.nsec) == bsec) ? bval : T(0));
         if (n + 1 < N_STAGES) {
             if constexpr (INV) ipre.fetch((const float*)LU, piv, s, n + 1, lane);
             else pre.fetch(LU, piv, s, n + 1, lane);
@@ -732,13 +736,14 @@ __global__ void __launch_bounds__(32 * WPB) solve_warp_kernel(const Params P, in
                                                                 const unsigned char* __restrict__ piv,
                                                                 const T* __restrict__ G, const double* x,
                                                                 const double* r0, const double* r1, double* o0,
-                                                                double* o1) {
+                                                                double* o1, int bsec = 0) {
     __shared__ T sL[INV ? 1 : WPB][NV][PADL];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * WPB + warp;
     const int pr = live_prob(b, s, S, PS_ACT);
     if (pr < 0) return;
-    solve_warp_body<T, NRHS, INV>(P, s, pr, lane, ld, jac, LU, piv, G, x, r0, r1, o0, o1, sL[INV ? 0 : warp]);
+    solve_warp_body<T, NRHS, INV>(P, s, pr, lane, ld, jac, LU, piv, G, x, r0, r1, o0, o1, sL[INV ? 0 : warp], b.NP,
+                                  bsec);
 }
 
 // the same with factors of mixed precision: scenarios with esc[s] != 0 use their FP64 LU
@@ -753,14 +758,18 @@ __global__ void __launch_bounds__(32 * WPB) solve_mixed_kernel(const Params P, i
                                                                  const double* __restrict__ G64,
                                                                  const int* __restrict__ esc, const double* x,
                                                                  const double* r0, const double* r1, double* o0,
-                                                                 double* o1) {
+                                                                 double* o1, int bsec = 0) {
     __shared__ double sL[WPB][NV][PADL];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int s = blockIdx.x * WPB + warp;
     const int pr = live_prob(b, s, S, PS_ACT);
     if (pr < 0) return;
-    if (esc[s]) solve_warp_body<double, NRHS, false>(P, s, pr, lane, ld, jac, LU, piv, G64, x, r0, r1, o0, o1, sL[warp]);
-    else solve_warp_body<float, NRHS, true>(P, s, pr, lane, ld, jac, AI, piv, G32, x, r0, r1, o0, o1, nullptr);
+    if (esc[s])
+        solve_warp_body<double, NRHS, false>(P, s, pr, lane, ld, jac, LU, piv, G64, x, r0, r1, o0, o1, sL[warp], b.NP,
+                                             bsec);
+    else
+        solve_warp_body<float, NRHS, true>(P, s, pr, lane, ld, jac, AI, piv, G32, x, r0, r1, o0, o1, nullptr, b.NP,
+                                           bsec);
 }
 
 // stage unknown j -> its index among the 11 stream-from-above unknowns (-1: none)

@@ -80,12 +80,25 @@ struct Params {
     double henry_a, henry_b, henry_m, henry_w, rho_L;
     double hL_ref[9], hL_cpa[9], hL_cpb[9], hL_dh[9];
     double hV_ref[4], hV_cpa[4], hV_cpb[4], hV_dh[4];
+    int nsec;        // column sections, each with its own diameter (1 or 2)
     // derived at creation
     double lnsx[9];
     double hL0[9];   // hL_ref + hL_dh
     double hV0[4];
     double Tlo_s, Thi_s;   // T_lo / sT, T_hi / sT: the scaled temperature bounds
 };
+
+constexpr int KSEC = 2;   // most column sections (design-vector entries)
+
+// the section of stage n among K: consecutive stages, floor(n K / N)
+__host__ __device__ constexpr int stage_sec(int n, int K) { return (n * K) / N_STAGES; }
+
+// objective weight of section k's diameter: its share of the stages
+__host__ __device__ inline double sec_weight(int k, int K) {
+    int c = 0;
+    for (int n = 0; n < N_STAGES; ++n) c += stage_sec(n, K) == k ? 1 : 0;
+    return (double)c / N_STAGES;
+}
 
 struct StageIn {
     double q[NV];     // own scaled unknowns

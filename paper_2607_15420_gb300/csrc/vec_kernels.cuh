@@ -12,7 +12,9 @@
 namespace absorber {
 
 // Schur: r_d and S_d per problem; PS_BASE: 1 if the problem starts from the base states
-enum PsExtra { PS_RD = PS_COUNT, PS_SD, PS_BASE, PS_DC, PS_NFIELDS };
+// PS_RD / PS_SD: the first design entry's right-hand side and the Schur complement (its
+// (0,0) entry with two sections, whose other entries are PS_SD01, PS_SD11, PS_RD1)
+enum PsExtra { PS_RD = PS_COUNT, PS_SD, PS_BASE, PS_DC, PS_SD01, PS_SD11, PS_RD1, PS_NFIELDS };
 
 __device__ inline double lo_of(const Params& P, int j) { return j == LT ? P.Tlo_s : 0.0; }
 __device__ inline double hi_of(const Params& P, int /*j*/) { return P.Thi_s; }
@@ -53,8 +55,9 @@ __device__ __forceinline__ void group_combine(double (&v)[K], double (*sm)[NC][3
 
 // J^T lambda for the stage's unknowns and the optimality-error partials:
 // [0] max |J^T l - zL + zU|, [1] sum |lambda|, [2] sum |zL| + |zU|, [3] max and [4] min
-// complementarity product over bounded unknowns, [5] the stage's hydraulic multiplier.
-// QS threads per (scenario, stage); grid (ceil(S / QS_SCEN), N_STAGES), 128 threads.
+// complementarity product over bounded unknowns, [5] the stage's hydraulic multiplier
+// (two sections: [5] for the first section's stages, [6] for the second's, each 0 on the
+// other's).  QS threads per (scenario, stage); grid (ceil(S / QS_SCEN), N_STAGES), 128 threads.
 __global__ void __launch_bounds__(128) dual_kernel(const Params P, int S, int64_t ld, const BView b,
                                                    const double* __restrict__ jac, const double* __restrict__ lam,
                                                    const double* __restrict__ x, const double* __restrict__ zL,
@@ -93,8 +96,15 @@ __global__ void __launch_bounds__(128) dual_kernel(const Params P, int S, int64_
     constexpr int ops[5] = {RMAX, RSUM, RSUM, RMAX, RMIN};
     group_combine<6, 5>(v, sm, ops);
     if (!live || q != 0) return;
-    v[5] = lam[(int64_t)(NR * n + R_H) * ld + s];
-    store_partials<6>(v, part, ld, s, n);
+    const double lh = lam[(int64_t)(NR * n + R_H) * ld + s];
+    if (P.nsec == 1) {
+        v[5] = lh;
+        store_partials<6>(v, part, ld, s, n);
+    } else {
+        const bool top = stage_sec(n, P.nsec) == 1;
+        const double w7[7] = {v[0], v[1], v[2], v[3], v[4], top ? 0.0 : lh, top ? lh : 0.0};
+        store_partials<7>(w7, part, ld, s, n);
+    }
 }
 
 // Elementwise kernels below: one thread per (entry v, scenario s), grid (ceil(S / 128),
@@ -134,25 +144,29 @@ __global__ void __launch_bounds__(128) rhs_kernel(const Params P, int S, int64_t
     rc[o] = -c[o];
 }
 
-// Schur partial sums with H = W + Sigma (W optional): with SCHUR_DD [0] q^T H q,
-// [1] q^T q; with SCHUR_RHS [2] q^T (r - H p), [3] q^T p; always [4] the scenario's d-d
-// Hessian entry and [5] the singular flag.  Terms not asked for are 0.  Optionally the
-// vectors behind them: hq = H q (SCHUR_DD), t = r - H p (SCHUR_RHS), from which
-// dz_fast_kernel forms g without another product with H.
+// Schur partial sums with H = W + Sigma (W optional), q = J^-1 b for the design entries
+// (q1: the second section's, or null for one section): with SCHUR_DD [0] q^T H q,
+// [1] q^T q and, with q1, [2] q^T H q1, [3] q^T q1, [6] q1^T H q1, [7] q1^T q1; with
+// SCHUR_RHS [2] q^T (r - H p), [3] q^T p and, with q1, [0] q1^T (r - H p), [1] q1^T p;
+// always [4] (and with q1 [8]) the scenario's d-d Hessian entry of each section and [5]
+// the singular flag.  Terms not asked for are 0.  Optionally the vectors behind them:
+// hq = H q, hq1 = H q1 (SCHUR_DD), t = r - H p (SCHUR_RHS), from which dz_fast_kernel
+// forms g without another product with H.
 enum { SCHUR_DD = 1, SCHUR_RHS = 2 };
-// QS threads per (scenario, stage).
+
 __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BView b, const double* __restrict__ hes,
                                                     const double* __restrict__ sig, bool use_w,
                                                     const double* __restrict__ p, const double* __restrict__ q,
                                                     const double* __restrict__ r, const int* __restrict__ sing,
                                                     double* part, int terms, double* __restrict__ hq,
-                                                    double* __restrict__ tv) {
-    __shared__ double sm[QS][4][32];
+                                                    double* __restrict__ tv, const double* __restrict__ q1 = nullptr,
+                                                    double* __restrict__ hq1 = nullptr) {
+    __shared__ double sm[QS][6][32];
     const int g = threadIdx.x >> 5;
     const int s = blockIdx.x * QS_SCEN + (threadIdx.x & 31);
     const int n = blockIdx.y;
     const bool live = live_prob(b, s, S, PS_ACT) >= 0;
-    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    double a[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (live) {
 #pragma unroll
         for (int j0 = 0; j0 < NV; j0 += QS) {
@@ -160,31 +174,52 @@ __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BVi
             if (j < NV) {
                 const int64_t o = (int64_t)(NV * n + j) * ld + s;
                 const double qj = q[o];
+                const double q1j = q1 ? q1[o] : 0.0;
                 if (terms & SCHUR_DD) {
                     const double hqj = hv_one(ld, hes, sig, 0.0, use_w, q, s, n, j);
                     if (hq) hq[o] = hqj;
-                    v[0] += qj * hqj;
-                    v[1] += qj * qj;
+                    a[0] += qj * hqj;
+                    a[1] += qj * qj;
+                    if (q1) {
+                        const double hq1j = hv_one(ld, hes, sig, 0.0, use_w, q1, s, n, j);
+                        if (hq1) hq1[o] = hq1j;
+                        a[2] += qj * hq1j;
+                        a[3] += qj * q1j;
+                        a[4] += q1j * hq1j;
+                        a[5] += q1j * q1j;
+                    }
                 }
                 if (terms & SCHUR_RHS) {
                     if (r) {
                         const double tj = r[o] - (p ? hv_one(ld, hes, sig, 0.0, use_w, p, s, n, j) : 0.0);
                         if (tv) tv[o] = tj;
-                        v[2] += qj * tj;
+                        a[2] += qj * tj;
+                        if (q1) a[0] += q1j * tj;
                     }
-                    if (p) v[3] += qj * p[o];
+                    if (p) {
+                        a[3] += qj * p[o];
+                        if (q1) a[1] += q1j * p[o];
+                    }
                 }
             }
         }
     }
-    constexpr int ops[4] = {RSUM, RSUM, RSUM, RSUM};
-    group_combine<6, 4>(v, sm, ops);
+    constexpr int ops[6] = {RSUM, RSUM, RSUM, RSUM, RSUM, RSUM};
+    group_combine<6, 6>(a, sm, ops);
     if (!live || g != 0) return;
+    double v[9] = {a[0], a[1], a[2], a[3], 0.0, 0.0, a[4], a[5], 0.0};
     if (n == 0) {
-        if (use_w) v[4] = hes[(int64_t)(NHS * N_STAGES) * ld + s];
+        if (use_w) {
+            v[4] = hes[(int64_t)(NHS * N_STAGES) * ld + s];
+            if (q1) v[8] = hes[(int64_t)(NHS * N_STAGES + 1) * ld + s];
+        }
         if (sing) v[5] = (double)sing[s];
     }
-    store_partials<6>(v, part, ld, s, n);
+    if (q1) store_partials<9>(v, part, ld, s, n);
+    else {
+        const double w6[6] = {v[0], v[1], v[2], v[3], v[4], v[5]};
+        store_partials<6>(w6, part, ld, s, n);
+    }
 }
 
 // dz = p - q dd ;  g = r - (W + Sigma + dw I) dz ;  dd, dw of the slot's problem.
@@ -216,11 +251,13 @@ __global__ void __launch_bounds__(128) dz_kernel(int S, int64_t ld, const BView 
 }
 
 // dz = p - q dd and g = r - (H + dw I) dz from the Schur pass's vectors t = r - H p and
-// hq = H q (H = W + Sigma): g = t - dw p + dd (hq + dw q), no product with H.  Elementwise.
+// hq = H q (H = W + Sigma): g = t - dw p + dd (hq + dw q), no product with H; with a
+// second design entry also - q1 dd1 and + dd1 (hq1 + dw q1).  Elementwise.
 __global__ void __launch_bounds__(128) dz_fast_kernel(int S, int64_t ld, const BView b, const double* __restrict__ p,
                                                       const double* __restrict__ q, const double* __restrict__ t,
                                                       const double* __restrict__ hq, double* __restrict__ dz,
-                                                      double* __restrict__ g) {
+                                                      double* __restrict__ g, const double* __restrict__ q1 = nullptr,
+                                                      const double* __restrict__ hq1 = nullptr) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     const int pr = live_prob(b, s, S, PS_ACT);
     if (pr < 0) return;
@@ -228,8 +265,15 @@ __global__ void __launch_bounds__(128) dz_fast_kernel(int S, int64_t ld, const B
     const double dw = b.ps ? psv(b, PS_DW, pr) : 0.0;
     const int64_t o = (int64_t)blockIdx.y * ld + s;
     const double pj = p[o], qj = q[o];
-    dz[o] = pj - qj * dd;
-    g[o] = t[o] - dw * pj + dd * (hq[o] + dw * qj);
+    if (!q1) {
+        dz[o] = pj - qj * dd;
+        g[o] = t[o] - dw * pj + dd * (hq[o] + dw * qj);
+    } else {
+        const double dd1 = dz[(int64_t)NSC * ld + b.NP + pr];
+        const double q1j = q1[o];
+        dz[o] = pj - qj * dd - q1j * dd1;
+        g[o] = t[o] - dw * pj + dd * (hq[o] + dw * qj) + dd1 * (hq1[o] + dw * q1j);
+    }
 }
 
 // residual of the full KKT system: rho_z = r_z - (H dz + J^T dl), rho_c = r_c - (J dz + b dd).
@@ -246,16 +290,17 @@ __global__ void __launch_bounds__(128) kkt_residual_kernel(int S, int64_t ld, co
                                                            const double* __restrict__ dz, const double* __restrict__ dl,
                                                            const double* __restrict__ rz, const double* __restrict__ rc,
                                                            double* __restrict__ rhoz, double* __restrict__ rhoc,
-                                                           double* part) {
+                                                           double* part, int nsec = 1) {
     __shared__ double sm[QS][5][32];
     const int gq = threadIdx.x >> 5;
     const int s = blockIdx.x * QS_SCEN + (threadIdx.x & 31);
     const int n = blockIdx.y;
     const int pr = live_prob(b, s, S, PS_ACT);
     const bool live = pr >= 0;
+    const int sec = stage_sec(n, nsec);
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (live) {
-        const double dd = dz[(int64_t)NSC * ld + pr];
+        const double dd = dz[(int64_t)NSC * ld + (int64_t)sec * b.NP + pr];   // the stage's section
         for (int j = gq; j < NV; j += QS) {
             const int64_t o = (int64_t)(NV * n + j) * ld + s;
             const double a = g[o] - jt_one(ld, jac, dlast, s, n, j);
@@ -272,8 +317,15 @@ __global__ void __launch_bounds__(128) kkt_residual_kernel(int S, int64_t ld, co
     constexpr int ops[5] = {RMAX, RMAX, RSUM, RMAX, RMAX};   // [2] is set below
     group_combine<5, 5>(v, sm, ops);
     if (!live || gq != 0) return;
-    v[2] = dl[(int64_t)(NR * n + R_H) * ld + s];
-    store_partials<5>(v, part, ld, s, n);
+    const double dlh = dl[(int64_t)(NR * n + R_H) * ld + s];
+    if (nsec == 1) {
+        v[2] = dlh;
+        store_partials<5>(v, part, ld, s, n);
+    } else {
+        // the hydraulic dl by section: [2] the first's, [5] the second's
+        const double w6[6] = {v[0], v[1], sec == 0 ? dlh : 0.0, v[3], v[4], sec == 1 ? dlh : 0.0};
+        store_partials<6>(w6, part, ld, s, n);
+    }
 }
 
 // bound-multiplier steps and step-size limits (mu, tau of the problem):
@@ -410,12 +462,16 @@ __global__ void __launch_bounds__(128) accept_kernel(const Params P, int S, int6
     }
 }
 
-// the problems' own step of d: x[d_p] += alpha_p dz[d_p]   (one thread per problem)
-__global__ void dstep_kernel(int64_t ld, const BView b, double* __restrict__ x, const double* __restrict__ dz) {
+// the problems' own step of their design entries: x[d_p] += alpha_p dz[d_p]   (one thread
+// per problem)
+__global__ void dstep_kernel(int64_t ld, const BView b, double* __restrict__ x, const double* __restrict__ dz,
+                             int nsec = 1) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= b.NP || psv(b, PS_ACT, p) == 0.0) return;
-    const int64_t o = (int64_t)NSC * ld + p;
-    x[o] += psv(b, PS_ALPHA, p) * dz[o];
+    for (int k = 0; k < nsec; ++k) {
+        const int64_t o = (int64_t)NSC * ld + (int64_t)k * b.NP + p;
+        x[o] += psv(b, PS_ALPHA, p) * dz[o];
+    }
 }
 
 // starting point: every stage copies the inlet streams (or, with base and the problem's
@@ -432,7 +488,7 @@ __global__ void __launch_bounds__(128) init_kernel(const Params P, int S, int64_
     const int n = blockIdx.y;
     const int pr = live_prob(b, s, S, PS_ACT);
     if (pr < 0) return;
-    const double d = x[(int64_t)NSC * ld + pr];
+    const double d = x[(int64_t)NSC * ld + (int64_t)stage_sec(n, P.nsec) * b.NP + pr];   // the stage's section
     double q[NV];
     if (base && (!b.ps || psv(b, PS_BASE, pr) != 0.0)) {
 #pragma unroll
@@ -528,14 +584,15 @@ __global__ void axpby_kernel(int S, int64_t ld, const BView b, int flag, int afi
     }
 }
 
-// y1 += x1 (per-scenario part and the problems' d slots) and y2 += x2 (per-scenario part).
-// Elementwise.
+// y1 += x1 (per-scenario part and the problems' design slots) and y2 += x2 (per-scenario
+// part).  Elementwise.
 __global__ void __launch_bounds__(128) axpy2_kernel(int S, int64_t ld, const BView b, const double* __restrict__ x1,
                                                     double* __restrict__ y1, const double* __restrict__ x2,
-                                                    double* __restrict__ y2) {
+                                                    double* __restrict__ y2, int nsec = 1) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (blockIdx.y == 0 && s < b.NP && (!b.ps || psv(b, PS_ACT, s) != 0.0))
-        y1[(int64_t)NSC * ld + s] += x1[(int64_t)NSC * ld + s];
+        for (int k = 0; k < nsec; ++k)
+            y1[(int64_t)NSC * ld + (int64_t)k * b.NP + s] += x1[(int64_t)NSC * ld + (int64_t)k * b.NP + s];
     if (live_prob(b, s, S, PS_ACT) < 0) return;
     const int64_t o = (int64_t)blockIdx.y * ld + s;
     y1[o] += x1[o];
@@ -650,12 +707,25 @@ __global__ void __launch_bounds__(RED_T) reduce_kernel(const double* __restrict_
 
 // dd_p = (r_d - (beta - dw qp)) / S_d from the Schur sums red[2][p], red[3][p]; into the
 // problem's d slot of dz
-__global__ void finalize_dd_kernel(int64_t ld, const BView b, const double* __restrict__ red, double* __restrict__ dz) {
+__global__ void finalize_dd_kernel(int64_t ld, const BView b, const double* __restrict__ red, double* __restrict__ dz,
+                                   int nsec = 1) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= b.NP || psv(b, PS_ACT, p) == 0.0) return;
     const double beta = red[2 * (int64_t)b.NP + p], qp = red[3 * (int64_t)b.NP + p];
     const double dw = psv(b, PS_DW, p);
-    dz[(int64_t)NSC * ld + p] = (psv(b, PS_RD, p) - (beta - dw * qp)) / psv(b, PS_SD, p);
+    if (nsec == 1) {
+        dz[(int64_t)NSC * ld + p] = (psv(b, PS_RD, p) - (beta - dw * qp)) / psv(b, PS_SD, p);
+        return;
+    }
+    // two design entries: S_theta [dd0; dd1] = r_theta - (beta - dw qp), S_theta symmetric
+    // positive definite (Algorithm IC), solved by its LDL^T
+    const double beta1 = red[0 * (int64_t)b.NP + p], qp1 = red[1 * (int64_t)b.NP + p];
+    const double r0 = psv(b, PS_RD, p) - (beta - dw * qp), r1 = psv(b, PS_RD1, p) - (beta1 - dw * qp1);
+    const double s00 = psv(b, PS_SD, p), s01 = psv(b, PS_SD01, p), s11 = psv(b, PS_SD11, p);
+    const double l = s01 / s00, e = s11 - l * s01;
+    const double dd1 = (r1 - l * r0) / e;
+    dz[(int64_t)NSC * ld + p] = (r0 - s01 * dd1) / s00;
+    dz[(int64_t)NSC * ld + b.NP + p] = dd1;
 }
 
 }  // namespace absorber
