@@ -349,6 +349,25 @@ def compare_forms(B, prob, net, reps):
     return out
 
 
+def two_section_form(B, ai, P, reps):
+    """The same 5000-scenario workload with a two-section column (a design vector of two
+    diameters, 2 x 2 Schur complement): FP64 and FP32 + refinement from the default start,
+    against the one-section solve of the same form."""
+    F = ai.workload_feeds("absorber-S5000-tn5-seed2")
+    out = {"scenarios": int(F.shape[1]), "n_sections": 2}
+    for nsec in (1, 2):
+        prob = B.Problem(dict(P, n_sections=nsec), F)
+        for form, prec in (("fp64", B.PREC_FP64), ("fp32", B.PREC_FP32)):
+            prob.ipm_solve(options(B, prec))
+            sec, rs = timed(lambda: prob.ipm_solve(options(B, prec)), reps)
+            r = rs[0]
+            out[f"{form}-{nsec}-section"] = {"solve_time_s": sec, "iters": r.iters, "base_iters": r.base_iters,
+                                            "status": r.status, "E0": r.E0,
+                                            "d_sections": list(r.d_sec)[:nsec]}
+        del prob
+    return out
+
+
 def batched_form(B, ai, reps):
     """64 independent design problems, scenario counts log-uniform in [50, 2000], solved
     as one batch (FP32 factors + FP64 refinement) against one-by-one solves."""
@@ -569,6 +588,7 @@ def main():
         forms["absorber-S20000-u10-seed4"] = compare_forms(B, p20, net, reps=2)
         del p20
         forms["batched"] = batched_form(B, ai, reps=2)
+        forms["two-section"] = two_section_form(B, ai, P, reps=2)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

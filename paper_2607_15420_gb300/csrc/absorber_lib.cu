@@ -985,9 +985,14 @@ abs_status kkt_factor_core(abs_problem* h, const KKTSys& K, const double* x, cud
     // a second design entry: q1 = J^-1 b1, b1 the border column of the second section
     const bool two = h->P.nsec == 2;
     if (two && (r = solve_j(h, K.prec, K.jac, x, nullptr, V(h, V_Q1), st, 1)) != ABS_OK) return r;
-    schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, nullptr, V(h, V_Q),
-                                             nullptr, h->sing, h->part, SCHUR_DD, V(h, V_HQ), nullptr,
-                                             two ? V(h, V_Q1) : nullptr, two ? V(h, V_HQ1) : nullptr);
+    if (two)
+        schur_kernel<true><<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, nullptr,
+                                                       V(h, V_Q), nullptr, h->sing, h->part, SCHUR_DD, V(h, V_HQ),
+                                                       nullptr, V(h, V_Q1), V(h, V_HQ1));
+    else
+        schur_kernel<false><<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, nullptr,
+                                                        V(h, V_Q), nullptr, h->sing, h->part, SCHUR_DD, V(h, V_HQ),
+                                                        nullptr);
     if ((r = launch_check(h, KD_SCHUR)) != ABS_OK) return r;
     if (two) return reduce(h, st, 9, make_ops({RSUM, RSUM, RSUM, RSUM, RSUM, RSUM, RSUM, RSUM, RSUM}), PS_ACT, fetch);
     return reduce(h, st, 6, make_ops({RSUM, RSUM, RSUM, RSUM, RSUM, RSUM}), PS_ACT, fetch);
@@ -1014,9 +1019,14 @@ abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, 
     }
     if (!have_p && (r = solve_j(h, K.prec, K.jac, x, rc, V(h, V_P), st)) != ABS_OK) return r;
     const bool two = h->P.nsec == 2;
-    schur_kernel<<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P), V(h, V_Q),
-                                             rz, nullptr, h->part, SCHUR_RHS, nullptr, V(h, V_T),
-                                             two ? V(h, V_Q1) : nullptr, nullptr);
+    if (two)
+        schur_kernel<true><<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P),
+                                                       V(h, V_Q), rz, nullptr, h->part, SCHUR_RHS, nullptr, V(h, V_T),
+                                                       V(h, V_Q1), nullptr);
+    else
+        schur_kernel<false><<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P),
+                                                        V(h, V_Q), rz, nullptr, h->part, SCHUR_RHS, nullptr,
+                                                        V(h, V_T));
     if ((r = launch_check(h, KD_SCHUR)) != ABS_OK) return r;
     if ((r = reduce(h, st, 4, make_ops({RSUM, RSUM, RSUM, RSUM}), PS_ACT, false)) != ABS_OK) return r;
     finalize_dd_kernel<<<(unsigned)((h->NP + 127) / 128), 128, 0, st>>>(h->ld, view(h), h->red, dz, h->P.nsec);
@@ -1527,7 +1537,7 @@ extern "C" abs_status kkt_newton_noalloc(const abs_params* p, int64_t S, int64_t
     solve_warp_kernel<double, 2><<<gs, 32 * WPB_S, 0, st>>>(P, (int)S, ld, bv, jac_vals, LU, piv, G, x, rhs_c, nullptr,
                                                             pv, qv);
     NA_LAUNCHED();
-    schur_kernel<<<gq, kThr, 0, st>>>((int)S, ld, bv, hess_vals, sigma, true, pv, qv, rhs_x, sing, part,
+    schur_kernel<false><<<gq, kThr, 0, st>>>((int)S, ld, bv, hess_vals, sigma, true, pv, qv, rhs_x, sing, part,
                                       SCHUR_DD | SCHUR_RHS, nullptr, nullptr);
     NA_LAUNCHED();
     double hx[2] = {0.0, 0.0};   // Sigma_dd and r_d

@@ -151,9 +151,11 @@ __global__ void __launch_bounds__(128) rhs_kernel(const Params P, int S, int64_t
 // always [4] (and with q1 [8]) the scenario's d-d Hessian entry of each section and [5]
 // the singular flag.  Terms not asked for are 0.  Optionally the vectors behind them:
 // hq = H q, hq1 = H q1 (SCHUR_DD), t = r - H p (SCHUR_RHS), from which dz_fast_kernel
-// forms g without another product with H.
+// forms g without another product with H.  TWO: q1 given (the one-entry instance keeps the
+// one-entry work and shared memory).
 enum { SCHUR_DD = 1, SCHUR_RHS = 2 };
 
+template <bool TWO>
 __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BView b, const double* __restrict__ hes,
                                                     const double* __restrict__ sig, bool use_w,
                                                     const double* __restrict__ p, const double* __restrict__ q,
@@ -161,11 +163,13 @@ __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BVi
                                                     double* part, int terms, double* __restrict__ hq,
                                                     double* __restrict__ tv, const double* __restrict__ q1 = nullptr,
                                                     double* __restrict__ hq1 = nullptr) {
-    __shared__ double sm[QS][6][32];
+    constexpr int NC = TWO ? 6 : 4;   // sums combined over the block's row groups
+    __shared__ double sm[QS][NC][32];
     const int g = threadIdx.x >> 5;
     const int s = blockIdx.x * QS_SCEN + (threadIdx.x & 31);
     const int n = blockIdx.y;
     const bool live = live_prob(b, s, S, PS_ACT) >= 0;
+    if (!TWO) q1 = nullptr;
     double a[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (live) {
 #pragma unroll
@@ -174,13 +178,13 @@ __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BVi
             if (j < NV) {
                 const int64_t o = (int64_t)(NV * n + j) * ld + s;
                 const double qj = q[o];
-                const double q1j = q1 ? q1[o] : 0.0;
+                const double q1j = TWO ? q1[o] : 0.0;
                 if (terms & SCHUR_DD) {
                     const double hqj = hv_one(ld, hes, sig, 0.0, use_w, q, s, n, j);
                     if (hq) hq[o] = hqj;
                     a[0] += qj * hqj;
                     a[1] += qj * qj;
-                    if (q1) {
+                    if (TWO) {
                         const double hq1j = hv_one(ld, hes, sig, 0.0, use_w, q1, s, n, j);
                         if (hq1) hq1[o] = hq1j;
                         a[2] += qj * hq1j;
@@ -194,28 +198,28 @@ __global__ void __launch_bounds__(128) schur_kernel(int S, int64_t ld, const BVi
                         const double tj = r[o] - (p ? hv_one(ld, hes, sig, 0.0, use_w, p, s, n, j) : 0.0);
                         if (tv) tv[o] = tj;
                         a[2] += qj * tj;
-                        if (q1) a[0] += q1j * tj;
+                        if (TWO) a[0] += q1j * tj;
                     }
                     if (p) {
                         a[3] += qj * p[o];
-                        if (q1) a[1] += q1j * p[o];
+                        if (TWO) a[1] += q1j * p[o];
                     }
                 }
             }
         }
     }
-    constexpr int ops[6] = {RSUM, RSUM, RSUM, RSUM, RSUM, RSUM};
-    group_combine<6, 6>(a, sm, ops);
+    constexpr int ops[NC] = {};   // RSUM (0) for every sum
+    group_combine<6, NC>(a, sm, ops);
     if (!live || g != 0) return;
     double v[9] = {a[0], a[1], a[2], a[3], 0.0, 0.0, a[4], a[5], 0.0};
     if (n == 0) {
         if (use_w) {
             v[4] = hes[(int64_t)(NHS * N_STAGES) * ld + s];
-            if (q1) v[8] = hes[(int64_t)(NHS * N_STAGES + 1) * ld + s];
+            if (TWO) v[8] = hes[(int64_t)(NHS * N_STAGES + 1) * ld + s];
         }
         if (sing) v[5] = (double)sing[s];
     }
-    if (q1) store_partials<9>(v, part, ld, s, n);
+    if (TWO) store_partials<9>(v, part, ld, s, n);
     else {
         const double w6[6] = {v[0], v[1], v[2], v[3], v[4], v[5]};
         store_partials<6>(w6, part, ld, s, n);
