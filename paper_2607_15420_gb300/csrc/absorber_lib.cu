@@ -1108,6 +1108,7 @@ bool make_params(const abs_params* p, Params* P) {
     for (int l = 0; l < 9; ++l) {
         if (!(p->sx[l] > 0.0)) return false;
         P->lnsx[l] = std::log(p->sx[l]);
+        for (int k = 0; k < 5; ++k) P->lnsxr[k] += nu(l, k) * P->lnsx[l];
         P->hL0[l] = p->hL_ref[l] + p->hL_dh[l];
     }
     for (int j = 0; j < 4; ++j) P->hV0[j] = p->hV_ref[j] + p->hV_dh[j];

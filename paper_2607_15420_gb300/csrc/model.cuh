@@ -83,6 +83,7 @@ struct Params {
     int nsec;        // column sections, each with its own diameter (1 or 2)
     // derived at creation
     double lnsx[9];
+    double lnsxr[5];   // sum_c nu_ck ln sx_c: the scales' share of each reaction's quotient
     double hL0[9];   // hL_ref + hL_dh
     double hV0[4];
     double Tlo_s, Thi_s;   // T_lo / sT, T_hi / sT: the scaled temperature bounds
@@ -180,10 +181,26 @@ __host__ __device__ inline void stage_eval(const Params& P, const StageIn& in, c
     const double ps1 = ps * bT2;                                        // dPsat/dT
     const double ps2 = ps * (bT2 * bT2 - 2.0 * P.psat_b * iTc * iTc * iTc);  // d2Psat/dT2
     const double iPr = 1.0 / Pr;
-    // reciprocals of the scaled liquid fractions (derivatives of their logarithms)
+    // reciprocals of the scaled liquid fractions (derivatives of their logarithms), all
+    // nine from one division: prefix products p_c = q_0 ... q_c, r = 1 / p_8, then walking
+    // back 1/q_c = r p_{c-1} and r <- r q_c (the fractions are positive and O(1))
     double iq[9];
+    if (E::want_jac || E::want_hes) {
+        double pre[9];
+        pre[0] = in.q[LX];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) iq[c] = (E::want_jac || E::want_hes) ? 1.0 / in.q[LX + c] : 0.0;
+        for (int c = 1; c < 9; ++c) pre[c] = pre[c - 1] * in.q[LX + c];
+        double r = 1.0 / pre[8];
+#pragma unroll
+        for (int c = 8; c > 0; --c) {
+            iq[c] = r * pre[c - 1];
+            r *= in.q[LX + c];
+        }
+        iq[0] = r;
+    } else {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) iq[c] = 0.0;
+    }
 
     // ---- (9b) Henry coefficient --------------------------------------------------------
     double am = 0, ac = 0, aw = 0;
@@ -222,17 +239,20 @@ __host__ __device__ inline void stage_eval(const Params& P, const StageIn& in, c
         }
         e.res(R_VH, Pr * y[1] - x[8] * ps);
         e.res(R_VC, Pr * y[0] - rhoH * x7);
-        // ln of each liquid fraction once (every species enters several reactions)
-        double lx[9];
-#pragma unroll
-        for (int c = 0; c < 9; ++c) lx[c] = log(in.q[LX + c]) + P.lnsx[c];
+        // sum_c nu_ck ln x_c as one logarithm per reaction: every nu is +-1, so it is
+        // ln(prod over products of q_c / prod over reactants of q_c) + sum_c nu_ck ln sx_c
+        // (the scaled fractions are O(1): the quotients stay far from over- and underflow)
         const double lT = log(T);
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            double r = -(P.KE_A[k] + P.KE_B[k] * invT + P.KE_C[k] * lT + P.KE_D[k] * T);
+            double num = 1.0, den = 1.0;
 #pragma unroll
-            for (int c = 0; c < 9; ++c)
-                if (nu(c, k) != 0) r += nu(c, k) * lx[c];
+            for (int c = 0; c < 9; ++c) {
+                if (nu(c, k) > 0) num *= in.q[LX + c];
+                if (nu(c, k) < 0) den *= in.q[LX + c];
+            }
+            const double r = -(P.KE_A[k] + P.KE_B[k] * invT + P.KE_C[k] * lT + P.KE_D[k] * T) + P.lnsxr[k] +
+                             log(num / den);
             e.res(R_RX + k, r);
         }
         double sx_ = -1.0, sy_ = -1.0;
