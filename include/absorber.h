@@ -90,6 +90,9 @@ typedef struct abs_params {
                              [d_lo, d_hi] used by its stages' hydraulic rows (10b), the
                              objective (theta_0 + theta_1) / 2.  Design entries of a primal
                              vector: problem q's theta_k at 220 ld + k P + q (P problems) */
+    double dp_stage;      /* pressure relation (7) with a specified drop: stage n (0 bottom, 9
+                             top) at P_n = P + (9 - n) dp_stage, P the feed's absorber (top)
+                             pressure; 0 (the case study): every stage at P */
 } abs_params;
 
 typedef struct abs_sizes {

@@ -84,6 +84,14 @@ def feed_rows():
 FEED = feed_rows()
 
 
+def stage_pressures(P, F):
+    """Stage pressures (S, N) from the pressure relation (7) with a specified drop:
+    P_n = P_top + (N - 1 - n) dP, P_top the scenario's absorber pressure (the top stage,
+    n = N - 1) and dP = P["dp_stage"] per stage (0: every stage at P^abs, the case study)."""
+    dp = float(P.get("dp_stage", 0.0))
+    return F[FEED["P"], :][:, None] + dp * (N - 1 - np.arange(N))[None, :]
+
+
 def n_sections(P):
     """Number of column sections K, each with its own diameter (1: the case study)."""
     return int(P.get("n_sections", 1))
@@ -138,7 +146,7 @@ def _hV(P, j, T):
 
 def stage_rows(P, pres, q):
     """The 22 rows of one stage.  q: list of the 40 local quantities (Jets or arrays);
-    pres: absorber pressure P^abs per point.  Returns a list of 22 values."""
+    pres: the stage's pressure per point (stage_pressures).  Returns a list of 22 values."""
     sx, sy, sT = P["sx"], P["sy"], P["sT"]
     x = [sx[l] * q[IX + l] for l in range(9)]
     y = [sy[j] * q[IY + j] for j in range(4)]
@@ -235,7 +243,7 @@ def _local_values(P, F, Z, d):
     active = np.ones((K_LOC, S, N), dtype=bool)
     active[A_X:B_Y, :, N - 1] = False
     active[B_Y:I_D, :, 0] = False
-    pres = np.repeat(F[FEED["P"], :][:, None], N, axis=1)
+    pres = stage_pressures(P, F)
     return vals.reshape(K_LOC, S * N), active.reshape(K_LOC, S * N), pres.reshape(S * N)
 
 
@@ -303,7 +311,7 @@ def hydraulic_volume(P, F, Z):
     """V R T / P^abs for every (scenario, stage): the gas volumetric flow of (10b)."""
     S = Z.shape[0]
     Zs = Z.reshape(S, N, NV)
-    return Zs[:, :, IV] * P["R"] * (P["sT"] * Zs[:, :, IT]) / F[FEED["P"], :][:, None]
+    return Zs[:, :, IV] * P["R"] * (P["sT"] * Zs[:, :, IT]) / stage_pressures(P, F)
 
 
 def bounds(P, S):
@@ -337,7 +345,7 @@ def initial_point(P, F):
     Z[:, :, IV] = F[FEED["V0"], :][:, None]
     Z[:, :, IT] = (0.5 * (F[FEED["T0"], :] + F[FEED["Tin"], :]) / P["sT"])[:, None]
     d = 0.5 * (P["d_lo"] + P["d_hi"])
-    vol = (Z[:, :, IV] * P["R"] * P["sT"] * Z[:, :, IT]) / F[FEED["P"], :][:, None]
+    vol = (Z[:, :, IV] * P["R"] * P["sT"] * Z[:, :, IT]) / stage_pressures(P, F)
     Z[:, :, IS] = P["u_max"] * math.pi * d * d / 4.0 - vol
     return Z.reshape(S, NS), d
 

@@ -34,7 +34,7 @@ class AbsParams(C.Structure):
                 ("hL_ref", C.c_double * 9), ("hL_cpa", C.c_double * 9), ("hL_cpb", C.c_double * 9),
                 ("hL_dh", C.c_double * 9),
                 ("hV_ref", C.c_double * 4), ("hV_cpa", C.c_double * 4), ("hV_cpb", C.c_double * 4),
-                ("hV_dh", C.c_double * 4), ("n_sections", C.c_int32)]
+                ("hV_dh", C.c_double * 4), ("n_sections", C.c_int32), ("dp_stage", C.c_double)]
 
 
 class AbsSizes(C.Structure):
@@ -186,6 +186,9 @@ def make_params(P: dict) -> AbsParams:
     for name, _ in AbsParams._fields_:
         if name == "n_sections":
             p.n_sections = int(P.get("n_sections", 1))
+            continue
+        if name == "dp_stage":
+            p.dp_stage = float(P.get("dp_stage", 0.0))
             continue
         v = P[name]
         if isinstance(v, (tuple, list)):

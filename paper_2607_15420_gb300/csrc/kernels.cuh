@@ -193,7 +193,7 @@ __device__ inline void load_stage(const Params& P, int S, int64_t ld, const doub
     }
     const int64_t od = (int64_t)NSC * ld + (int64_t)stage_sec(n, P.nsec) * NP + p;   // its section's diameter
     in.d = x[od] + (dx ? alpha * dx[od] : 0.0);
-    in.P = feed[(int64_t)F_P * ld + s];
+    in.P = stage_pres(P, feed[(int64_t)F_P * ld + s], n);
 }
 
 // partials (if part non-null): [0] |c| summed over the stage's rows, [1] their max,

@@ -81,6 +81,7 @@ struct Params {
     double hL_ref[9], hL_cpa[9], hL_cpb[9], hL_dh[9];
     double hV_ref[4], hV_cpa[4], hV_cpb[4], hV_dh[4];
     int nsec;        // column sections, each with its own diameter (1 or 2)
+    double dp_stage; // specified pressure drop per stage (relation (7)); 0: P^abs everywhere
     // derived at creation
     double lnsx[9];
     double lnsxr[5];   // sum_c nu_ck ln sx_c: the scales' share of each reaction's quotient
@@ -99,6 +100,11 @@ __host__ __device__ inline double sec_weight(int k, int K) {
     int c = 0;
     for (int n = 0; n < N_STAGES; ++n) c += stage_sec(n, K) == k ? 1 : 0;
     return (double)c / N_STAGES;
+}
+
+// pressure of stage n by relation (7) with a specified drop, Pt the top stage's
+__host__ __device__ inline double stage_pres(const Params& P, double Pt, int n) {
+    return Pt + (double)(N_STAGES - 1 - n) * P.dp_stage;
 }
 
 struct StageIn {

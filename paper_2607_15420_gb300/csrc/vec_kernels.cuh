@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(128) init_kernel(const Params P, int S, int64_
 #pragma unroll
         for (int r = 0; r < 5; ++r) q[LE + r] = 0.0;
     }
-    q[LS] = P.u_max * M_PI * d * d * 0.25 - q[LV] * P.R * (P.sT * q[LT]) / feed[(int64_t)F_P * ld + s];
+    q[LS] = P.u_max * M_PI * d * d * 0.25 - q[LV] * P.R * (P.sT * q[LT]) / stage_pres(P, feed[(int64_t)F_P * ld + s], n);
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
         const int64_t o = (int64_t)(NV * n + j) * ld + s;
