@@ -537,7 +537,9 @@ def main():
                                 "measured FP64 FMA throughput") + " (abs_measure_fma_peak)"}
     else:
         roof = {"bound": "hbm", "achieved": dk["GB_s"], "peak": hbm, "unit": "GB/s", "frac": dk["GB_s"] / hbm,
-                "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json), of measured"}
+                "peak_source": ("measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured"
+                                if hbm_src == "measured" else
+                                "fallback copy bandwidth 6.8 TB/s (MEASURED_PEAKS.json absent), of fallback")}
     roof.update({"kernel": dom, "traffic": captured_traffic(dom, es, Sx), "algorithmic_bytes_per_launch": by,
                  "algorithmic_flops_per_launch": fl})
     # the whole solve: every kernel kind's launches (counted by the library in the profiled
