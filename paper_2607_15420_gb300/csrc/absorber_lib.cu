@@ -726,6 +726,10 @@ struct KKTSys {
     // set before kkt_factor_core: p = J^-1 rc is solved together with q = J^-1 b (one
     // two-right-hand-side launch) and the first KKT solve with this rc reuses it
     const double* pre_rc = nullptr;
+    // with pre_rc (one design entry): the Schur pass of kkt_factor_core also forms the
+    // right-hand-side sums of the first solve with this rz (q^T (rz - H p), q^T p and
+    // t = rz - H p; they do not depend on dw), so that solve skips its own Schur pass
+    const double* pre_rz = nullptr;
 };
 
 // ---- block-tile autotuner ----------------------------------------------------------------
@@ -989,6 +993,12 @@ abs_status kkt_factor_core(abs_problem* h, const KKTSys& K, const double* x, cud
         schur_kernel<true><<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, nullptr,
                                                        V(h, V_Q), nullptr, h->sing, h->part, SCHUR_DD, V(h, V_HQ),
                                                        nullptr, V(h, V_Q1), V(h, V_HQ1));
+    else if (K.pre_rc && K.pre_rz)
+        // the matrix sums and the first solve's right-hand-side sums in one pass: planes
+        // [0] q^T H q, [1] q^T q, [2] q^T (rz - H p), [3] q^T p, [4] d-d, [5] singular
+        schur_kernel<false><<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P),
+                                                        V(h, V_Q), K.pre_rz, h->sing, h->part, SCHUR_DD | SCHUR_RHS,
+                                                        V(h, V_HQ), V(h, V_T));
     else
         schur_kernel<false><<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, nullptr,
                                                         V(h, V_Q), nullptr, h->sing, h->part, SCHUR_DD, V(h, V_HQ),
@@ -1019,7 +1029,11 @@ abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, 
     }
     if (!have_p && (r = solve_j(h, K.prec, K.jac, x, rc, V(h, V_P), st)) != ABS_OK) return r;
     const bool two = h->P.nsec == 2;
-    if (two)
+    // the Schur pass of kkt_factor_core already formed this solve's sums (h->red [2], [3])
+    const bool sums_ready = have_p && !two && K.pre_rc == rc && K.pre_rz == rz;
+    if (sums_ready) {
+        // nothing: t, hq and the reduced sums are in place
+    } else if (two)
         schur_kernel<true><<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P),
                                                        V(h, V_Q), rz, nullptr, h->part, SCHUR_RHS, nullptr, V(h, V_T),
                                                        V(h, V_Q1), nullptr);
@@ -1027,8 +1041,10 @@ abs_status kkt_solve_launches(abs_problem* h, const KKTSys& K, const double* x, 
         schur_kernel<false><<<gridq(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), K.hes, K.sig, K.use_w, V(h, V_P),
                                                         V(h, V_Q), rz, nullptr, h->part, SCHUR_RHS, nullptr,
                                                         V(h, V_T));
-    if ((r = launch_check(h, KD_SCHUR)) != ABS_OK) return r;
-    if ((r = reduce(h, st, 4, make_ops({RSUM, RSUM, RSUM, RSUM}), PS_ACT, false)) != ABS_OK) return r;
+    if (!sums_ready) {
+        if ((r = launch_check(h, KD_SCHUR)) != ABS_OK) return r;
+        if ((r = reduce(h, st, 4, make_ops({RSUM, RSUM, RSUM, RSUM}), PS_ACT, false)) != ABS_OK) return r;
+    }
     finalize_dd_kernel<<<(unsigned)((h->NP + 127) / 128), 128, 0, st>>>(h->ld, view(h), h->red, dz, h->P.nsec);
     if ((r = launch_check(h, KD_VEC)) != ABS_OK) return r;
     dz_fast_kernel<<<gride(h), kThr, 0, st>>>((int)h->S, h->ld, view(h), V(h, V_P), V(h, V_Q), V(h, V_T),

@@ -623,6 +623,7 @@ constexpr int RED_T = 128;                  // threads per chunk block
 constexpr int RED_PER = 2;                  // elements per thread and plane
 constexpr int RED_CHUNK = RED_T * RED_PER;  // elements per chunk
 constexpr int RED_KMAX = 12;
+constexpr int RED_TAIL = 8;                 // chunk rounds whose loads the last block issues together
 
 __device__ inline double warp_red(int op, double a) {
     // xor tree: every lane ends with the same value (each pair is combined in both orders
@@ -695,12 +696,41 @@ __global__ void __launch_bounds__(RED_T) reduce_kernel(const double* __restrict_
     if (!last) return;
     if (threadIdx.x == 0) cnt[p] = 0;
     __threadfence();
-    // the problem's chunk results: plane k on warp k % 4 (L2 reads: other blocks wrote them)
-    for (int k = warp; k < K; k += RED_T / 32) {
-        const int op = ops.op[k];
-        double a = red_id(op);
-        for (int cc = c0 + lane; cc < c1; cc += 32) a = red_op(op, a, __ldcg(&cout[(int64_t)k * nchunk + cc]));
-        a = warp_red(op, a);
+    // the problem's chunk results: plane k on warp k % 4, chunk c0 + lane + 32 i on lane
+    // `lane` in increasing i (L2 reads: other blocks wrote them).  The loads of RED_TAIL
+    // rounds of all the warp's planes are issued before the first combination: one L2
+    // latency per RED_TAIL rounds instead of one per round and plane
+    constexpr int NW = RED_T / 32;
+    constexpr int KW = (K + NW - 1) / NW;   // planes per warp
+    int opk[KW];
+    double acc[KW];
+#pragma unroll
+    for (int u = 0; u < KW; ++u) {
+        const int k = warp + NW * u;
+        opk[u] = k < K ? ops.op[k] : RSUM;
+        acc[u] = red_id(opk[u]);
+    }
+    const int nc = c1 - c0;
+    for (int base = 0; base < nc; base += 32 * RED_TAIL) {
+        double t[KW][RED_TAIL];
+#pragma unroll
+        for (int u = 0; u < KW; ++u)
+#pragma unroll
+            for (int i = 0; i < RED_TAIL; ++i) {
+                const int k = warp + NW * u, cc = base + lane + 32 * i;
+                t[u][i] = (k < K && cc < nc) ? __ldcg(&cout[(int64_t)k * nchunk + c0 + cc]) : 0.0;
+            }
+#pragma unroll
+        for (int u = 0; u < KW; ++u)
+#pragma unroll
+            for (int i = 0; i < RED_TAIL; ++i)
+                if (base + lane + 32 * i < nc) acc[u] = red_op(opk[u], acc[u], t[u][i]);
+    }
+#pragma unroll
+    for (int u = 0; u < KW; ++u) {
+        const int k = warp + NW * u;
+        if (k >= K) continue;   // warp-uniform
+        const double a = warp_red(opk[u], acc[u]);
         if (lane == 0) {
             out[(int64_t)k * NP + p] = a;
             if (hout) hout[(int64_t)k * NP + p] = a;
