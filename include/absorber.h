@@ -343,7 +343,8 @@ typedef struct abs_result {
     int32_t warm_status;         /* ipm_solve_learned: 1 learned start used, 0 rejected */
     int32_t fp64_scenarios;      /* FP32 factors: scenario factorizations escalated to FP64 in
                                     total (over the iterations; see fp64_fallbacks) */
-    double warm_ms;              /* ipm_solve_learned: host time of prediction + acceptance test */
+    double warm_ms;              /* ipm_solve_learned: host time of the prediction and of queueing
+                                    the inlet-copy start's evaluation */
     double warm_E0, cold_E0;     /* E_0 at the learned start and at the inlet-copy start */
     double warm_theta, cold_theta;  /* constraint violation ||c||_1 at the same two starts */
     int32_t tiles[4];            /* warps per block last used: factor, solve (1 and 2 right-hand
@@ -551,9 +552,10 @@ abs_status abs_mlp_make_dataset(const abs_problem* h, const double* x, const dou
  * bound multipliers warm_mu_init / slack; row multipliers from the least-squares
  * estimate at that point (warm_multipliers = 0) or the network's, scaled onto the same
  * central path (1).  The start is accepted when its E_0 and ||c||_1 do not exceed those
- * of the inlet-copy start; the solve then runs from it with mu_init = warm_mu_init,
- * else from the default start (res.warm_status says which).  Outputs as ipm_solve.
- * Synchronous. */
+ * of the inlet-copy start (evaluated first, with zero iterations); the solve runs from it
+ * with mu_init = warm_mu_init and takes the test at its first evaluation, where a
+ * rejected start ends that run and the solve restarts from the default start
+ * (res.warm_status says which).  Outputs as ipm_solve.  Synchronous. */
 abs_status ipm_solve_learned(abs_problem* h, abs_mlp* net, const abs_options* opt,
                              abs_result* res, double* x_out, double* y_out, abs_stream_t stream);
 

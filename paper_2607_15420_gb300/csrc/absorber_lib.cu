@@ -373,6 +373,9 @@ struct DState {
     double dw, Sd, S01, S11, resid;                // Sd (and S01, S11): the design Schur complement
     int ic_trial;                                  // Algorithm IC trial of the block LDL^T path
     double dc;                                     // its delta_c of the iteration
+    // the learned start's acceptance test at the first evaluation: the inlet-copy start's
+    // (E_0, theta) and the learned start's
+    double gate_E0, gate_theta, first_E0, first_theta;
 };
 
 // state shared by the problems of a run
@@ -470,6 +473,7 @@ struct abs_problem {
     // the method's state on the device
     DState* dst = nullptr;           // [NP]
     DGlobal* dglob = nullptr;
+    double* gate = nullptr;          // [2][NP] the inlet-copy start's E_0 and theta (learned-start test)
     double* filt = nullptr;          // [NP][fcap][2]
     int fcap = 0;
     int* esc = nullptr;              // [ld] per-scenario FP64 escalation flags of the iteration
@@ -1254,6 +1258,7 @@ void absorber_destroy(abs_problem* h) {
     if (h->stream) cudaStreamDestroy(h->stream);
     cudaFree(h->dst);
     cudaFree(h->dglob);
+    cudaFree(h->gate);
     cudaFree(h->filt);
     cudaFree(h->esc);
     cudaFree(h->escn);
