@@ -505,6 +505,19 @@ abs_status abs_mlp_fit_normalization(abs_mlp* net, const float* X, const float* 
 /* Prediction: raw inputs X [n][3] -> raw outputs Y [n][440] (device).  Asynchronous. */
 abs_status abs_mlp_forward(abs_mlp* net, const float* X, int64_t n, float* Y, abs_stream_t stream);
 
+/* The products of the layers with 256 inputs (layers 2-4, forward) run on the tensor cores
+ * (tcgen05 MMAs of bfloat16 operands with FP32 accumulation in tensor memory; each FP32
+ * activation enters as the sum of three bfloat16 terms, so the product keeps FP32
+ * accuracy) when on = 1, the default, or as FP32 FMAs on the CUDA cores when on = 0.
+ * Returns ABS_ERR_ARG for another value. */
+abs_status abs_mlp_set_tensor_cores(abs_mlp* net, int32_t on);
+
+/* Nonzero once a tensor-core product of this network gave up waiting for its MMAs (after
+ * about 4M polls of its mbarrier; that block's outputs are left unwritten and its tensor
+ * memory freed).  Read after the stream the network ran on has synchronised;
+ * abs_mlp_forward, abs_mlp_loss_grad and abs_mlp_train then return ABS_ERR_TIMEOUT. */
+int32_t abs_mlp_device_fault(const abs_mlp* net);
+
 /* Loss of the n pairs (X, Y) (raw, device) and its gradient with respect to the
  * parameters (device, ABS_MLP_PARAMS floats, or NULL).  *loss: host.  Synchronous. */
 abs_status abs_mlp_loss_grad(abs_mlp* net, const float* X, const float* Y, int64_t n, double* loss,

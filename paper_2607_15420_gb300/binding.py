@@ -146,6 +146,8 @@ EXPORTS = {
     "abs_mlp_get_normalization": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "abs_mlp_fit_normalization": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "abs_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "abs_mlp_set_tensor_cores": (C.c_int, [C.c_void_p, C.c_int32]),
+    "abs_mlp_device_fault": (C.c_int32, [C.c_void_p]),
     "abs_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double),
                                     C.c_void_p, C.c_void_p]),
     "abs_default_train_options": (None, [C.POINTER(AbsTrainOptions)]),
@@ -540,6 +542,12 @@ class MLP:
 
     def forward(self, X, Y, stream=None):
         self._check(lib().abs_mlp_forward(self.h, _ptr(X), X.shape[0], _ptr(Y), _stream(stream)))
+
+    def set_tensor_cores(self, on):
+        self._check(lib().abs_mlp_set_tensor_cores(self.h, int(on)))
+
+    def device_fault(self):
+        return int(lib().abs_mlp_device_fault(self.h))
 
     def loss_grad(self, X, Y, grad=None, stream=None):
         loss = C.c_double()

@@ -18,9 +18,11 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "absorber.h"
+#include "kernels_umma.cuh"
 
 namespace {
 
@@ -67,6 +69,9 @@ struct abs_mlp {
     int64_t lpart_cap = 0;
     double* lacc = nullptr;          // per-epoch loss accumulators
     int64_t lacc_cap = 0;
+    bool tc = true;                  // tensor-core products for the 256-input layers
+    int* hfault = nullptr;           // mapped host flag: a tensor-core wait gave up
+    int* dfault = nullptr;
     std::string err = "no error";
 };
 
@@ -200,12 +205,174 @@ __global__ void __launch_bounds__(GT) gemm_kernel(int M, int N, int K, const flo
     }
 }
 
+// The forward products on the tensor cores (kernels_umma.cuh): A FP32 [M][K] row-major, W
+// bfloat16 [N][K] row-major, K a multiple of 64; epilogues EPI_BIAS_GELU, EPI_BIAS,
+// EPI_DENORM as gemm_kernel's.  Grid (ceil(N / 64), ceil(M / 128)), 128 threads,
+// umma::SMEM bytes of dynamic shared memory.  fault: set when a wait for the MMAs gave up
+// (the block then frees its tensor memory and leaves its outputs unwritten).
+template <int EPI>
+__global__ void __launch_bounds__(umma::T) gemm_tc_kernel(int M, int N, int K, const float* __restrict__ A,
+                                                          const __nv_bfloat16* __restrict__ W,
+                                                          const float* __restrict__ bias, float* __restrict__ Z,
+                                                          float* __restrict__ C, const float* __restrict__ scale,
+                                                          const float* __restrict__ shift, int* __restrict__ fault) {
+    using namespace umma;
+    extern __shared__ unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tbase;
+    unsigned char* sm = (unsigned char*)(((uintptr_t)tc_smem + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    const uint32_t sa = smem_u32(sm), sb = sa + 3 * A_PLANE, mb = smem_u32(&mbar);
+    if (warp == 0) {
+        tmem_alloc(smem_u32(&tbase), TN);
+        tmem_relinquish();
+    }
+    if (tid == 0) mbar_init(mb, 1);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = tbase;
+    bool ok = true;
+    for (int c = 0; c < K / KC; ++c) {
+        const int k0 = c * KC;
+        // A chunk: 128 x 64 FP32 as float4, W chunk: 64 x 64 bfloat16 as 16-byte rows of core
+        // matrices; every load in flight before the first store.  Float4 e of the A chunk
+        // fills half a row of core matrix cm = e / 16 (row group cm / 8, K block cm % 8) and
+        // W's row v of core matrix v / 8 (row group (v / 8) / 8, K block (v / 8) % 8): a
+        // half-warp's stores cover whole 128-byte core matrices.  A is split into its three
+        // bfloat16 terms (8-byte stores into the three term planes)
+        constexpr int NA = (TM * KC / 4) / T, NB = (TN * KC / 8) / T;
+        float4 av[NA];
+        uint4 wv[NB];
+#pragma unroll
+        for (int i = 0; i < NA; ++i) {
+            const int e = i * T + tid, cm = e >> 4, q = e & 15;
+            const int r = ((cm >> 3) << 3) + (q >> 1), k = ((cm & 7) << 3) + ((q & 1) << 2);
+            av[i] = m0 + r < M ? *reinterpret_cast<const float4*>(A + (int64_t)(m0 + r) * K + k0 + k)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int v = i * T + tid, cm = v >> 3;
+            const int n = ((cm >> 3) << 3) + (v & 7), k = (cm & 7) << 3;
+            wv[i] = n0 + n < N ? *reinterpret_cast<const uint4*>(W + (int64_t)(n0 + n) * K + k0 + k)
+                               : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int i = 0; i < NA; ++i) {
+            const int e = i * T + tid, cm = e >> 4, q = e & 15;
+            const int r = ((cm >> 3) << 3) + (q >> 1), k = ((cm & 7) << 3) + ((q & 1) << 2);
+            const float a4[4] = {av[i].x, av[i].y, av[i].z, av[i].w};
+            __nv_bfloat16 t[3][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(a4[j]);
+                const float r1 = a4[j] - __bfloat162float(h);
+                const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+                t[0][j] = h;
+                t[1][j] = m;
+                t[2][j] = __float2bfloat16_rn(r1 - __bfloat162float(m));
+            }
+            const uint32_t o = core_off(r, k, TM / 8);
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+                *reinterpret_cast<uint2*>(sm + p * A_PLANE + o) = make_uint2(pack2(t[p][0], t[p][1]), pack2(t[p][2], t[p][3]));
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int v = i * T + tid, cm = v >> 3;
+            const int n = ((cm >> 3) << 3) + (v & 7), k = (cm & 7) << 3;
+            *reinterpret_cast<uint4*>(sm + 3 * A_PLANE + core_off(n, k, TN / 8)) = wv[i];
+        }
+        fence_smem_async();
+        __syncthreads();
+        if (tid == 0) {
+            fence_after();
+#pragma unroll
+            for (int s = 0; s < KC / 16; ++s)
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+                    mma(tmem, desc(sa + p * A_PLANE + s * 2 * (TM / 8) * 128, A_LBO, A_SBO),
+                        desc(sb + s * 2 * (TN / 8) * 128, B_LBO, B_SBO), IDESC, (c | s | p) != 0);
+            commit(mb);
+        }
+        // the chunk's MMAs are done before its shared memory is refilled
+        ok = __syncthreads_and(ok && mbar_wait(mb, (uint32_t)(c & 1)));
+        if (!ok) break;
+        fence_after();
+    }
+    if (ok) {
+        // accumulator rows + bias into a padded shared tile over the A planes (the MMAs are
+        // done): warp w its lanes (rows) 32 (w % 4) + 0..31, columns 32 (w / 4) + 0..31.
+        // Then rows written with the lanes along the columns (coalesced), the epilogue's
+        // nonlinearity on the way
+        constexpr int LDS = TN + 1;
+        float* tile = reinterpret_cast<float*>(sm);
+        const int q4 = warp & 3, ch = warp >> 2;
+        const int r = q4 * 32 + lane;
+#pragma unroll
+        for (int cb = ch * 32; cb < ch * 32 + 32; cb += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)cb, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int gn = n0 + cb + j;
+                tile[r * LDS + cb + j] = v[j] + (gn < N ? bias[gn] : 0.0f);
+            }
+        }
+        __syncthreads();
+        for (int rr = warp; rr < TM; rr += T / 32) {
+            const int row = m0 + rr;
+            if (row >= M) break;   // warp-uniform
+#pragma unroll
+            for (int h = 0; h < TN / 32; ++h) {
+                const int c = lane + 32 * h, gn = n0 + c;
+                if (gn >= N) continue;
+                const int64_t o = (int64_t)row * N + gn;
+                float vv = tile[rr * LDS + c];
+                if (EPI == EPI_BIAS_GELU) {
+                    Z[o] = vv;
+                    vv = gelu_f(vv);
+                } else if (EPI == EPI_DENORM) {
+                    vv = vv * scale[gn] + shift[gn];
+                }
+                C[o] = vv;
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TN);
+    if (!ok && tid == 0) atomicExch(fault, 1);
+}
+
+template <int EPI>
+abs_status gemm_tc(abs_mlp* net, cudaStream_t st, int M, int N, int K, const float* A, const __nv_bfloat16* W,
+                   float* C, const float* bias, float* Z, const float* scale, const float* shift) {
+    static bool attr = false;
+    if (!attr) {
+        MCK(cudaFuncSetAttribute(gemm_tc_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, umma::SMEM));
+        attr = true;
+    }
+    const dim3 grid((unsigned)((N + umma::TN - 1) / umma::TN), (unsigned)((M + umma::TM - 1) / umma::TM));
+    gemm_tc_kernel<EPI><<<grid, umma::T, umma::SMEM, st>>>(M, N, K, A, W, bias, Z, C, scale, shift, net->dfault);
+    return mlaunch(net);
+}
+
 template <class TB, int EPI>
 abs_status gemm(abs_mlp* net, cudaStream_t st, int M, int N, int K, const float* A, int64_t sam, int64_t sak,
                 const TB* B, int64_t sbk, int64_t sbn, float* C, const float* bias = nullptr,
                 const float* aux = nullptr, float* Z = nullptr, const float* scale = nullptr,
                 const float* shift = nullptr) {
     if (M <= 0 || N <= 0) return ABS_OK;
+    if constexpr (std::is_same<TB, __nv_bfloat16>::value &&
+                  (EPI == EPI_BIAS_GELU || EPI == EPI_BIAS || EPI == EPI_DENORM)) {
+        // a forward product of a 256-input layer: A [M][K], W [N][K] row-major, aligned
+        if (net->tc && K % umma::KC == 0 && sak == 1 && sam == K && sbk == 1 && sbn == K &&
+            ((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0)
+            return gemm_tc<EPI>(net, st, M, N, K, A, B, C, bias, Z, scale, shift);
+    }
     const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
     gemm_kernel<TB, EPI><<<grid, GT, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, bias, aux, Z, C, scale, shift);
     return mlaunch(net);
@@ -466,6 +633,9 @@ abs_status abs_mlp_create(uint64_t seed, abs_mlp** out) {
     MCK2(cudaMalloc(&net->m, sizeof(float) * NPAR));
     MCK2(cudaMalloc(&net->v, sizeof(float) * NPAR));
     MCK2(cudaMalloc(&net->norm, sizeof(float) * (2 * NIN + 2 * NOUT)));
+    MCK2(cudaHostAlloc(&net->hfault, sizeof(int), cudaHostAllocMapped));
+    *net->hfault = 0;
+    MCK2(cudaHostGetDevicePointer(&net->dfault, net->hfault, 0));
 #undef MCK2
     // Glorot-uniform weights (Glorot & Bengio 2010), zero biases, identity normalisation
     std::vector<float> th(NPAR, 0.0f);
@@ -493,6 +663,7 @@ abs_status abs_mlp_create(uint64_t seed, abs_mlp** out) {
 
 void abs_mlp_destroy(abs_mlp* net) {
     if (!net) return;
+    if (net->hfault) cudaFreeHost(net->hfault);
     cudaFree(net->theta);
     cudaFree(net->wb);
     cudaFree(net->grad);
@@ -575,8 +746,17 @@ abs_status abs_mlp_fit_normalization(abs_mlp* net, const float* X, const float* 
     return ABS_OK;
 }
 
+int32_t abs_mlp_device_fault(const abs_mlp* net) { return net && net->hfault ? *(volatile int*)net->hfault : 0; }
+
+abs_status abs_mlp_set_tensor_cores(abs_mlp* net, int32_t on) {
+    if (!net || (on != 0 && on != 1)) return mfail(net, ABS_ERR_ARG, "bad argument");
+    net->tc = on != 0;
+    return ABS_OK;
+}
+
 abs_status abs_mlp_forward(abs_mlp* net, const float* X, int64_t n, float* Y, abs_stream_t stream) {
     if (!net || n < 0 || (n > 0 && (!X || !Y))) return mfail(net, ABS_ERR_ARG, "bad argument");
+    if (abs_mlp_device_fault(net)) return mfail(net, ABS_ERR_TIMEOUT, "a tensor-core product gave up waiting");
     cudaStream_t st = (cudaStream_t)stream;
     abs_status r;
     for (int64_t r0 = 0; r0 < n; r0 += CHUNK_ROWS) {
@@ -590,6 +770,7 @@ abs_status abs_mlp_forward(abs_mlp* net, const float* X, int64_t n, float* Y, ab
 abs_status abs_mlp_loss_grad(abs_mlp* net, const float* X, const float* Y, int64_t n, double* loss, float* grad,
                              abs_stream_t stream) {
     if (!net || !X || !Y || n < 1) return mfail(net, ABS_ERR_ARG, "bad argument");
+    if (abs_mlp_device_fault(net)) return mfail(net, ABS_ERR_TIMEOUT, "a tensor-core product gave up waiting");
     cudaStream_t st = (cudaStream_t)stream;
     abs_status r;
     if ((r = ensure_cap(net, n)) != ABS_OK) return r;
@@ -623,6 +804,7 @@ void abs_default_train_options(abs_train_options* o) {
 abs_status abs_mlp_train(abs_mlp* net, const float* X, const float* Y, int64_t n, const abs_train_options* opt_in,
                          double* epoch_loss, abs_stream_t stream) {
     if (!net || !X || !Y || n < 1) return mfail(net, ABS_ERR_ARG, "bad argument");
+    if (abs_mlp_device_fault(net)) return mfail(net, ABS_ERR_TIMEOUT, "a tensor-core product gave up waiting");
     abs_train_options o;
     if (opt_in) o = *opt_in;
     else abs_default_train_options(&o);

@@ -4,7 +4,9 @@ learned warm start against the method without it.
 Parity tolerances: the GPU computes in FP32 with the same bfloat16-rounded weights as
 the oracle (which computes in FP64), so forward outputs agree to FP32 rounding over
 sums of <= 256 terms (1e-5 relative to the output scale) and gradients to 1e-4 of each
-tensor's largest entry (sums over all samples)."""
+tensor's largest entry (sums over all samples).  The products of the 256-input layers run
+on the tensor cores by default (each FP32 activation as three bfloat16 terms, FP32
+accumulation): the same tolerances hold, and the CUDA-core products are checked too."""
 import numpy as np
 import pytest
 
@@ -73,6 +75,35 @@ def test_forward_matches_oracle(B, n):
     yo = mlp.predict(theta, X, norm)
     scale = norm["out_scale"] * (1.0 + np.abs(mlp.forward(theta, X, norm)))
     assert np.max(np.abs(_host(Yg) - yo) / scale) <= 1e-5
+
+
+@pytest.mark.parametrize("n", [128, 300, 5000])
+def test_tensor_core_products_match_cuda_core_products_and_oracle(B, n):
+    # the tcgen05 forward products (tiles of 128 rows x 64 columns; 440 outputs = 6 full
+    # tiles and a 56-column one; ragged last row tile) against the FP32 FMA products and
+    # the oracle; no wait gave up
+    import torch
+    theta, norm, X, Y = _case(40 + n, n)
+    net = _net(B, theta, norm)
+    Yt = torch.zeros((n, mlp.N_OUT), dtype=torch.float32, device="cuda")
+    Yc = torch.zeros_like(Yt)
+    net.forward(_dev32(X), Yt)
+    net.set_tensor_cores(0)
+    net.forward(_dev32(X), Yc)
+    net.set_tensor_cores(1)
+    yt, yc = _host(Yt), _host(Yc)
+    assert net.device_fault() == 0
+    rows = np.arange(n) if n <= 300 else np.r_[0:64, 2500:2564, n - 72:n]
+    yo = mlp.predict(theta, X[rows], norm)
+    scale = norm["out_scale"] * (1.0 + np.abs(mlp.forward(theta, X[rows], norm)))
+    assert np.max(np.abs(yt[rows] - yo) / scale) <= 1e-5
+    assert np.max(np.abs(yc[rows] - yo) / scale) <= 1e-5
+    # every row: the two within twice that bound of each other (each within it of the
+    # exact product), on the normalised-output scale
+    yn = (yc - norm["out_shift"]) / norm["out_scale"]
+    assert np.max(np.abs(yt - yc) / (norm["out_scale"] * (1.0 + np.abs(yn)))) <= 2e-5
+    with pytest.raises(B.AbsorberError):
+        net.set_tensor_cores(2)
 
 
 def test_forward_large_chunked(B):
