@@ -32,8 +32,11 @@ constexpr int B_BYTES = TN * KC * 2;              // the W chunk: 8 KB
 constexpr int SMEM = 3 * A_PLANE + B_BYTES + 1024;
 // core-matrix strides (bytes): A [kc][16 row groups], B [kc][8 row groups]; adjacent
 // core matrices along K ("leading") and along M / N ("stride")
-constexpr uint32_t A_LBO = 16 * 128, A_SBO = 128, B_LBO = 8 * 128, B_SBO = 128;
+constexpr uint32_t A_LBO = (TM / 8) * 128, A_SBO = 128, B_LBO = (TN / 8) * 128, B_SBO = 128;
 constexpr long long WAIT_LIMIT = 1ll << 22;      // mbarrier polls before a wait gives up
+static_assert(TM == 128 && TN % 16 == 0 && TN >= 32 && TN <= 256 && (TN & (TN - 1)) == 0,
+              "an M = 128 MMA shape; tensor-memory columns a power of two >= 32");
+static_assert((TM * KC / 4) % T == 0 && (TN * KC / 8) % T == 0 && (TN / 2) % 16 == 0, "staging and epilogue split");
 
 // instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B bfloat16 (bits 7-9,
 // 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24

@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(umma::T) gemm_tc_kernel(int M, int N, int K, c
     }
     if (ok) {
         // accumulator rows + bias into a padded shared tile over the A planes (the MMAs are
-        // done): warp w its lanes (rows) 32 (w % 4) + 0..31, columns 32 (w / 4) + 0..31.
+        // done): warp w its lanes (rows) 32 (w % 4) + 0..31, columns TN / 2 (w / 4) + ...
         // Then rows written with the lanes along the columns (coalesced), the epilogue's
         // nonlinearity on the way
         constexpr int LDS = TN + 1;
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(umma::T) gemm_tc_kernel(int M, int N, int K, c
         const int q4 = warp & 3, ch = warp >> 2;
         const int r = q4 * 32 + lane;
 #pragma unroll
-        for (int cb = ch * 32; cb < ch * 32 + 32; cb += 16) {
+        for (int cb = ch * (TN / 2); cb < (ch + 1) * (TN / 2); cb += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)cb, v);
 #pragma unroll
