@@ -486,6 +486,7 @@ struct abs_problem {
     int64_t kcount[ABS_N_KINDS] = {0};   // ... by kind
     float* mlp_x = nullptr;          // learned warm start: network inputs [ld][3] and outputs [ld][440]
     float* mlp_y = nullptr;
+    double* wd0 = nullptr;           // learned warm start: its d0 (device)
     // bound multipliers of d at the end of the last engine run, per problem, of the scaled
     // problem, and each problem's objective scaling w (absorber_bound_multipliers)
     std::vector<double> zLd_last, zUd_last, w_last;
@@ -1268,6 +1269,7 @@ void absorber_destroy(abs_problem* h) {
     cudaFree(h->pid);
     cudaFree(h->mlp_x);
     cudaFree(h->mlp_y);
+    cudaFree(h->wd0);
     cudaFree(h->jac);
     cudaFree(h->hes);
     cudaFree(h->vec);

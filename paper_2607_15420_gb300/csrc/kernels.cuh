@@ -109,6 +109,18 @@ __device__ inline int live_prob(const BView& b, int s, int S, int flag) {
 // ------------------------------------------------------------------------------------
 enum RedOp { RSUM = 0, RMAX = 1, RMIN = 2 };
 
+// |a| as an unsigned integer that orders like |a| (the IEEE layout with the sign cleared;
+// a NaN orders above +inf): maxima of magnitudes taken on the integer pipe, off the FP64
+// pipe, and a NaN among them survives (the key of the maximum is NaN's)
+__device__ __forceinline__ unsigned long long mag_key(double a) {
+    return (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long key_max(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
+}
+__device__ __forceinline__ double key_double(unsigned long long k) { return __longlong_as_double((long long)k); }
+constexpr unsigned long long INF_KEY = 0x7ff0000000000000ull;   // keys above it are NaN
+
 __device__ inline double red_id(int op) { return op == RSUM ? 0.0 : (op == RMAX ? -INFINITY : INFINITY); }
 
 __device__ inline double red_op(int op, double a, double b) {

@@ -70,14 +70,14 @@ __global__ void __launch_bounds__(128) dual_kernel(const Params P, int S, int64_
     const bool live = live_prob(b, s, S, PS_ACT) >= 0;
     double v[6] = {0.0, 0.0, 0.0, -INFINITY, INFINITY, 0.0};
     if (live) {
+        unsigned long long k0 = 0;   // max |J^T l - zL + zU| as an integer key (NaN survives)
 #pragma unroll 1
         for (int j = q; j < NV; j += QS) {
             const int64_t o = (int64_t)(NV * n + j) * ld + s;
             const double gj = jt_one(ld, jac, lam, s, n, j);
             jtl[o] = gj;
             const double zl = zL[o], zu = zU[o];
-            const double r = fabs(gj - zl + zu);
-            v[0] = (r > v[0] || r != r) ? r : v[0];
+            k0 = key_max(k0, mag_key(gj - zl + zu));
             v[1] += fabs(lam[o]);
             v[2] += fabs(zl) + fabs(zu);
             const double xv = x[o];
@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(128) dual_kernel(const Params P, int S, int64_
                 v[4] = fmin(v[4], cp);
             }
         }
+        v[0] = key_double(k0);
     }
     constexpr int ops[5] = {RMAX, RSUM, RSUM, RMAX, RMIN};
     group_combine<6, 5>(v, sm, ops);
@@ -305,6 +306,7 @@ __global__ void __launch_bounds__(128) kkt_residual_kernel(int S, int64_t ld, co
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (live) {
         const double dd = dz[(int64_t)NSC * ld + (int64_t)sec * b.NP + pr];   // the stage's section
+        bool bad = false;
         for (int j = gq; j < NV; j += QS) {
             const int64_t o = (int64_t)(NV * n + j) * ld + s;
             const double a = g[o] - jt_one(ld, jac, dlast, s, n, j);
@@ -315,8 +317,9 @@ __global__ void __launch_bounds__(128) kkt_residual_kernel(int S, int64_t ld, co
             v[1] = fmax(v[1], fabs(c));
             v[3] = fmax(v[3], fabs(rz[o]));
             v[4] = fmax(v[4], fabs(rc[o]));
-            if (a != a || c != c) v[0] = NAN;
+            bad = bad || a != a || c != c;
         }
+        if (bad) v[0] = NAN;   // fmax skips a NaN: any NaN of the rows makes [0] NaN
     }
     constexpr int ops[5] = {RMAX, RMAX, RSUM, RMAX, RMAX};   // [2] is set below
     group_combine<5, 5>(v, sm, ops);
