@@ -565,8 +565,8 @@ abs_status abs_mlp_make_dataset(const abs_problem* h, const double* x, const dou
  * bound multipliers warm_mu_init / slack; row multipliers from the least-squares
  * estimate at that point (warm_multipliers = 0) or the network's, scaled onto the same
  * central path (1).  The start is accepted when its E_0 and ||c||_1 do not exceed those
- * of the inlet-copy start (evaluated with zero iterations on the handle's stream while
- * the prediction runs on the caller's); the solve runs from it
+ * of the inlet-copy start (evaluated with zero iterations on a second handle of the same
+ * problem, created on first use, while the prediction runs); the solve runs from it
  * with mu_init = warm_mu_init and takes the test at its first evaluation, where a
  * rejected start ends that run and the solve restarts from the default start
  * (res.warm_status says which).  Outputs as ipm_solve.  Synchronous. */

@@ -493,6 +493,8 @@ struct abs_problem {
     bool sol_valid = false;
     abs_problem* base = nullptr;     // expected-value sub-problem(s) for the starting point
     abs_problem* batch = nullptr;    // cached batch handle of ipm_solve_batched (on probs[0])
+    abs_problem* aux = nullptr;      // ipm_solve_learned: the inlet-copy start's evaluation (same problem)
+    cudaEvent_t gate_ev = nullptr;   // recorded after that evaluation's (E_0, theta) reached gate
     std::vector<int64_t> batch_key;  // the sizes it was built for
 };
 
@@ -1249,6 +1251,8 @@ void absorber_destroy(abs_problem* h) {
     if (!h) return;
     absorber_destroy(h->base);
     absorber_destroy(h->batch);
+    absorber_destroy(h->aux);
+    if (h->gate_ev) cudaEventDestroy(h->gate_ev);
     for (auto e : h->prof.pool) cudaEventDestroy(e);
     for (auto& g : h->rgraphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);

@@ -228,6 +228,20 @@ def test_learned_warm_start_beats_cold_start(B):
     ZL, _ = prob.from_soa(_host(zl))
     ZU, _ = prob.from_soa(_host(zu))
     assert checks.kkt_error(P, F, d, Z, lam, ZL, ZU, zd[0], zd[1], chunk=100) <= 1e-8
+    # repeated solves replay the captured graphs (the inlet-copy evaluation on the second
+    # handle, the solve from the learned start waiting for it): the first solve bit for bit
+    again = [B.ipm_solve_learned(prob, net, o) for _ in range(3)]
+    assert again[-1].graph_replays >= 1
+    for r in again:
+        assert r.status == 0 and r.warm_status == 1 and r.iters == warm.iters and r.d == warm.d
+        assert r.warm_E0 == warm.warm_E0 and r.cold_E0 == warm.cold_E0
+    # the same with FP32 factors and FP64 refinement
+    o32 = B.default_options(precision=1, max_refine=8)
+    w32 = [B.ipm_solve_learned(prob, net, o32) for _ in range(4)]
+    assert w32[-1].graph_replays >= 1
+    for r in w32:
+        assert r.status == 0 and r.warm_status == 1 and r.E0 <= 1e-8 and abs(r.d - warm.d) <= 1e-6 * warm.d
+        assert r.iters == w32[0].iters and r.d == w32[0].d
 
 
 def test_learned_warm_start_rejects_a_bad_network(B):
