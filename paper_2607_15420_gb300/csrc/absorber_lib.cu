@@ -384,7 +384,8 @@ struct DGlobal {
     int rk;             // refinement round of the current solve (shared, as the launches are)
     int esc_any;        // an FP64 escalation took place in this iteration
     int guard_iter, guard_ls;   // executions of the iteration / line-search loop bodies
-    int pad;
+    int lsfac;          // the stored factors of J are those of the least-squares estimate at x
+    int fac_skip;       // the Newton step's factorization keeps them (iteration 0 only)
     long long launches; // kernels of this library launched by graph execution
 };
 }  // namespace
@@ -737,6 +738,9 @@ struct KKTSys {
     // right-hand-side sums of the first solve with this rz (q^T (rz - H p), q^T p and
     // t = rz - H p; they do not depend on dw), so that solve skips its own Schur pass
     const double* pre_rz = nullptr;
+    // device flag: when set, kkt_factor_core keeps the stored factors of J (those of the
+    // least-squares multiplier estimate at the same point)
+    const int* skip = nullptr;
 };
 
 // ---- block-tile autotuner ----------------------------------------------------------------
@@ -818,7 +822,8 @@ abs_status tuned_launch(abs_problem* h, int kind, int es, std::initializer_list<
 // Gauss-Jordan (factor_gj_kernel); FP64: LU factors, row order and G (factor_warp_kernel),
 // of the scenarios with mask[s] != 0 only when mask is given
 template <class T, int W>
-void factor_w(abs_problem* h, const double* jac, double pivtol, const int* mask, cudaStream_t st) {
+void factor_w(abs_problem* h, const double* jac, double pivtol, const int* mask, cudaStream_t st,
+              const int* skip) {
     if constexpr (std::is_same<T, float>::value) {
         if (h->factor_kernel == 1)
             factor_gj_tc_kernel<W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac,
@@ -827,24 +832,28 @@ void factor_w(abs_problem* h, const double* jac, double pivtol, const int* mask,
         else
             factor_gj_kernel<W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac,
                                                                 (float*)h->LUp[ABS_PREC_FP32], h->piv,
-                                                                (float*)h->Gp[ABS_PREC_FP32], h->sing, pivtol);
+                                                                (float*)h->Gp[ABS_PREC_FP32], h->sing, pivtol,
+                                                                skip);
     }
     else if constexpr (factor_fits<T, W>())
         factor_warp_kernel<T, W><<<gridw(h, W), 32 * W, 0, st>>>((int)h->S, h->ld, view(h), jac,
                                                                 (T*)h->LUp[ABS_PREC_FP64], h->piv,
-                                                                (T*)h->Gp[ABS_PREC_FP64], h->sing, pivtol, mask);
+                                                                (T*)h->Gp[ABS_PREC_FP64], h->sing, pivtol, mask,
+                                                                skip);
 }
 
+// skip (device flag, optional): when set at run time the launch leaves the stored factors
+// as they are (they are those of this Jacobian)
 template <class T>
 abs_status factor_launch(abs_problem* h, const double* jac, double pivtol, cudaStream_t st,
-                         const int* mask = nullptr) {
+                         const int* mask = nullptr, const int* skip = nullptr) {
     prof_begin(h, K_FACTOR, st);
     auto go = [&](int w) {
         switch (w) {
-            case 1: factor_w<T, 1>(h, jac, pivtol, mask, st); break;
-            case 2: factor_w<T, 2>(h, jac, pivtol, mask, st); break;
-            case 8: factor_w<T, 8>(h, jac, pivtol, mask, st); break;
-            default: factor_w<T, 4>(h, jac, pivtol, mask, st); break;
+            case 1: factor_w<T, 1>(h, jac, pivtol, mask, st, skip); break;
+            case 2: factor_w<T, 2>(h, jac, pivtol, mask, st, skip); break;
+            case 8: factor_w<T, 8>(h, jac, pivtol, mask, st, skip); break;
+            default: factor_w<T, 4>(h, jac, pivtol, mask, st, skip); break;
         }
         return launch_check(h, KD_FACTOR);
     };
@@ -986,8 +995,8 @@ abs_status kkt_factor_core(abs_problem* h, const KKTSys& K, const double* x, cud
         // FP64: a pivot below 1e-14 of the block's largest entry marks the stage block
         // singular; FP32: only (numerically) zero pivots do -- accuracy is guarded by the
         // FP64 refinement instead, with FP64 escalation where it stalls
-        if (K.prec == ABS_PREC_FP32) r = factor_launch<float>(h, K.jac, 1e-30, st);
-        else r = factor_launch<double>(h, K.jac, 1e-14, st);
+        if (K.prec == ABS_PREC_FP32) r = factor_launch<float>(h, K.jac, 1e-30, st, nullptr, K.skip);
+        else r = factor_launch<double>(h, K.jac, 1e-14, st, nullptr, K.skip);
     }
     if (r != ABS_OK) return r;
     r = K.pre_rc ? solve_j2(h, K.prec, K.jac, x, K.pre_rc, nullptr, V(h, V_P), V(h, V_Q), st)

@@ -233,7 +233,9 @@ __global__ void __launch_bounds__(32 * WPB) factor_warp_kernel(int S, int64_t ld
                                                                  const double* __restrict__ jac, T* __restrict__ LU,
                                                                  unsigned char* __restrict__ piv, T* __restrict__ G,
                                                                  int* __restrict__ sing, double pivtol,
-                                                                 const int* __restrict__ mask = nullptr) {
+                                                                 const int* __restrict__ mask = nullptr,
+                                                                 const int* __restrict__ skip = nullptr) {
+    if (skip && *skip) return;   // the stored factors are those of this Jacobian (every block leaves)
     __shared__ T sA[WPB][NV][PADA];
     __shared__ T sG[WPB][NV][NABV];
     __shared__ LaneTables lt;
@@ -353,7 +355,9 @@ template <int WPB = WPB_F>
 __global__ void __launch_bounds__(32 * WPB, WPB >= 8 ? 3 : 24 / WPB) factor_gj_kernel(int S, int64_t ld, const BView b,
                                                              const double* __restrict__ jac, float* __restrict__ AI,
                                                              unsigned char* __restrict__ piv, float* __restrict__ G,
-                                                             int* __restrict__ sing, double pivtol) {
+                                                             int* __restrict__ sing, double pivtol,
+                                                             const int* __restrict__ skip = nullptr) {
+    if (skip && *skip) return;   // the stored inverses are those of this Jacobian (every block leaves)
     // per warp: the assembly block (reused as the row-major inverse on the way out), G_n
     // by unknown (the next stage's Schur update reads it), and the broadcast row
     __shared__ __align__(16) float sA[WPB][NV * PADQ];
