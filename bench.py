@@ -42,11 +42,11 @@ DEFAULT_WORKLOAD = "absorber-S5000-tn5-seed2"
 # 22 x 22 factor (968), the coupling (28) and G (484) per stage and right-hand side.
 EVAL_BYTES_PER_SCEN = 8 * (220 + 220 + 18 + 220 + 1497 + 661)    # read x, lambda, feed; write c, J, H
 # FP64 flops of one evaluation, per scenario, from the kernels' executed FP64 instructions
-# (one ncu capture at 5000 scenarios: DFMA 29.325e6, DMUL 27.92e6, DADD 12.875e6 thread
-# instructions for the full evaluation; DFMA 18.99e6, DMUL 7.125e6, DADD 8.45e6 for the
+# (one ncu capture at 5000 scenarios: DFMA 26.875e6, DMUL 28.27e6, DADD 12.775e6 thread
+# instructions for the full evaluation; DFMA 16.59e6, DMUL 7.775e6, DADD 8.6e6 for the
 # trial evaluation), a fused multiply-add counted as two
-EVAL_FP64_FLOPS_PER_SCEN = (2 * 29.325e6 + 27.92e6 + 12.875e6) / 5000
-TRIAL_FP64_FLOPS_PER_SCEN = (2 * 18.99e6 + 7.125e6 + 8.45e6) / 5000
+EVAL_FP64_FLOPS_PER_SCEN = (2 * 26.875e6 + 28.27e6 + 12.775e6) / 5000
+TRIAL_FP64_FLOPS_PER_SCEN = (2 * 16.59e6 + 7.775e6 + 8.6e6) / 5000
 TRIAL_BYTES_PER_SCEN = 8 * (2 * 220 + 18)                         # read x, dx, feed
 FACTOR_FLOPS_PER_SCEN = {8: 10 * 7183 + 9 * 10406,                # FP64: stage LUs + G
                          4: 9 * 22 * (21 * 32 * 2 + 33) + 22 * (21 * 21 * 2 + 22)}   # FP32: Gauss-Jordan

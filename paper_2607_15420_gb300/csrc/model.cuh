@@ -146,6 +146,24 @@ __host__ __device__ inline void stage_eval(const Params& P, const StageIn& in, c
     const double Vb = in.qb[4], Tb = sT * in.qb[5];
     const double Pr = in.P;
 
+    // ---- reciprocals of T + C (Antoine), the stage pressure, the apparent-fraction total
+    // of (9b) and T from one division: a = Tc Pr, b = tot T, r = 1 / (a b), then
+    // 1/Tc = r b Pr, 1/Pr = r b Tc, 1/tot = r a T, 1/T = r a tot (all positive and O(1e-3
+    // .. 1e3) at interior points)
+    double am = 0, ac = 0, aw = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        am += app_m(k) * x[k];
+        ac += app_c(k) * x[k];
+        aw += app_w(k) * x[k];
+    }
+    const double tot = am + ac + aw;
+    const double Tc = T + P.psat_c;
+    const double ra = Tc * Pr, rb = tot * T;
+    const double r4 = 1.0 / (ra * rb);
+    const double rbr = r4 * rb, rar = r4 * ra;
+    const double iTc = rbr * Pr, iPr = rbr * Tc, it = rar * T, invT = rar * tot;
+
     // ---- enthalpies ---------------------------------------------------------------
     const double dT = T - P.T_ref, dTa = Ta - P.T_ref, dTb = Tb - P.T_ref;
     double hL[9], cpL[9], hLa[9], cpLa[9], hV[4], cpV[4], hVb[4], cpVb[4];
@@ -180,13 +198,10 @@ __host__ __device__ inline void stage_eval(const Params& P, const StageIn& in, c
     }
 
     // ---- (9a) water saturation pressure ---------------------------------------------
-    const double Tc = T + P.psat_c;
-    const double iTc = 1.0 / Tc;
     const double ps = exp(P.psat_a - P.psat_b * iTc);
     const double bT2 = P.psat_b * iTc * iTc;
     const double ps1 = ps * bT2;                                        // dPsat/dT
     const double ps2 = ps * (bT2 * bT2 - 2.0 * P.psat_b * iTc * iTc * iTc);  // d2Psat/dT2
-    const double iPr = 1.0 / Pr;
     // reciprocals of the scaled liquid fractions (derivatives of their logarithms), all
     // nine from one division: prefix products p_c = q_0 ... q_c, r = 1 / p_8, then walking
     // back 1/q_c = r p_{c-1} and r <- r q_c (the fractions are positive and O(1))
@@ -209,17 +224,7 @@ __host__ __device__ inline void stage_eval(const Params& P, const StageIn& in, c
     }
 
     // ---- (9b) Henry coefficient --------------------------------------------------------
-    double am = 0, ac = 0, aw = 0;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        am += app_m(k) * x[k];
-        ac += app_c(k) * x[k];
-        aw += app_w(k) * x[k];
-    }
-    const double tot = am + ac + aw;
-    const double it = 1.0 / tot;
     const double um = am * it, uw = aw * it;
-    const double invT = 1.0 / T;
     const double g = P.henry_a + P.henry_b * invT + P.henry_m * um + P.henry_w * uw;
     const double Hh = exp(g);
     const double gT = -P.henry_b * invT * invT;
@@ -249,6 +254,9 @@ __host__ __device__ inline void stage_eval(const Params& P, const StageIn& in, c
         // ln(prod over products of q_c / prod over reactants of q_c) + sum_c nu_ck ln sx_c
         // (the scaled fractions are O(1): the quotients stay far from over- and underflow)
         const double lT = log(T);
+        // the five quotients' denominators inverted together from one division (prefix
+        // products, then back)
+        double qn[5], qd[5], pre[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             double num = 1.0, den = 1.0;
@@ -257,8 +265,17 @@ __host__ __device__ inline void stage_eval(const Params& P, const StageIn& in, c
                 if (nu(c, k) > 0) num *= in.q[LX + c];
                 if (nu(c, k) < 0) den *= in.q[LX + c];
             }
+            qn[k] = num;
+            qd[k] = den;
+            pre[k] = k ? pre[k - 1] * den : den;
+        }
+        double rq = 1.0 / pre[4];
+#pragma unroll
+        for (int k = 4; k >= 0; --k) {
+            const double rk = k ? rq * pre[k - 1] : rq;
+            if (k) rq *= qd[k];
             const double r = -(P.KE_A[k] + P.KE_B[k] * invT + P.KE_C[k] * lT + P.KE_D[k] * T) + P.lnsxr[k] +
-                             log(num / den);
+                             log(qn[k] * rk);
             e.res(R_RX + k, r);
         }
         double sx_ = -1.0, sy_ = -1.0;
