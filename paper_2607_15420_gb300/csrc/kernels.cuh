@@ -119,7 +119,6 @@ __device__ __forceinline__ unsigned long long key_max(unsigned long long a, unsi
     return a > b ? a : b;
 }
 __device__ __forceinline__ double key_double(unsigned long long k) { return __longlong_as_double((long long)k); }
-constexpr unsigned long long INF_KEY = 0x7ff0000000000000ull;   // keys above it are NaN
 
 __device__ inline double red_id(int op) { return op == RSUM ? 0.0 : (op == RMAX ? -INFINITY : INFINITY); }
 
