@@ -376,6 +376,9 @@ struct DState {
     // the learned start's acceptance test at the first evaluation: the inlet-copy start's
     // (E_0, theta) and the learned start's
     double gate_E0, gate_theta, first_E0, first_theta;
+    // the switching condition's powers at the iterate, for every trial of its line search:
+    // (-grad phi . d)^s_phi (when negative) and delta theta^s_theta
+    double pw_phi, pw_th;
 };
 
 // state shared by the problems of a run
