@@ -387,6 +387,7 @@ struct DGlobal {
     int rk;             // refinement round of the current solve (shared, as the launches are)
     int esc_any;        // an FP64 escalation took place in this iteration
     int guard_iter, guard_ls;   // executions of the iteration / line-search loop bodies
+    int esc_blocks;     // blocks of esc_kernel done (its last block decides; reset there)
     int lsfac;          // the stored factors of J are those of the least-squares estimate at x
     int fac_skip;       // the Newton step's factorization keeps them (iteration 0 only)
     long long launches; // kernels of this library launched by graph execution
