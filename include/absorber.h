@@ -518,6 +518,13 @@ abs_status abs_mlp_set_tensor_cores(abs_mlp* net, int32_t on);
  * abs_mlp_forward, abs_mlp_loss_grad and abs_mlp_train then return ABS_ERR_TIMEOUT. */
 int32_t abs_mlp_device_fault(const abs_mlp* net);
 
+/* Self-test of that path: one 128 x 256 x 256 tensor-core product whose MMAs are withheld,
+ * so that its wait runs out after 1024 polls; the kernel frees its tensor memory and sets
+ * the fault flag, which this call reads after synchronising the stream and then clears.
+ * Returns ABS_ERR_TIMEOUT (the expected outcome: the expiry was reported), ABS_ERR_CUDA
+ * when it was not reported or a CUDA call failed. */
+abs_status abs_mlp_selftest_wait(abs_mlp* net, abs_stream_t stream);
+
 /* Loss of the n pairs (X, Y) (raw, device) and its gradient with respect to the
  * parameters (device, ABS_MLP_PARAMS floats, or NULL).  *loss: host.  Synchronous. */
 abs_status abs_mlp_loss_grad(abs_mlp* net, const float* X, const float* Y, int64_t n, double* loss,

@@ -148,6 +148,7 @@ EXPORTS = {
     "abs_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "abs_mlp_set_tensor_cores": (C.c_int, [C.c_void_p, C.c_int32]),
     "abs_mlp_device_fault": (C.c_int32, [C.c_void_p]),
+    "abs_mlp_selftest_wait": (C.c_int, [C.c_void_p, C.c_void_p]),
     "abs_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double),
                                     C.c_void_p, C.c_void_p]),
     "abs_default_train_options": (None, [C.POINTER(AbsTrainOptions)]),
@@ -548,6 +549,11 @@ class MLP:
 
     def device_fault(self):
         return int(lib().abs_mlp_device_fault(self.h))
+
+    def selftest_wait(self, stream=None):
+        """Status of the tensor-core wait's self-test (ABS_ERR_TIMEOUT when the expiry was
+        reported)."""
+        return int(lib().abs_mlp_selftest_wait(self.h, _stream(stream)))
 
     def loss_grad(self, X, Y, grad=None, stream=None):
         loss = C.c_double()

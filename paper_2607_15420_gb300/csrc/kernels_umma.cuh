@@ -92,9 +92,10 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait for the completion of phase `parity`; false when it gave up
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (long long it = 0; it < WAIT_LIMIT; ++it)
+// bounded wait for the completion of phase `parity` (at most `limit` polls); false when it
+// gave up
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit) {
+    for (long long it = 0; it < limit; ++it)
         if (mbar_try(mbar, parity)) return true;
     return false;
 }

@@ -209,13 +209,16 @@ __global__ void __launch_bounds__(GT) gemm_kernel(int M, int N, int K, const flo
 // bfloat16 [N][K] row-major, K a multiple of 64; epilogues EPI_BIAS_GELU, EPI_BIAS,
 // EPI_DENORM as gemm_kernel's.  Grid (ceil(N / 64), ceil(M / 128)), 128 threads,
 // umma::SMEM bytes of dynamic shared memory.  fault: set when a wait for the MMAs gave up
-// (the block then frees its tensor memory and leaves its outputs unwritten).
+// (the block then frees its tensor memory and leaves its outputs unwritten).  idle (the
+// self-test of that path): no MMA and no commit are issued, so the first wait runs out
+// after wait_limit polls.
 template <int EPI>
 __global__ void __launch_bounds__(umma::T) gemm_tc_kernel(int M, int N, int K, const float* __restrict__ A,
                                                           const __nv_bfloat16* __restrict__ W,
                                                           const float* __restrict__ bias, float* __restrict__ Z,
                                                           float* __restrict__ C, const float* __restrict__ scale,
-                                                          const float* __restrict__ shift, int* __restrict__ fault) {
+                                                          const float* __restrict__ shift, int* __restrict__ fault,
+                                                          int idle, long long wait_limit) {
     using namespace umma;
     extern __shared__ unsigned char tc_smem[];
     __shared__ __align__(8) uint64_t mbar;
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(umma::T) gemm_tc_kernel(int M, int N, int K, c
         }
         fence_smem_async();
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !idle) {
             fence_after();
 #pragma unroll
             for (int s = 0; s < KC / 16; ++s)
@@ -298,7 +301,7 @@ __global__ void __launch_bounds__(umma::T) gemm_tc_kernel(int M, int N, int K, c
             commit(mb);
         }
         // the chunk's MMAs are done before its shared memory is refilled
-        ok = __syncthreads_and(ok && mbar_wait(mb, (uint32_t)(c & 1)));
+        ok = __syncthreads_and(ok && mbar_wait(mb, (uint32_t)(c & 1), wait_limit));
         if (!ok) break;
         fence_after();
     }
@@ -349,14 +352,16 @@ __global__ void __launch_bounds__(umma::T) gemm_tc_kernel(int M, int N, int K, c
 
 template <int EPI>
 abs_status gemm_tc(abs_mlp* net, cudaStream_t st, int M, int N, int K, const float* A, const __nv_bfloat16* W,
-                   float* C, const float* bias, float* Z, const float* scale, const float* shift) {
+                   float* C, const float* bias, float* Z, const float* scale, const float* shift,
+                   bool idle = false) {
     static bool attr = false;
     if (!attr) {
         MCK(cudaFuncSetAttribute(gemm_tc_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, umma::SMEM));
         attr = true;
     }
     const dim3 grid((unsigned)((N + umma::TN - 1) / umma::TN), (unsigned)((M + umma::TM - 1) / umma::TM));
-    gemm_tc_kernel<EPI><<<grid, umma::T, umma::SMEM, st>>>(M, N, K, A, W, bias, Z, C, scale, shift, net->dfault);
+    gemm_tc_kernel<EPI><<<grid, umma::T, umma::SMEM, st>>>(M, N, K, A, W, bias, Z, C, scale, shift, net->dfault,
+                                                           idle ? 1 : 0, idle ? 1024ll : umma::WAIT_LIMIT);
     return mlaunch(net);
 }
 
@@ -752,6 +757,23 @@ abs_status abs_mlp_set_tensor_cores(abs_mlp* net, int32_t on) {
     if (!net || (on != 0 && on != 1)) return mfail(net, ABS_ERR_ARG, "bad argument");
     net->tc = on != 0;
     return ABS_OK;
+}
+
+abs_status abs_mlp_selftest_wait(abs_mlp* net, abs_stream_t stream) {
+    if (!net) return mfail(net, ABS_ERR_ARG, "bad argument");
+    if (abs_mlp_device_fault(net)) return mfail(net, ABS_ERR_TIMEOUT, "a tensor-core product gave up waiting");
+    cudaStream_t st = (cudaStream_t)stream;
+    abs_status r;
+    if ((r = ensure_cap(net, umma::TM)) != ABS_OK) return r;
+    // one 128 x 256 x 256 product with its MMAs withheld, on the activation workspace
+    if ((r = gemm_tc<EPI_BIAS_GELU>(net, st, umma::TM, NH, NH, net->a[0], net->wb + OFF_W[1], net->a[1],
+                                     net->theta + OFF_B[1], net->z[1], nullptr, nullptr, true)) != ABS_OK)
+        return r;
+    MCK(cudaStreamSynchronize(st));
+    const bool expired = abs_mlp_device_fault(net) != 0;
+    *(volatile int*)net->hfault = 0;
+    if (!expired) return mfail(net, ABS_ERR_CUDA, "the withheld wait did not report its expiry");
+    return mfail(net, ABS_ERR_TIMEOUT, "a tensor-core product gave up waiting (self-test)");
 }
 
 abs_status abs_mlp_forward(abs_mlp* net, const float* X, int64_t n, float* Y, abs_stream_t stream) {

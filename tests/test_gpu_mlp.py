@@ -106,6 +106,24 @@ def test_tensor_core_products_match_cuda_core_products_and_oracle(B, n):
         net.set_tensor_cores(2)
 
 
+def test_tensor_core_wait_expiry_is_reported(B):
+    # the one device-side wait: its self-test withholds the MMAs so that the bounded wait
+    # runs out; the kernel frees its tensor memory and reports through the fault flag, the
+    # call returns ABS_ERR_TIMEOUT and clears the flag, and the products work afterwards
+    import torch
+    theta, norm, X, Y = _case(77, 300)
+    net = _net(B, theta, norm)
+    assert net.device_fault() == 0
+    assert net.selftest_wait() == -8   # ABS_ERR_TIMEOUT
+    assert net.device_fault() == 0
+    Yt = torch.zeros((300, mlp.N_OUT), dtype=torch.float32, device="cuda")
+    net.forward(_dev32(X), Yt)
+    yo = mlp.predict(theta, X, norm)
+    scale = norm["out_scale"] * (1.0 + np.abs(mlp.forward(theta, X, norm)))
+    assert np.max(np.abs(_host(Yt) - yo) / scale) <= 1e-5
+    assert net.device_fault() == 0
+
+
 def test_forward_large_chunked(B):
     # more rows than one inference pass holds (8192): sampled rows against the oracle
     import torch
