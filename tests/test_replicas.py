@@ -1,6 +1,7 @@
 """The bench's multi-GPU path is replicas only (independent problems, no data-path
 collective): its whole-job numbers are the slowest rank's time and the sum of every
-rank's iterations.  Checked with two gloo ranks on the CPU."""
+rank's iterations.  Checked with two gloo ranks on the CPU.  Also: the roofline line's captured
+DRAM traffic is reported only for the kernel source it was measured on."""
 import os
 import socket
 
@@ -44,3 +45,26 @@ def test_job_totals_two_gloo_ranks():
 def test_job_totals_single_rank():
     import bench
     assert bench.job_totals(1.25, 7.0, 1, "cpu") == (1.25, 7.0)
+
+
+def test_roofline_traffic_only_for_the_captured_kernel_source(tmp_path, monkeypatch):
+    # the factor's DRAM traffic is reported only while its kernel source is the one the
+    # capture measured (sha256 of kernels_warp.cuh), only at the captured size and element
+    # size; an edited source makes it null
+    import shutil
+    import bench
+    val = bench.captured_traffic("factor", 4, 5000)
+    assert val is not None and val > 0
+    assert bench.captured_traffic("factor", 4, 4999) is None
+    assert bench.captured_traffic("factor", 8, 5000) is None
+    assert bench.captured_traffic("solve", 4, 5000) is None
+    root = tmp_path / "repo"
+    csrc = root / "paper_2607_15420_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    src = os.path.join(bench.ROOT, "paper_2607_15420_gb300", "csrc", "kernels_warp.cuh")
+    shutil.copy(src, csrc / "kernels_warp.cuh")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.captured_traffic("factor", 4, 5000) == val
+    with open(csrc / "kernels_warp.cuh", "a") as f:
+        f.write("\n// edited\n")
+    assert bench.captured_traffic("factor", 4, 5000) is None
